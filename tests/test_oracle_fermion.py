@@ -1,0 +1,191 @@
+"""Pins for the oracle's fermion matrix and solvers, each against something other than
+the oracle itself: closed forms derived from Eq. (D_formula), the antiunitary symmetry the
+paper cites for sign-problem freedom, momentum-space block diagonalisation at uniform phi,
+numpy's dense solver and eigenvalue routines."""
+
+import numpy as np
+import pytest
+from scipy.optimize import linear_sum_assignment
+
+from oracle.model import Params
+from oracle import fermion, solver, hmc
+from paper_2204_14241_gb300 import inputs
+
+P = Params(L=4, Nt=6)
+
+
+def rand_phi(p, seed=0):
+    return np.random.default_rng(seed).standard_normal((3, p.Nt, p.L, p.L))
+
+
+def rand_vec(p, seed=1):
+    g = np.random.default_rng(seed)
+    sh = (2, 2, p.Nt, p.L, p.L)
+    return g.standard_normal(sh) + 1j * g.standard_normal(sh)
+
+
+def match_multisets(a, b):
+    """Largest distance after optimally pairing two equal-size sets of complex numbers."""
+    d = np.abs(a[:, None] - b[None, :])
+    i, j = linear_sum_assignment(d)
+    return d[i, j].max()
+
+
+def free_eigs_closed_form(p):
+    """Eigenvalues of D at g = 0: e^{i w} - 1 - dtau (mu_a + 2 t_h cos kx + 2 t_v cos ky),
+    w = (2n+1) pi / Nt (antiperiodic), k = 2 pi m / L, each twice (spin)."""
+    out = []
+    for a in range(2):
+        for n in range(p.Nt):
+            w = (2 * n + 1) * np.pi / p.Nt
+            for mx in range(p.L):
+                for my in range(p.L):
+                    kx, ky = 2 * np.pi * mx / p.L, 2 * np.pi * my / p.L
+                    e = np.exp(1j * w) - 1 - p.dtau * (p.mu[a] + 2 * p.t_h[a] * np.cos(kx)
+                                                        + 2 * p.t_v[a] * np.cos(ky))
+                    out += [e, e]
+    return np.array(out)
+
+
+@pytest.mark.parametrize("L,Nt", [(4, 6), (2, 5), (6, 3)])
+def test_free_spectrum_closed_form(L, Nt):
+    p = Params(L=L, Nt=Nt, g=0.0)
+    D = fermion.dense_D(p, rand_phi(p))
+    assert match_multisets(np.linalg.eigvals(D), free_eigs_closed_form(p)) < 1e-12
+
+
+def test_free_logdet_closed_form():
+    # prod over the Nt antiperiodic roots z_n of z^Nt = -1 of (z_n - a) has modulus |1 + a^Nt|
+    p = Params(L=4, Nt=6, g=0.0)
+    D = fermion.dense_D(p, rand_phi(p))
+    _, logabs = np.linalg.slogdet(D @ D.conj().T)
+    k = 2 * np.pi * np.arange(p.L) / p.L
+    ref = 0.0
+    for a in range(2):
+        eps = 2 * p.t_h[a] * np.cos(k)[:, None] + 2 * p.t_v[a] * np.cos(k)[None, :]
+        aa = 1 + p.dtau * (p.mu[a] + eps)
+        ref += 2 * 2 * np.sum(np.log(np.abs(1 + aa ** p.Nt)))   # x2 spin, x2 for |det D|^2
+    assert abs(logabs - ref) < 1e-10 * abs(ref)
+
+
+def test_det_real_nonnegative_and_conjugate_pairs():
+    # Berg et al. (cited for sign-problem freedom): det D is real and >= 0 for any phi.
+    p = Params(L=4, Nt=6, g=1.3)
+    D = fermion.dense_D(p, rand_phi(p, 5))
+    sign, _ = np.linalg.slogdet(D)
+    assert abs(sign - 1.0) < 1e-10
+    ev = np.linalg.eigvals(D)
+    assert match_multisets(ev, np.conj(ev)) < 1e-9
+
+
+def test_antiunitary_symmetry():
+    # T = (i sigma^y_spin x sigma^z_band) K with T^2 = -1 commutes with D: U conj(D) U^-1 = D.
+    p = Params(L=4, Nt=4, g=0.9)
+    D = fermion.dense_D(p, rand_phi(p, 3))
+    isy = np.array([[0, 1], [-1, 0]], dtype=complex)
+    sz = np.diag([1.0, -1.0])
+    U = np.kron(np.kron(sz, isy), np.eye(p.V))   # (alpha, s, tau, x, y) C-order
+    assert np.abs(U @ D.conj() @ np.linalg.inv(U) - D).max() < 1e-13
+    assert np.abs(U @ U.conj() + np.eye(p.n)).max() < 1e-13
+
+
+def test_uniform_phi_block_diagonalisation():
+    # Uniform phi: e^{iQ.r} couples k to k+Q, so D splits into 8x8 blocks over
+    # (band, spin, {k, k+Q}) per Matsubara frequency; brute-force their eigenvalues.
+    p = Params(L=4, Nt=4, g=0.8)
+    ph = np.array([0.3, -0.7, 0.5])
+    phi = np.broadcast_to(ph[:, None, None, None], (3, p.Nt, p.L, p.L)).copy()
+    D = fermion.dense_D(p, phi)
+    s = [np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]), np.array([[1, 0], [0, -1]])]
+    phs = sum(ph[a] * s[a] for a in range(3))
+    eigs = []
+    for n in range(p.Nt):
+        w = (2 * n + 1) * np.pi / p.Nt
+        for mx in range(p.L):
+            for my in range(p.L):
+                ks = [(2 * np.pi * mx / p.L, 2 * np.pi * my / p.L),
+                      (2 * np.pi * mx / p.L + np.pi, 2 * np.pi * my / p.L + np.pi)]
+                B = np.zeros((8, 8), dtype=complex)   # index (q, alpha, s), q = k or k+Q
+                for q, (kx, ky) in enumerate(ks):
+                    for a in range(2):
+                        e = np.exp(1j * w) - 1 - p.dtau * (p.mu[a] + 2 * p.t_h[a] * np.cos(kx)
+                                                            + 2 * p.t_v[a] * np.cos(ky))
+                        for sp in range(2):
+                            B[q * 4 + a * 2 + sp, q * 4 + a * 2 + sp] = e
+                        for sp in range(2):
+                            for sq in range(2):
+                                B[q * 4 + a * 2 + sp, (1 - q) * 4 + (1 - a) * 2 + sq] = (
+                                    p.dtau * p.g * phs[sp, sq])
+                eigs.extend(np.linalg.eigvals(B))
+    eigs = np.array(eigs)                      # every block appears twice (k and k+Q)
+    dense = np.linalg.eigvals(D)
+    assert match_multisets(np.concatenate([dense, dense]), eigs) < 1e-11
+
+
+def test_matrix_free_equals_dense():
+    p = Params(L=4, Nt=5, g=1.1)
+    phi = rand_phi(p, 7)
+    D = fermion.dense_D(p, phi)
+    v = rand_vec(p, 8)
+    assert np.abs(D @ v.ravel() - fermion.apply_D(p, phi, v).ravel()).max() < 1e-13
+    assert np.abs(D.conj().T @ v.ravel() - fermion.apply_Ddag(p, phi, v).ravel()).max() < 1e-13
+    A = D @ D.conj().T
+    assert np.abs(A @ v.ravel() - fermion.apply_A(p, phi, v).ravel()).max() < 1e-12
+
+
+def test_heatbath_identity():
+    # varphi = D chi  =>  varphi^dag (D D^dag)^{-1} varphi = chi^dag chi (Section HMC).
+    phi = rand_phi(P, 2)
+    chi = rand_vec(P, 3)
+    vp = hmc.heatbath(P, phi, chi)
+    s = hmc.pseudofermion_action(P, phi, [vp])
+    assert abs(s - np.vdot(chi, chi).real) < 1e-10 * np.vdot(chi, chi).real
+
+
+@pytest.mark.parametrize("method", ["cg", "pcg"])
+def test_cg_matches_dense_solve(method):
+    phi = rand_phi(P, 4)
+    b = rand_vec(P, 5)
+    D = fermion.dense_D(P, phi)
+    ref = np.linalg.solve(D @ D.conj().T, b.ravel()).reshape(b.shape)
+    f = solver.cg if method == "cg" else solver.pcg
+    x, it, res = f(P, phi, b, tol=1e-12)
+    assert res < 1e-11
+    assert np.abs(x - ref).max() < 1e-9 * np.abs(ref).max()
+
+
+def test_pcg_exact_at_zero_coupling():
+    # g -> 0: P = (D D^dag)^{-1}, so PCG converges in a single iteration (Eq. precon ff.).
+    p = Params(L=4, Nt=6, g=0.0)
+    x, it, res = solver.pcg(p, rand_phi(p), rand_vec(p), tol=1e-12)
+    assert it == 1 and res < 1e-13
+
+
+def test_twisted_fourier_diagonalises_K():
+    # Eq. (Kdiag): K = F~ K-hat F~^*. Apply dense K to twisted plane waves.
+    p = Params(L=4, Nt=6, g=0.0)
+    K = fermion.dense_D(p, np.zeros((3, p.Nt, p.L, p.L)))
+    kh = fermion.free_symbol(p)
+    tau = np.arange(p.Nt)[:, None, None]
+    x = np.arange(p.L)[None, :, None]
+    y = np.arange(p.L)[None, None, :]
+    for (a, s, n, mx, my) in [(0, 0, 0, 0, 0), (1, 1, 2, 1, 3), (0, 1, 5, 2, 2), (1, 0, 3, 3, 1)]:
+        wave = np.exp(1j * np.pi * (2 * n + 1) * tau / p.Nt + 2j * np.pi * (mx * x + my * y) / p.L)
+        v = np.zeros((2, 2, p.Nt, p.L, p.L), dtype=complex)
+        v[a, s] = wave
+        assert np.abs(K @ v.ravel() - kh[a, n, mx, my] * v.ravel()).max() < 1e-13
+
+
+def test_precond_is_inverse_of_KKdag():
+    p = Params(L=4, Nt=6, g=0.7)
+    K = fermion.dense_D(p, np.zeros((3, p.Nt, p.L, p.L)))
+    v = rand_vec(p, 9)
+    Pv = solver.apply_precond(p, v)
+    assert np.abs((K @ K.conj().T) @ Pv.ravel() - v.ravel()).max() < 1e-11 * np.abs(v).max()
+
+
+def test_layout_roundtrip():
+    v = inputs.fermion_noise(0, 1, 4, 6)[0]
+    assert np.array_equal(inputs.from_paper_fermion(inputs.to_paper_fermion(v)), v)
+    f = inputs.gaussian_field(0, 4, 6)
+    assert np.array_equal(inputs.from_paper_boson(inputs.to_paper_boson(f)), f)
