@@ -1,0 +1,202 @@
+/*
+ * hmc.h -- C ABI of the GB300 pseudofermion HMC library (libhmc.so) for the two-band
+ * O(3) spin-fermion model of Lunts, Albergo and Lindsey, arXiv:2204.14241.
+ *
+ * Notation bridge. The paper calls the fermion matrix D(phi) (Eq. D_formula) and the
+ * HMC mass matrix M. This ABI keeps the conventional names apply_M / apply_MdagM for
+ * the FERMION matrix: "M" below is the paper's D, and apply_MdagM applies the paper's
+ * Hermitian positive definite normal operator A = D D^dagger (Eq. linsys).
+ *
+ * Layouts (all field pointers are caller-owned, contiguous, device memory unless a
+ * function says "host"):
+ *   site index      s = (tau * L + y) * L + x            (x fastest; V = Nt * L * L)
+ *   boson field     phi[a][s], a = 0, 1, 2               real, 3 * V entries
+ *   fermion vector  v[k][s][alpha][spin]                 complex, interleaved re/im,
+ *                   k < nrhs right-hand sides, alpha in {x-band, y-band}, 4 * V entries per k
+ *   sigma-hat       sig[a][n_tau][m_y][m_x]              real, the metric's Fourier variances
+ * The paper orders fermion indices (alpha, s, tau, x, y); the layout above is a
+ * permutation of it with the four internal components of a site adjacent.
+ *
+ * Precision arguments: HMC_FP64 means phi is double and vectors are complex128
+ * (double re, double im); HMC_FP32 means phi is float and vectors are complex64.
+ *
+ * Streams and synchronisation: every call is enqueued on the stream given to hmc_init
+ * (0 = legacy default stream). Calls that return host scalars (S_pf, norms, stats,
+ * trajectory results) synchronise that stream before returning; the others are
+ * asynchronous. Workspace is allocated once in hmc_init; no call allocates afterwards.
+ *
+ * Errors: every function returns HMC_OK (0) or a positive code; hmc_last_error()
+ * gives a one-line message. Invalid arguments never reach the GPU.
+ */
+#ifndef HMC_H
+#define HMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum hmc_status {
+    HMC_OK = 0,
+    HMC_ERR_ARG = 1,        /* bad size, chain index, null pointer, or misaligned pointer */
+    HMC_ERR_NOCONV = 2,     /* CG hit maxit; x holds the last iterate, stats the true residual */
+    HMC_ERR_NONFINITE = 3,  /* NaN or Inf seen in a residual norm or an energy */
+    HMC_ERR_TIMEOUT = 4,    /* reserved for bounded device-side waits that gave up */
+    HMC_ERR_CUDA = 5,       /* a CUDA runtime call failed; see hmc_last_error */
+    HMC_ERR_STATE = 6       /* call not valid in the context's current state */
+};
+
+enum hmc_prec { HMC_FP64 = 0, HMC_FP32 = 1 };
+
+/* Solver precision of a context: plain FP64 CG, or FP32 inner CG with FP64 reliable
+ * updates (true residual and solution accumulated in FP64). */
+enum hmc_solver_mode { HMC_SOLVER_FP64 = 0, HMC_SOLVER_MIXED = 1 };
+
+enum hmc_noise { HMC_NOISE_EXPLICIT = 0, HMC_NOISE_PHILOX = 1 };
+
+/* Model and solver parameters (Section "Sign-problem-free UV completion" and Section
+ * "QMC path integral with fermions"; the lattice S_B is the forward-difference
+ * discretisation of the paper's continuum boson action). */
+typedef struct {
+    int L;              /* spatial extent, even, >= 2 */
+    int Nt;             /* time slices, >= 2 */
+    double dtau;        /* Trotter step */
+    double t_h[2];      /* nearest-neighbour hopping along x for bands x, y */
+    double t_v[2];      /* nearest-neighbour hopping along y for bands x, y */
+    double mu[2];       /* chemical potential per band */
+    double g;           /* Yukawa coupling in D's on-site term dtau g (-1)^{x+y} phi.sigma sigma^x */
+    double r;           /* boson mass term (r/2) phi^2 */
+    double u;           /* quartic term (u/4) phi^4 */
+    double c;           /* boson velocity: (1/c^2)(d_tau phi)^2 */
+    int solver_mode;    /* hmc_solver_mode */
+    int nrhs_max;       /* most pseudofermion right-hand sides per call, >= 1 */
+    double cg_tol;      /* default relative true-residual tolerance ||b - A x|| / ||b|| */
+    int cg_maxit;       /* default iteration cap */
+} hmc_params;
+
+/* Per-chain lattice (batched chains of uneven sizes). Coupling constants other than r
+ * are shared; L, Nt and r may differ per chain. */
+typedef struct {
+    int L, Nt;
+    double r;
+} hmc_chain;
+
+/* Solver statistics (per call, over all right-hand sides). */
+typedef struct {
+    int iterations;          /* inner iterations of the slowest right-hand side */
+    int reliable_updates;    /* FP64 true-residual recomputations (mixed mode) */
+    int converged;           /* 1 if every right-hand side met the tolerance */
+    double true_rel_resid;   /* max over RHS of ||b - A x|| / ||b||, evaluated in FP64 */
+} hmc_cg_stats;
+
+typedef struct hmc_ctx hmc_ctx;
+
+/* Create a context for n_chains lattices. chains may be NULL, in which case every chain
+ * uses p->L, p->Nt, p->r. cuda_stream is a cudaStream_t (or NULL for the default
+ * stream). Allocates all device workspace. Errors: HMC_ERR_ARG, HMC_ERR_CUDA. */
+int hmc_init(const hmc_params* p, int n_chains, const hmc_chain* chains, void* cuda_stream,
+             hmc_ctx** out);
+int hmc_destroy(hmc_ctx* ctx);
+const char* hmc_last_error(const hmc_ctx* ctx);   /* ctx may be NULL (global last error) */
+
+/* y = D x (dagger = 0) or y = D^dagger x (dagger = 1) for nrhs vectors -- Eq. (D_formula):
+ * diagonal -1 - dtau mu_alpha, forward time hop with -1 at tau = Nt-1 (antiperiodic),
+ * spatial hop -dtau t_alpha, on-site dtau g (-1)^{x+y} phi(tau,r).sigma (x) sigma^x.
+ * phi: [3][V] in prec; x, y: [nrhs][V][4] complex in prec; x and y must not overlap. */
+int apply_M(hmc_ctx* ctx, int chain, int prec, const void* phi, const void* x, void* y,
+            int dagger, int nrhs);
+
+/* y = A x = D (D^dagger x) (Eq. linsys), fused in one pass. If norm2 is not NULL it
+ * receives (host, nrhs doubles) ||D^dagger x_k||^2 = x_k^dagger A x_k. */
+int apply_MdagM(hmc_ctx* ctx, int chain, int prec, const void* phi, const void* x, void* y,
+                int nrhs, double* norm2);
+
+/* y = P x with P = (K K^dagger)^{-1} = F~ P-hat F~^* (Eqs. Dsplit, twist, Kdiag, precon),
+ * K the phi-independent part of D, applied with the twisted FFT. x, y: [nrhs][V][4] in prec. */
+int apply_precond(hmc_ctx* ctx, int chain, int prec, const void* x, void* y, int nrhs);
+
+/* Solve A x = b (Eq. linsys) by CG (precond = 0) or preconditioned CG (precond = 1),
+ * zero initial guess, for nrhs right-hand sides at once. phi: [3][V] double; b, x:
+ * complex128. Stops when the FP64 true residual of every RHS is <= tol ||b||.
+ * tol <= 0 or maxit <= 0 select the context defaults. st may be NULL.
+ * Returns HMC_ERR_NOCONV if maxit was reached (x then holds the last iterate). */
+int cg_solve(hmc_ctx* ctx, int chain, const void* phi, const void* b, void* x, int nrhs,
+             double tol, int maxit, int precond, hmc_cg_stats* st);
+
+/* F = -dS/dphi for S = S_PF (+ S_B if include_boson) at phi (Eq. hamiltonseq), with
+ * S_PF = sum_k varphi_k^dagger A^{-1} varphi_k (Eq. Z with pfs). The fermion part is
+ * 2 dtau g (-1)^{x+y} Re[X^dagger (sigma^x (x) sigma^a) Y] per site, X = A^{-1} varphi,
+ * Y = D^dagger X. phi: [3][V] double; phi_pf: [nrhs][V][4] complex128; F: [3][V] double
+ * (overwritten). S_pf (host, may be NULL) receives 2 Re(varphi^dagger X) - ||Y||^2 summed
+ * over RHS (equal to S_PF up to the square of the solver error); S_b (host, may be NULL)
+ * receives S_B(phi). The solve uses the context tolerance and precond. */
+int force(hmc_ctx* ctx, int chain, const void* phi, const void* phi_pf, int nrhs, void* F,
+          double* S_pf, int include_boson, int precond, double* S_b, hmc_cg_stats* st);
+
+/* Fourier-diagonal metric of Section "Online metric estimation" with the unitary DFT F
+ * over (tau, y, x) per component and sigma-hat even in the wave vector:
+ *   HMC_METRIC_MOMENTUM: out = F^{-1}(sigma^{-1/2} . F in)   (momentum draw from z = in)
+ *   HMC_METRIC_VELOCITY: out = F^{-1}(sigma . F in)          (d phi / dt = M^{-1} pi)
+ *   HMC_METRIC_KINETIC:  *scalar = (1/2) sum sigma |F in|^2  (out unused)
+ *   HMC_METRIC_ACCUM:    out += |F in|^2                     (Eq. covest numerator)
+ * in, out: [3][V] double; sig: [3][V] double; scalar: host. */
+enum hmc_metric_op { HMC_METRIC_MOMENTUM = 0, HMC_METRIC_VELOCITY = 1, HMC_METRIC_KINETIC = 2,
+                     HMC_METRIC_ACCUM = 3 };
+int metric_apply(hmc_ctx* ctx, int chain, int op, const void* sig, const void* in, void* out,
+                 double* scalar);
+
+/* Inputs of one HMC update of every chain (Section "HMC": heatbath varphi = D chi,
+ * pi ~ N(0, M), leapfrog, Metropolis). Arrays of device pointers have n_chains entries
+ * and are themselves host arrays. */
+typedef struct {
+    void** phi;              /* [n_chains] device double [3][V]; replaced by the new state */
+    const void** sigma_hat;  /* [n_chains] device double [3][V] */
+    double eps;              /* leapfrog step */
+    int n_leap;              /* leapfrog steps (n_leap + 1 force evaluations) */
+    int nrhs;                /* pseudofermion right-hand sides per chain */
+    int precond;             /* 1: preconditioned CG in every force evaluation */
+    int noise;               /* hmc_noise */
+    const void** chi;        /* EXPLICIT: [n_chains] device complex128 [nrhs][V][4], std complex normal */
+    const void** z;          /* EXPLICIT: [n_chains] device double [3][V], N(0, 1) */
+    const double* u;         /* EXPLICIT: [n_chains] host uniforms in [0, 1) */
+    uint64_t seed;           /* PHILOX: key */
+    uint64_t counter;        /* PHILOX: trajectory counter (distinct per trajectory) */
+} hmc_traj_in;
+
+/* Per-chain results, host arrays of n_chains entries (any may be NULL). energies holds
+ * 6 doubles per chain: kinetic, S_B, S_PF at the start, then the same at the end. */
+typedef struct {
+    double* dH;
+    int* accepted;
+    double* energies;
+    int* cg_iterations;      /* total inner CG iterations over the trajectory */
+    double* max_true_resid;  /* worst final true relative residual of any solve */
+} hmc_traj_out;
+
+/* One HMC update of every chain. Returns HMC_ERR_NOCONV / HMC_ERR_NONFINITE if a solve
+ * failed or an energy is not finite (phi is then restored to its input value). */
+int trajectory(hmc_ctx* ctx, const hmc_traj_in* in, hmc_traj_out* out);
+
+/* Tracing: *kernel_launches receives the number of kernels this context has launched since
+ * hmc_init (host-side count, no synchronisation). */
+int hmc_counters(const hmc_ctx* ctx, int64_t* kernel_launches);
+
+/* Counter-based random numbers used by HMC_NOISE_PHILOX: Philox4x32-10 (Salmon, Moraes,
+ * Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11).
+ * philox_raw: out[4j .. 4j+3] (device uint32) = Philox4x32-10(key, ctr + j), the 128-bit
+ *   counter ctr[0] (least significant word) .. ctr[3] advanced by j; key word 0 is the
+ *   low half of key. For known-answer tests.
+ * philox_normal: n standard normals (complex_out = 0: n doubles) or n standard complex
+ *   normals (complex_out = 1: n complex128 with parts N(0, 1/2)) into device memory out.
+ *   Block j of the stream (seed, counter) is Philox(key = seed, ctr = {lo j, hi j,
+ *   lo counter, hi counter}); each block gives two 53-bit uniforms and, by Box-Muller,
+ *   two normals. */
+int philox_raw(hmc_ctx* ctx, uint64_t key, const uint32_t ctr[4], int64_t nblocks, void* out);
+int philox_normal(hmc_ctx* ctx, uint64_t seed, uint64_t counter, int64_t n, int complex_out,
+                  void* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HMC_H */

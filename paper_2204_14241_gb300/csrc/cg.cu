@@ -1,0 +1,384 @@
+// Conjugate gradient on A = D D^dagger (Eq. linsys), optionally preconditioned with
+// P = (K K^dagger)^{-1} (Eq. precon), for k right-hand sides at once.
+//
+// Precision: HMC_SOLVER_FP64 iterates in complex128. HMC_SOLVER_MIXED iterates in complex64
+// and keeps the solution and the true residual in complex128 ("reliable updates": whenever
+// the iterated residual has dropped by a factor delta since the last update, or meets the
+// tolerance, the partial solution is folded into the FP64 solution, the residual is
+// recomputed in FP64 as b - A x, and the iteration continues from it with the same search
+// direction). Both modes stop on the FP64 true residual ||b - A x|| <= tol ||b||.
+//
+// Scalars (alpha, beta, norms, flags) live on the device; kernels of right-hand sides that
+// have converged return at once. The host looks at the flags every few iterations.
+#include <cmath>
+#include <type_traits>
+
+#include "internal.h"
+
+namespace hmc {
+
+template <typename R> using V16 = std::conditional_t<sizeof(R) == 4, float4, double2>;
+
+__device__ __forceinline__ float4 v_axpy(float a, float4 x, float4 y) {
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__device__ __forceinline__ double2 v_axpy(double a, double2 x, double2 y) {
+    return make_double2(fma(a, x.x, y.x), fma(a, x.y, y.y));
+}
+__device__ __forceinline__ double v_dot(float4 a, float4 b) {
+    return (double)(a.x * b.x + a.y * b.y) + (double)(a.z * b.z + a.w * b.w);
+}
+__device__ __forceinline__ double v_dot(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }
+
+constexpr int kRedBlocks = 512;   // partial sums per right-hand side for vector reductions
+
+// part[k * gridDim.x + b] = partial Re<a_k, b_k> over the 16-byte units of rhs k
+template <typename R>
+__global__ void __launch_bounds__(256) k_dot(const V16<R>* __restrict__ a, const V16<R>* __restrict__ b,
+                                             int64_t n16, double* __restrict__ part,
+                                             const CgScalars* __restrict__ cgs) {
+    __shared__ double red[8];
+    const int k = blockIdx.y;
+    if (cgs && !cgs[k].active) return;
+    const V16<R>* ak = a + k * n16;
+    const V16<R>* bk = b + k * n16;
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x)
+        s += v_dot(ak[i], bk[i]);
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) part[(int64_t)k * gridDim.x + blockIdx.x] = s;
+}
+
+// x += alpha p; r -= alpha q; partial ||r||^2
+template <typename R>
+__global__ void __launch_bounds__(256) k_cg_xr(V16<R>* __restrict__ x, V16<R>* __restrict__ r,
+                                               const V16<R>* __restrict__ p, const V16<R>* __restrict__ q,
+                                               int64_t n16, double* __restrict__ part,
+                                               const CgScalars* __restrict__ cgs) {
+    __shared__ double red[8];
+    const int k = blockIdx.y;
+    if (!cgs[k].active) return;
+    const R alpha = (R)cgs[k].alpha;
+    const int64_t off = k * n16;
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x) {
+        x[off + i] = v_axpy(alpha, p[off + i], x[off + i]);
+        const V16<R> rn = v_axpy(-alpha, q[off + i], r[off + i]);
+        r[off + i] = rn;
+        s += v_dot(rn, rn);
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) part[(int64_t)k * gridDim.x + blockIdx.x] = s;
+}
+
+// p = z + beta p
+template <typename R>
+__global__ void __launch_bounds__(256) k_cg_p(V16<R>* __restrict__ p, const V16<R>* __restrict__ z,
+                                              int64_t n16, const CgScalars* __restrict__ cgs) {
+    const int k = blockIdx.y;
+    if (!cgs[k].active) return;
+    const R beta = (R)cgs[k].beta;
+    const int64_t off = k * n16;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x)
+        p[off + i] = v_axpy(beta, p[off + i], z[off + i]);
+}
+
+__device__ __forceinline__ double row_sum(const double* part, int nblk, double* red) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += part[i];
+    return block_sum(s, red);
+}
+
+// alpha = <r, z> / <p, A p>; one block per right-hand side
+__global__ void k_cg_alpha(CgScalars* cgs, const double* __restrict__ part, int nblk) {
+    __shared__ double red[8];
+    const int k = blockIdx.x;
+    if (!cgs[k].active) return;
+    const double pAp = row_sum(part + (int64_t)k * nblk, nblk, red);
+    if (threadIdx.x == 0) {
+        cgs[k].pAp = pAp;
+        cgs[k].alpha = (pAp > 0.0 && isfinite(pAp)) ? cgs[k].rr / pAp : 0.0;
+        if (!isfinite(pAp)) cgs[k].nonfinite = 1;
+    }
+}
+
+// r2 = ||r||^2, rz_new = <r, z> (= r2 without preconditioner), beta, convergence flags
+__global__ void k_cg_beta(CgScalars* cgs, const double* __restrict__ part_r2,
+                          const double* __restrict__ part_rz, int nblk, double tol2, double delta2,
+                          int mixed) {
+    __shared__ double red[8];
+    const int k = blockIdx.x;
+    if (!cgs[k].active) return;
+    const double r2 = row_sum(part_r2 + (int64_t)k * nblk, nblk, red);
+    const double rz = part_rz ? row_sum(part_rz + (int64_t)k * nblk, nblk, red) : r2;
+    if (threadIdx.x == 0) {
+        CgScalars& c = cgs[k];
+        c.beta = c.rr > 0.0 ? rz / c.rr : 0.0;
+        c.rr = rz;
+        c.r2 = r2;
+        c.iters += 1;
+        if (!isfinite(r2) || !isfinite(rz)) c.nonfinite = 1;
+        if (r2 <= tol2 * c.b2 || (mixed && r2 < delta2 * c.r2_max)) c.need_ru = 1;
+    }
+}
+
+// Initial scalars: b2 = ||b||^2 from part, r2 = r2_max = b2, active = b2 > 0
+__global__ void k_cg_start(CgScalars* cgs, const double* __restrict__ part, int nblk) {
+    __shared__ double red[8];
+    const int k = blockIdx.x;
+    const double b2 = row_sum(part + (int64_t)k * nblk, nblk, red);
+    if (threadIdx.x == 0) {
+        CgScalars c = {};
+        c.b2 = b2;
+        c.r2 = b2;
+        c.r2_max = b2;
+        c.r2true = b2;
+        c.active = b2 > 0.0 ? 1 : 0;
+        c.nonfinite = isfinite(b2) ? 0 : 1;
+        if (!isfinite(b2)) c.active = 0;
+        cgs[k] = c;
+    }
+}
+
+// rr = <r, z> after a (re)start; one block per RHS
+__global__ void k_cg_set_rz(CgScalars* cgs, const double* __restrict__ part, int nblk) {
+    __shared__ double red[8];
+    const int k = blockIdx.x;
+    if (!cgs[k].active) return;
+    const double rz = row_sum(part + (int64_t)k * nblk, nblk, red);
+    if (threadIdx.x == 0) {
+        cgs[k].rr = rz;
+        if (!isfinite(rz)) cgs[k].nonfinite = 1;
+    }
+}
+
+// After a true-residual evaluation: r2true from part; converged RHS become inactive.
+__global__ void k_ru_finish(CgScalars* cgs, const double* __restrict__ part, int nblk, double tol2) {
+    __shared__ double red[8];
+    const int k = blockIdx.x;
+    if (!cgs[k].active) return;
+    const double r2 = row_sum(part + (int64_t)k * nblk, nblk, red);
+    if (threadIdx.x == 0) {
+        CgScalars& c = cgs[k];
+        c.r2true = r2;
+        c.need_ru = 0;
+        if (!isfinite(r2)) { c.nonfinite = 1; c.active = 0; return; }
+        if (r2 <= tol2 * c.b2) { c.active = 0; return; }
+        c.r2 = r2;
+        c.r2_max = r2;
+    }
+}
+
+// x_hi += x_lo; x_lo = 0 (mixed mode)
+__global__ void k_accum_x(double2* __restrict__ xhi, float2* __restrict__ xlo, int64_t n,
+                          const CgScalars* __restrict__ cgs) {
+    const int k = blockIdx.y;
+    if (!cgs[k].active) return;
+    const int64_t off = k * n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 l = xlo[off + i];
+        double2 h = xhi[off + i];
+        h.x += (double)l.x;
+        h.y += (double)l.y;
+        xhi[off + i] = h;
+        xlo[off + i] = make_float2(0.f, 0.f);
+    }
+}
+
+// r = b - Ax (FP64) with partial ||r||^2; optionally also r32 = (float) r
+__global__ void __launch_bounds__(256) k_residual(const double2* __restrict__ b, const double2* __restrict__ Ax,
+                                                  double2* __restrict__ r, float2* __restrict__ r32, int64_t n,
+                                                  double* __restrict__ part, const CgScalars* __restrict__ cgs) {
+    __shared__ double red[8];
+    const int k = blockIdx.y;
+    if (cgs && !cgs[k].active) return;
+    const int64_t off = k * n;
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 bb = b[off + i], a = Ax[off + i];
+        const double2 v = make_double2(bb.x - a.x, bb.y - a.y);
+        r[off + i] = v;
+        if (r32) r32[off + i] = make_float2((float)v.x, (float)v.y);
+        s += v.x * v.x + v.y * v.y;
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) part[(int64_t)k * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void k_to32(const double2* __restrict__ a, float2* __restrict__ b, int64_t n,
+                       const CgScalars* __restrict__ cgs) {
+    const int k = blockIdx.y;
+    if (cgs && !cgs[k].active) return;
+    const int64_t off = k * n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = a[off + i];
+        b[off + i] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+__global__ void k_phi_to32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+// ---- host driver ---------------------------------------------------------------------------
+template <typename R>
+static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2* b, double2* x,
+               int nrhs, double tol, int maxit, int precond, hmc_cg_stats* st) {
+    constexpr bool kMixed = sizeof(R) == 4;
+    using C = cplx<R>;
+    cudaStream_t sm = ctx->stream;
+    const int64_t n = 4 * lat.V;                      // complex entries per RHS
+    const int64_t n16 = n * sizeof(C) / 16;
+    const double tol2 = tol * tol;
+    const double delta2 = 0.01;                       // reliable update at ||r|| < 0.1 max||r||
+    CgScalars* cgs = ctx->d_cg;
+    double* part = ctx->d_part;
+    double* part2 = ctx->d_part + (int64_t)ctx->kmax * kRedBlocks;
+    const dim3 vgrid(kRedBlocks, nrhs);
+
+    C *xv, *rv, *pv, *qv, *zv;
+    const R* phiR;
+    if constexpr (kMixed) {
+        xv = ctx->d_x32; rv = ctx->d_r32; pv = ctx->d_p32; qv = ctx->d_q32;
+        zv = precond ? ctx->d_z32 : ctx->d_r32;
+        k_phi_to32<<<(unsigned)((3 * lat.V + 255) / 256), 256, 0, sm>>>(phi64, ctx->d_phi32, 3 * lat.V);
+        HMC_LAUNCH(ctx, "k_phi_to32");
+        phiR = ctx->d_phi32;
+        HMC_CUDA(ctx, cudaMemsetAsync(ctx->d_x32, 0, nrhs * n * sizeof(float2), sm));
+    } else {
+        xv = x; rv = ctx->d_r64; pv = ctx->d_p64; qv = ctx->d_q64;
+        zv = precond ? ctx->d_z64 : ctx->d_r64;
+        phiR = phi64;
+    }
+    HMC_CUDA(ctx, cudaMemsetAsync(x, 0, nrhs * n * sizeof(double2), sm));
+    // r_hi = b, ||b||^2
+    k_residual<<<vgrid, 256, 0, sm>>>(b, x, ctx->d_r64, kMixed ? ctx->d_r32 : nullptr, n, part, nullptr);
+    HMC_LAUNCH(ctx, "k_residual");
+    k_cg_start<<<nrhs, 256, 0, sm>>>(cgs, part, kRedBlocks);
+    HMC_LAUNCH(ctx, "k_cg_start");
+
+    int rc;
+    // z = P r, rz = <r, z>, p = z
+    auto restart_dir = [&](bool set_p) -> int {
+        if (precond) {
+            if ((rc = launch_precond<R>(ctx, lat, rv, zv, nrhs))) return rc;
+            k_dot<R><<<vgrid, 256, 0, sm>>>(reinterpret_cast<const V16<R>*>(rv), reinterpret_cast<const V16<R>*>(zv),
+                                            n16, part, cgs);
+        } else {
+            k_dot<R><<<vgrid, 256, 0, sm>>>(reinterpret_cast<const V16<R>*>(rv), reinterpret_cast<const V16<R>*>(rv),
+                                            n16, part, cgs);
+        }
+        HMC_LAUNCH(ctx, "k_dot");
+        k_cg_set_rz<<<nrhs, 256, 0, sm>>>(cgs, part, kRedBlocks);
+        HMC_LAUNCH(ctx, "k_cg_set_rz");
+        if (set_p) HMC_CUDA(ctx, cudaMemcpyAsync(pv, zv, nrhs * n * sizeof(C), cudaMemcpyDeviceToDevice, sm));
+        return HMC_OK;
+    };
+    if ((rc = restart_dir(true))) return rc;
+
+    // true-residual update for every active RHS
+    int n_ru = 0;
+    auto reliable_update = [&]() -> int {
+        ++n_ru;
+        if constexpr (kMixed) {
+            k_accum_x<<<vgrid, 256, 0, sm>>>(x, ctx->d_x32, n, cgs);
+            HMC_LAUNCH(ctx, "k_accum_x");
+        }
+        int nb = 0;
+        if ((rc = launch_apply_A<double>(ctx, lat, phi64, x, ctx->d_q64, nrhs, nullptr, &nb, cgs))) return rc;
+        k_residual<<<vgrid, 256, 0, sm>>>(b, ctx->d_q64, ctx->d_r64, kMixed ? ctx->d_r32 : nullptr, n, part, cgs);
+        HMC_LAUNCH(ctx, "k_residual");
+        k_ru_finish<<<nrhs, 256, 0, sm>>>(cgs, part, kRedBlocks, tol2);
+        HMC_LAUNCH(ctx, "k_ru_finish");
+        return restart_dir(false);
+    };
+
+    const int check_every = 8;
+    bool done = false, nonfinite = false;
+    int it = 0;
+    while (!done) {
+        if (it >= maxit) break;
+        int nb = 0;
+        if ((rc = launch_apply_A<R>(ctx, lat, phiR, pv, qv, nrhs, part, &nb, cgs))) return rc;
+        k_cg_alpha<<<nrhs, 256, 0, sm>>>(cgs, part, nb);
+        HMC_LAUNCH(ctx, "k_cg_alpha");
+        k_cg_xr<R><<<vgrid, 256, 0, sm>>>(reinterpret_cast<V16<R>*>(xv), reinterpret_cast<V16<R>*>(rv),
+                                          reinterpret_cast<const V16<R>*>(pv), reinterpret_cast<const V16<R>*>(qv),
+                                          n16, part, cgs);
+        HMC_LAUNCH(ctx, "k_cg_xr");
+        if (precond) {
+            if ((rc = launch_precond<R>(ctx, lat, rv, zv, nrhs))) return rc;
+            k_dot<R><<<vgrid, 256, 0, sm>>>(reinterpret_cast<const V16<R>*>(rv), reinterpret_cast<const V16<R>*>(zv),
+                                            n16, part2, cgs);
+            HMC_LAUNCH(ctx, "k_dot");
+        }
+        k_cg_beta<<<nrhs, 256, 0, sm>>>(cgs, part, precond ? part2 : nullptr, kRedBlocks, tol2, delta2, kMixed);
+        HMC_LAUNCH(ctx, "k_cg_beta");
+        k_cg_p<R><<<vgrid, 256, 0, sm>>>(reinterpret_cast<V16<R>*>(pv), reinterpret_cast<const V16<R>*>(zv), n16, cgs);
+        HMC_LAUNCH(ctx, "k_cg_p");
+        ++it;
+        if (it % check_every == 0 || it >= maxit) {
+            HMC_CUDA(ctx, cudaMemcpyAsync(ctx->h_cg, cgs, nrhs * sizeof(CgScalars), cudaMemcpyDeviceToHost, sm));
+            HMC_CUDA(ctx, cudaStreamSynchronize(sm));
+            bool any_ru = false, any_active = false;
+            for (int k = 0; k < nrhs; ++k) {
+                if (ctx->h_cg[k].nonfinite) nonfinite = true;
+                if (ctx->h_cg[k].active) {
+                    any_active = true;
+                    if (ctx->h_cg[k].need_ru) any_ru = true;
+                }
+            }
+            if (nonfinite) break;
+            if (any_ru) {
+                if ((rc = reliable_update())) return rc;
+                HMC_CUDA(ctx, cudaMemcpyAsync(ctx->h_cg, cgs, nrhs * sizeof(CgScalars), cudaMemcpyDeviceToHost, sm));
+                HMC_CUDA(ctx, cudaStreamSynchronize(sm));
+                any_active = false;
+                for (int k = 0; k < nrhs; ++k) {
+                    if (ctx->h_cg[k].nonfinite) nonfinite = true;
+                    if (ctx->h_cg[k].active) any_active = true;
+                }
+                if (nonfinite) break;
+            }
+            if (!any_active) done = true;
+        }
+    }
+    if (!done && !nonfinite) {
+        // maxit reached: fold the partial solution in and measure the true residual
+        if ((rc = reliable_update())) return rc;
+        HMC_CUDA(ctx, cudaMemcpyAsync(ctx->h_cg, cgs, nrhs * sizeof(CgScalars), cudaMemcpyDeviceToHost, sm));
+        HMC_CUDA(ctx, cudaStreamSynchronize(sm));
+        done = true;
+        for (int k = 0; k < nrhs; ++k)
+            if (ctx->h_cg[k].active) done = false;
+    }
+    double worst = 0.0;
+    int iters = 0;
+    for (int k = 0; k < nrhs; ++k) {
+        const CgScalars& c = ctx->h_cg[k];
+        if (c.nonfinite) nonfinite = true;
+        const double rel = c.b2 > 0.0 ? std::sqrt(c.r2true / c.b2) : 0.0;
+        if (!(rel <= worst)) worst = rel;
+        if (c.iters > iters) iters = c.iters;
+    }
+    if (st) {
+        st->iterations = iters;
+        st->reliable_updates = n_ru;
+        st->converged = done && !nonfinite;
+        st->true_rel_resid = worst;
+    }
+    if (nonfinite) return fail(ctx, HMC_ERR_NONFINITE, "cg_solve: non-finite residual norm");
+    if (!done) return fail(ctx, HMC_ERR_NOCONV, "cg_solve: no convergence in " + std::to_string(maxit) + " iterations");
+    return HMC_OK;
+}
+
+int cg_run(hmc_ctx* ctx, int chain, const double* phi, const double2* b, double2* x, int nrhs,
+           double tol, int maxit, int precond, hmc_cg_stats* st) {
+    const Lat& lat = ctx->chains[chain].lat;
+    if (ctx->p.solver_mode == HMC_SOLVER_MIXED)
+        return run<float>(ctx, lat, phi, b, x, nrhs, tol, maxit, precond, st);
+    return run<double>(ctx, lat, phi, b, x, nrhs, tol, maxit, precond, st);
+}
+
+}  // namespace hmc

@@ -1,0 +1,497 @@
+// Mixed-radix Stockham FFT along one axis of a strided array, the twisted-Fourier
+// preconditioner P = F~ P-hat F~^* (Eqs. twist, Kdiag, precon), and the Fourier-diagonal
+// metric operations of Section "Online metric estimation".
+//
+// A block loads a tile of `nl` lines of length n into shared memory ([j][line] layout, so
+// threads working on consecutive lines touch consecutive words), runs every radix stage
+// there (Stockham autosort, ping-pong buffers) and writes the tile back. Twiddles come from
+// a per-length table e^{-2 pi i t / n} computed on the host in double precision.
+#include <cmath>
+
+#include "internal.h"
+
+namespace hmc {
+
+constexpr int kMaxStages = 16;
+
+struct StagePlan {
+    int n;
+    int nst;
+    int radix[kMaxStages];
+};
+
+template <typename C, int R>
+__device__ __forceinline__ void dft_small(C* v, const C* __restrict__ tw, int n, int dir) {
+    if constexpr (R == 2) {
+        C a = v[0], b = v[1];
+        v[0] = cadd(a, b); v[1] = csub(a, b);
+    } else if constexpr (R == 4) {
+        C a = v[0], b = v[1], c = v[2], d = v[3];
+        C s0 = cadd(a, c), s1 = csub(a, c), s2 = cadd(b, d), s3 = csub(b, d);
+        // multiply s3 by (dir * i): forward (dir = -1) -> -i
+        C s3r; s3r.x = -dir * s3.y; s3r.y = dir * s3.x;
+        v[0] = cadd(s0, s2); v[2] = csub(s0, s2);
+        v[1] = cadd(s1, s3r); v[3] = csub(s1, s3r);
+    } else {
+        C out[R];
+        const int step = n / R;
+#pragma unroll
+        for (int p = 0; p < R; ++p) {
+            C acc = v[0];
+#pragma unroll
+            for (int q = 1; q < R; ++q) {
+                C w = __ldg(tw + ((p * q) % R) * step);
+                if (dir > 0) w.y = -w.y;
+                acc = cadd(acc, cmul(v[q], w));
+            }
+            out[p] = acc;
+        }
+#pragma unroll
+        for (int p = 0; p < R; ++p) v[p] = out[p];
+    }
+}
+
+// One Stockham stage for all lines of the tile: src/dst are [n][nl].
+template <typename C, int R>
+__device__ __forceinline__ void stage(const C* src, C* dst, int n, int nl, int Ns,
+                                      const C* __restrict__ tw, int dir) {
+    const int M = n / R;
+    const int total = M * nl;
+    const int tstep = n / (Ns * R);
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int line = idx % nl, j = idx / nl;
+        const int k = j % Ns;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            C a = src[(j + r * M) * nl + line];
+            if (r > 0 && k > 0) {
+                C w = __ldg(tw + ((r * k * tstep) % n));
+                if (dir > 0) w.y = -w.y;
+                a = cmul(a, w);
+            }
+            v[r] = a;
+        }
+        dft_small<C, R>(v, tw, n, dir);
+        const int d = (j / Ns) * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[(d + r * Ns) * nl + line] = v[r];
+    }
+}
+
+// Runs all stages; returns the buffer holding the result.
+template <typename C>
+__device__ C* run_stages(C* a, C* b, const StagePlan& sp, int nl, const C* __restrict__ tw, int dir) {
+    int Ns = 1;
+    for (int s = 0; s < sp.nst; ++s) {
+        const int R = sp.radix[s];
+        switch (R) {
+            case 2: stage<C, 2>(a, b, sp.n, nl, Ns, tw, dir); break;
+            case 3: stage<C, 3>(a, b, sp.n, nl, Ns, tw, dir); break;
+            case 4: stage<C, 4>(a, b, sp.n, nl, Ns, tw, dir); break;
+            case 5: stage<C, 5>(a, b, sp.n, nl, Ns, tw, dir); break;
+            default: stage<C, 7>(a, b, sp.n, nl, Ns, tw, dir); break;
+        }
+        __syncthreads();
+        C* t = a; a = b; b = t;
+        Ns *= R;
+    }
+    return a;
+}
+
+// Tile geometry: lines are (o, i) with o in [o0, o0 + OB) and i in [i0, i0 + IC).
+struct FftTile {
+    int64_t outer, inner;
+    int OB, IC;
+    int64_t nib;   // number of inner blocks
+};
+
+template <typename C>
+__device__ __forceinline__ void tile_origin(const FftTile& ft, int64_t& o0, int64_t& i0) {
+    o0 = (blockIdx.x / ft.nib) * ft.OB;
+    i0 = (blockIdx.x % ft.nib) * ft.IC;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_fft(cplx<R>* __restrict__ data, FftTile ft, StagePlan sp,
+                                             const cplx<R>* __restrict__ tw, int dir, R scale) {
+    using C = cplx<R>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nl = ft.OB * ft.IC, n = sp.n;
+    C* a = reinterpret_cast<C*>(smem_raw);
+    C* b = a + (int64_t)n * nl;
+    int64_t o0, i0;
+    tile_origin<C>(ft, o0, i0);
+    const int tot = n * nl;
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        const int ic = e % ft.IC, rest = e / ft.IC;
+        const int j = rest % n, ob = rest / n;
+        const int64_t o = o0 + ob, i = i0 + ic;
+        if (o < ft.outer && i < ft.inner) a[j * nl + ob * ft.IC + ic] = data[(o * n + j) * ft.inner + i];
+    }
+    __syncthreads();
+    C* res = run_stages<C>(a, b, sp, nl, tw, dir);
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        const int ic = e % ft.IC, rest = e / ft.IC;
+        const int j = rest % n, ob = rest / n;
+        const int64_t o = o0 + ob, i = i0 + ic;
+        if (o < ft.outer && i < ft.inner) data[(o * n + j) * ft.inner + i] = cscale(res[j * nl + ob * ft.IC + ic], scale);
+    }
+}
+
+// Preconditioner pass along tau on data [nrhs][Nt][L*L*4] already Fourier transformed in
+// x and y: multiply by the twist conj(T) = e^{-i pi t / Nt}, forward FFT over t, multiply by
+// P-hat = 1 / |K-hat|^2 with K-hat = e^{i w_n} - 1 - dtau (mu_a + 2 t_h cos kx + 2 t_v cos ky),
+// w_n = (2n + 1) pi / Nt, inverse FFT, multiply by T. Inner index i = (m_y * L + m_x) * 4 + c.
+struct PrecondCoef {
+    double dtau, mu[2], th[2], tv[2];
+    int L, Nt;
+    const double* cosk;    // cos(2 pi m / L), m < L
+    const double2* eitw;   // (cos w_n, sin w_n), n < Nt
+    const double2* twist;  // e^{i pi t / Nt}, t < Nt
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_precond_tau(cplx<R>* __restrict__ data, FftTile ft,
+                                                     StagePlan sp, const cplx<R>* __restrict__ tw,
+                                                     PrecondCoef pc, R scale2) {
+    using C = cplx<R>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nl = ft.OB * ft.IC, n = sp.n;
+    C* a = reinterpret_cast<C*>(smem_raw);
+    C* b = a + (int64_t)n * nl;
+    int64_t o0, i0;
+    tile_origin<C>(ft, o0, i0);
+    const int tot = n * nl;
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        const int ic = e % ft.IC, rest = e / ft.IC;
+        const int j = rest % n, ob = rest / n;
+        const int64_t o = o0 + ob, i = i0 + ic;
+        C v = mk<C>(0.0, 0.0);
+        if (o < ft.outer && i < ft.inner) {
+            v = data[(o * n + j) * ft.inner + i];
+            const double2 w = pc.twist[j];
+            C wc = mk<C>(w.x, -w.y);
+            v = cmul(v, wc);
+        }
+        a[j * nl + ob * ft.IC + ic] = v;
+    }
+    __syncthreads();
+    C* res = run_stages<C>(a, b, sp, nl, tw, -1);
+    C* other = (res == a) ? b : a;
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        const int line = e % nl, j = e / nl;
+        const int ic = line % ft.IC;
+        const int64_t i = i0 + ic;
+        if (i < ft.inner) {
+            const int c = (int)(i & 3);
+            const int alpha = c >> 1;
+            const int64_t kk = i >> 2;
+            const int mx = (int)(kk % pc.L), my = (int)(kk / pc.L);
+            const double eps = 2.0 * pc.th[alpha] * pc.cosk[mx] + 2.0 * pc.tv[alpha] * pc.cosk[my];
+            const double2 ew = pc.eitw[j];
+            const double re = ew.x - 1.0 - pc.dtau * (pc.mu[alpha] + eps);
+            const double im = ew.y;
+            const R ph = (R)(1.0 / (re * re + im * im));
+            res[j * nl + line] = cscale(res[j * nl + line], ph);
+        }
+    }
+    __syncthreads();
+    C* res2 = run_stages<C>(res, other, sp, nl, tw, +1);
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        const int ic = e % ft.IC, rest = e / ft.IC;
+        const int j = rest % n, ob = rest / n;
+        const int64_t o = o0 + ob, i = i0 + ic;
+        if (o < ft.outer && i < ft.inner) {
+            const double2 w = pc.twist[j];
+            C v = cmul(res2[j * nl + ob * ft.IC + ic], mk<C>(w.x, w.y));
+            data[(o * n + j) * ft.inner + i] = cscale(v, scale2);
+        }
+    }
+}
+
+// ---- host side ----------------------------------------------------------------------------
+static std::vector<int> factorize(int n) {
+    std::vector<int> f;
+    while (n % 4 == 0) { f.push_back(4); n /= 4; }
+    while (n % 2 == 0) { f.push_back(2); n /= 2; }
+    for (int r : {3, 5, 7})
+        while (n % r == 0) { f.push_back(r); n /= r; }
+    if (n != 1) f.clear();
+    return f;
+}
+
+FftPlan* get_plan(hmc_ctx* ctx, int n) {
+    for (auto& p : ctx->plans)
+        if (p.n == n) return &p;
+    return nullptr;
+}
+
+static int add_plan(hmc_ctx* ctx, int n) {
+    if (get_plan(ctx, n)) return HMC_OK;
+    FftPlan p;
+    p.n = n;
+    p.radix = factorize(n);
+    if (p.radix.empty() || (int)p.radix.size() > kMaxStages)
+        return fail(ctx, HMC_ERR_ARG, "FFT length " + std::to_string(n) + " must factor into 2, 3, 5, 7");
+    std::vector<double2> t64(n);
+    std::vector<float2> t32(n);
+    for (int k = 0; k < n; ++k) {
+        const double ang = -2.0 * M_PI * (double)k / (double)n;
+        t64[k] = make_double2(std::cos(ang), std::sin(ang));
+        t32[k] = make_float2((float)t64[k].x, (float)t64[k].y);
+    }
+    HMC_CUDA(ctx, cudaMalloc(&p.tw64, n * sizeof(double2)));
+    HMC_CUDA(ctx, cudaMalloc(&p.tw32, n * sizeof(float2)));
+    HMC_CUDA(ctx, cudaMemcpy(p.tw64, t64.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
+    HMC_CUDA(ctx, cudaMemcpy(p.tw32, t32.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+    ctx->plans.push_back(p);
+    return HMC_OK;
+}
+
+static PcTables* get_pc(hmc_ctx* ctx, int L, int Nt) {
+    for (auto& t : ctx->pcs)
+        if (t.L == L && t.Nt == Nt) return &t;
+    return nullptr;
+}
+
+// Per-lattice preconditioner tables: cos k (L), e^{i w_n} (Nt), twist e^{i pi t / Nt} (Nt).
+static int add_pc(hmc_ctx* ctx, int L, int Nt) {
+    if (get_pc(ctx, L, Nt)) return HMC_OK;
+    PcTables t;
+    t.L = L;
+    t.Nt = Nt;
+    std::vector<double> ck(L);
+    std::vector<double2> ew(Nt), tw(Nt);
+    for (int m = 0; m < L; ++m) ck[m] = std::cos(2.0 * M_PI * m / L);
+    for (int n = 0; n < Nt; ++n) {
+        const double w = (2.0 * n + 1.0) * M_PI / Nt;
+        ew[n] = make_double2(std::cos(w), std::sin(w));
+        const double a = M_PI * n / Nt;
+        tw[n] = make_double2(std::cos(a), std::sin(a));
+    }
+    HMC_CUDA(ctx, cudaMalloc(&t.cosk, L * sizeof(double)));
+    HMC_CUDA(ctx, cudaMalloc(&t.eitw, Nt * sizeof(double2)));
+    HMC_CUDA(ctx, cudaMalloc(&t.twist, Nt * sizeof(double2)));
+    HMC_CUDA(ctx, cudaMemcpy(t.cosk, ck.data(), L * sizeof(double), cudaMemcpyHostToDevice));
+    HMC_CUDA(ctx, cudaMemcpy(t.eitw, ew.data(), Nt * sizeof(double2), cudaMemcpyHostToDevice));
+    HMC_CUDA(ctx, cudaMemcpy(t.twist, tw.data(), Nt * sizeof(double2), cudaMemcpyHostToDevice));
+    ctx->pcs.push_back(t);
+    return HMC_OK;
+}
+
+int build_plans(hmc_ctx* ctx) {
+    for (auto& ch : ctx->chains) {
+        int rc;
+        if ((rc = add_plan(ctx, ch.lat.L))) return rc;
+        if ((rc = add_plan(ctx, ch.lat.Nt))) return rc;
+        if ((rc = add_pc(ctx, ch.lat.L, ch.lat.Nt))) return rc;
+    }
+    return HMC_OK;
+}
+
+void free_plans(hmc_ctx* ctx) {
+    for (auto& p : ctx->plans) {
+        cudaFree(p.tw64);
+        cudaFree(p.tw32);
+    }
+    ctx->plans.clear();
+    for (auto& t : ctx->pcs) {
+        cudaFree(t.cosk);
+        cudaFree(t.eitw);
+        cudaFree(t.twist);
+    }
+    ctx->pcs.clear();
+}
+
+static StagePlan stage_plan(const FftPlan* p) {
+    StagePlan sp;
+    sp.n = p->n;
+    sp.nst = (int)p->radix.size();
+    for (int i = 0; i < sp.nst; ++i) sp.radix[i] = p->radix[i];
+    return sp;
+}
+
+template <typename R>
+static FftTile make_tile(int64_t outer, int n, int64_t inner) {
+    FftTile ft;
+    ft.outer = outer;
+    ft.inner = inner;
+    const int target = (sizeof(R) == 8 ? 2048 : 4096) / n;   // lines per tile
+    const int want = target < 1 ? 1 : target;
+    int cap = (int)(inner < 32 ? inner : 32);
+    if (cap > want) cap = want;
+    ft.IC = 1;
+    while (ft.IC * 2 <= cap) ft.IC *= 2;
+    if (inner < 32 && inner <= want) ft.IC = (int)inner;
+    int ob = want / ft.IC;
+    if (ob < 1) ob = 1;
+    if (ob > outer) ob = (int)outer;
+    ft.OB = ob;
+    ft.nib = (inner + ft.IC - 1) / ft.IC;
+    return ft;
+}
+
+template <typename R> static const cplx<R>* tw_of(const FftPlan* p);
+template <> const float2* tw_of<float>(const FftPlan* p) { return p->tw32; }
+template <> const double2* tw_of<double>(const FftPlan* p) { return p->tw64; }
+
+template <typename R>
+int fft_axis(hmc_ctx* ctx, cplx<R>* data, int64_t outer, int n, int64_t inner, int dir) {
+    const FftPlan* p = get_plan(ctx, n);
+    if (!p) return fail(ctx, HMC_ERR_STATE, "no FFT plan for length " + std::to_string(n));
+    FftTile ft = make_tile<R>(outer, n, inner);
+    const size_t sm = 2 * (size_t)n * ft.OB * ft.IC * sizeof(cplx<R>);
+    static bool attr[2] = {false, false};
+    if (!attr[sizeof(R) == 8]) {
+        HMC_CUDA(ctx, cudaFuncSetAttribute(k_fft<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        attr[sizeof(R) == 8] = true;
+    }
+    const int64_t nblk = ((outer + ft.OB - 1) / ft.OB) * ft.nib;
+    k_fft<R><<<(unsigned)nblk, 256, sm, ctx->stream>>>(data, ft, stage_plan(p), tw_of<R>(p), dir,
+                                                      (R)(1.0 / std::sqrt((double)n)));
+    HMC_LAUNCH(ctx, "k_fft");
+    return HMC_OK;
+}
+template int fft_axis<float>(hmc_ctx*, float2*, int64_t, int, int64_t, int);
+template int fft_axis<double>(hmc_ctx*, double2*, int64_t, int, int64_t, int);
+
+// y = P x: copy to y, x and y FFTs forward, the fused tau pass, x and y FFTs inverse.
+template <typename R>
+int launch_precond(hmc_ctx* ctx, const Lat& lat, const cplx<R>* x, cplx<R>* y, int nrhs) {
+    const int L = lat.L, Nt = lat.Nt;
+    const int64_t n4 = 4 * lat.V * (int64_t)nrhs;
+    if (x != y) HMC_CUDA(ctx, cudaMemcpyAsync(y, x, n4 * sizeof(cplx<R>), cudaMemcpyDeviceToDevice, ctx->stream));
+    int rc;
+    // forward along x then y (unitary)
+    if ((rc = fft_axis<R>(ctx, y, (int64_t)nrhs * Nt * L, L, 4, -1))) return rc;
+    if ((rc = fft_axis<R>(ctx, y, (int64_t)nrhs * Nt, L, 4 * (int64_t)L, -1))) return rc;
+    // tau pass
+    const FftPlan* p = get_plan(ctx, Nt);
+    PcTables* pt = get_pc(ctx, L, Nt);
+    if (!p || !pt) return fail(ctx, HMC_ERR_STATE, "no preconditioner plan for this lattice");
+    PrecondCoef pc;
+    pc.dtau = ctx->p.dtau;
+    for (int a = 0; a < 2; ++a) {
+        pc.mu[a] = ctx->p.mu[a];
+        pc.th[a] = ctx->p.t_h[a];
+        pc.tv[a] = ctx->p.t_v[a];
+    }
+    pc.L = L;
+    pc.Nt = Nt;
+    pc.cosk = pt->cosk;
+    pc.eitw = pt->eitw;
+    pc.twist = pt->twist;
+    FftTile ft = make_tile<R>(nrhs, Nt, 4 * (int64_t)L * L);
+    const size_t sm = 2 * (size_t)Nt * ft.OB * ft.IC * sizeof(cplx<R>);
+    static bool attr[2] = {false, false};
+    if (!attr[sizeof(R) == 8]) {
+        HMC_CUDA(ctx, cudaFuncSetAttribute(k_precond_tau<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        attr[sizeof(R) == 8] = true;
+    }
+    const int64_t nblk = ((ft.outer + ft.OB - 1) / ft.OB) * ft.nib;
+    k_precond_tau<R><<<(unsigned)nblk, 256, sm, ctx->stream>>>(y, ft, stage_plan(p), tw_of<R>(p), pc,
+                                                              (R)(1.0 / (double)Nt));
+    HMC_LAUNCH(ctx, "k_precond_tau");
+    // inverse along y then x
+    if ((rc = fft_axis<R>(ctx, y, (int64_t)nrhs * Nt, L, 4 * (int64_t)L, +1))) return rc;
+    if ((rc = fft_axis<R>(ctx, y, (int64_t)nrhs * Nt * L, L, 4, +1))) return rc;
+    return HMC_OK;
+}
+template int launch_precond<float>(hmc_ctx*, const Lat&, const float2*, float2*, int);
+template int launch_precond<double>(hmc_ctx*, const Lat&, const double2*, double2*, int);
+
+// ---- metric -----------------------------------------------------------------------------
+__global__ void k_pack_real(const double* __restrict__ in, double2* __restrict__ out, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_double2(in[i], 0.0);
+}
+
+// mode 0: v *= sig; 1: v /= sqrt(sig); 2: partial sums of 0.5 sig |v|^2; 3: acc += |v|^2
+__global__ void __launch_bounds__(256) k_spectral(double2* __restrict__ v, const double* __restrict__ sig,
+                                                  int64_t n, int mode, double* __restrict__ acc,
+                                                  double* __restrict__ part) {
+    __shared__ double red[8];
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double e = 0.0;
+    if (i < n) {
+        double2 a = v[i];
+        if (mode == 0) {
+            const double s = sig[i];
+            v[i] = make_double2(a.x * s, a.y * s);
+        } else if (mode == 1) {
+            const double s = 1.0 / sqrt(sig[i]);
+            v[i] = make_double2(a.x * s, a.y * s);
+        } else if (mode == 2) {
+            e = 0.5 * sig[i] * (a.x * a.x + a.y * a.y);
+        } else {
+            acc[i] += a.x * a.x + a.y * a.y;
+        }
+    }
+    if (mode == 2) {
+        const double t = block_sum(e, red);
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
+    }
+}
+
+// out = Re(v) (eps == 0) or out += eps Re(v)
+__global__ void k_unpack_real(const double2* __restrict__ v, double* __restrict__ out, int64_t n, double eps) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = eps == 0.0 ? v[i].x : out[i] + eps * v[i].x;
+}
+
+static int fft3_real_field(hmc_ctx* ctx, const Lat& lat, double2* v, int dir) {
+    const int L = lat.L, Nt = lat.Nt;
+    int rc;
+    if ((rc = fft_axis<double>(ctx, v, 3 * (int64_t)Nt * L, L, 1, dir))) return rc;
+    if ((rc = fft_axis<double>(ctx, v, 3 * (int64_t)Nt, L, L, dir))) return rc;
+    if ((rc = fft_axis<double>(ctx, v, 3, Nt, (int64_t)L * L, dir))) return rc;
+    return HMC_OK;
+}
+
+int metric_op(hmc_ctx* ctx, const Lat& lat, int op, const double* sig, const double* in,
+              double* out, double eps, double* scalar_dev) {
+    const int64_t n = 3 * lat.V;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    double2* v = ctx->d_fft;
+    k_pack_real<<<nb, 256, 0, ctx->stream>>>(in, v, n);
+    HMC_LAUNCH(ctx, "k_pack_real");
+    int rc;
+    if ((rc = fft3_real_field(ctx, lat, v, -1))) return rc;
+    if (op == HMC_METRIC_KINETIC) {
+        if (nb > ctx->part_cap) return fail(ctx, HMC_ERR_ARG, "metric: reduction buffer too small");
+        k_spectral<<<nb, 256, 0, ctx->stream>>>(v, sig, n, 2, nullptr, ctx->d_part);
+        HMC_LAUNCH(ctx, "k_spectral");
+        return reduce_rows(ctx, ctx->d_part, 1, (int)nb, scalar_dev);
+    }
+    if (op == HMC_METRIC_ACCUM) {
+        k_spectral<<<nb, 256, 0, ctx->stream>>>(v, sig, n, 3, out, nullptr);
+        HMC_LAUNCH(ctx, "k_spectral");
+        return HMC_OK;
+    }
+    k_spectral<<<nb, 256, 0, ctx->stream>>>(v, sig, n, op == HMC_METRIC_MOMENTUM ? 1 : 0, nullptr, nullptr);
+    HMC_LAUNCH(ctx, "k_spectral");
+    if ((rc = fft3_real_field(ctx, lat, v, +1))) return rc;
+    k_unpack_real<<<nb, 256, 0, ctx->stream>>>(v, out, n, eps);
+    HMC_LAUNCH(ctx, "k_unpack_real");
+    return HMC_OK;
+}
+
+// ---- deterministic reductions ----------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_reduce_rows(const double* __restrict__ part, int nblk,
+                                                     double* __restrict__ out) {
+    __shared__ double red[8];
+    const double* row = part + (int64_t)blockIdx.x * nblk;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += row[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+int reduce_rows(hmc_ctx* ctx, const double* part, int k, int nblk, double* out) {
+    k_reduce_rows<<<k, 256, 0, ctx->stream>>>(part, nblk, out);
+    HMC_LAUNCH(ctx, "k_reduce_rows");
+    return HMC_OK;
+}
+
+}  // namespace hmc

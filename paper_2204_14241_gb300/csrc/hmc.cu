@@ -1,0 +1,525 @@
+// Context management, the C ABI of include/hmc.h, the HMC trajectory (Section "HMC":
+// heatbath, momentum draw, leapfrog, Metropolis) and the Philox4x32-10 generator.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+namespace hmc {
+
+static thread_local std::string g_err;
+
+int fail(hmc_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    g_err = msg;
+    return code;
+}
+
+int cuda_check(hmc_ctx* ctx, cudaError_t e, const char* what) {
+    return fail(ctx, HMC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) ---------------------------------------
+struct U4 { uint32_t v[4]; };
+
+__host__ __device__ __forceinline__ void mulhilo(uint32_t a, uint32_t b, uint32_t& hi, uint32_t& lo) {
+    const uint64_t p = (uint64_t)a * (uint64_t)b;
+    hi = (uint32_t)(p >> 32);
+    lo = (uint32_t)p;
+}
+
+__host__ __device__ __forceinline__ U4 philox(U4 c, uint32_t k0, uint32_t k1) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round) { k0 += W0; k1 += W1; }
+        uint32_t hi0, lo0, hi1, lo1;
+        mulhilo(M0, c.v[0], hi0, lo0);
+        mulhilo(M1, c.v[2], hi1, lo1);
+        U4 n;
+        n.v[0] = hi1 ^ c.v[1] ^ k0;
+        n.v[1] = lo1;
+        n.v[2] = hi0 ^ c.v[3] ^ k1;
+        n.v[3] = lo0;
+        c = n;
+    }
+    return c;
+}
+
+__global__ void k_philox_raw(uint64_t key, U4 ctr, int64_t nblocks, uint32_t* __restrict__ out) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= nblocks) return;
+    // 128-bit counter + j
+    U4 c = ctr;
+    uint64_t lo = ((uint64_t)c.v[1] << 32 | c.v[0]);
+    const uint64_t nlo = lo + (uint64_t)j;
+    uint64_t hi = ((uint64_t)c.v[3] << 32 | c.v[2]) + (nlo < lo ? 1u : 0u);
+    c.v[0] = (uint32_t)nlo; c.v[1] = (uint32_t)(nlo >> 32);
+    c.v[2] = (uint32_t)hi; c.v[3] = (uint32_t)(hi >> 32);
+    const U4 r = philox(c, (uint32_t)key, (uint32_t)(key >> 32));
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[4 * j + q] = r.v[q];
+}
+
+// two uniforms in (0, 1] from one Philox block (53 bits each)
+__device__ __forceinline__ void uniforms(uint64_t seed, uint64_t counter, uint64_t j, double& u1, double& u2) {
+    U4 c;
+    c.v[0] = (uint32_t)j; c.v[1] = (uint32_t)(j >> 32);
+    c.v[2] = (uint32_t)counter; c.v[3] = (uint32_t)(counter >> 32);
+    const U4 r = philox(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint64_t a = ((uint64_t)r.v[0] << 21) ^ (uint64_t)(r.v[1] >> 11);
+    const uint64_t b = ((uint64_t)r.v[2] << 21) ^ (uint64_t)(r.v[3] >> 11);
+    const double s = 1.0 / 9007199254740992.0;   // 2^-53
+    u1 = ((double)(a & ((1ull << 53) - 1)) + 1.0) * s;
+    u2 = ((double)(b & ((1ull << 53) - 1)) + 1.0) * s;
+}
+
+// n normals (complex_out = 0) or n complex normals with parts N(0, 1/2); Box-Muller per block.
+__global__ void k_philox_normal(uint64_t seed, uint64_t counter, uint64_t jbase, int64_t n,
+                                int complex_out, double* __restrict__ out) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nreal = complex_out ? 2 * n : n;
+    if (2 * j >= nreal) return;
+    double u1, u2;
+    uniforms(seed, counter, jbase + (uint64_t)j, u1, u2);
+    const double rad = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    const double scale = complex_out ? sqrt(0.5) : 1.0;
+    out[2 * j] = scale * rad * c;
+    if (2 * j + 1 < nreal) out[2 * j + 1] = scale * rad * s;
+}
+
+__global__ void k_philox_uniform(uint64_t seed, uint64_t counter, uint64_t jbase, double* out) {
+    double u1, u2;
+    uniforms(seed, counter, jbase, u1, u2);
+    out[0] = 1.0 - u1;   // [0, 1)
+}
+
+// ---- small vector kernels ------------------------------------------------------------------
+__global__ void k_axpy(double a, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] += a * x[i];
+}
+
+__global__ void __launch_bounds__(256) k_norm2(const double* __restrict__ a, int64_t n, double* __restrict__ part) {
+    __shared__ double red[8];
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += a[i] * a[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+}  // namespace hmc
+
+using namespace hmc;
+
+// ---- helpers ------------------------------------------------------------------------------------
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+static int check_chain(hmc_ctx* ctx, int chain) {
+    if (!ctx) return fail(nullptr, HMC_ERR_ARG, "null context");
+    if (chain < 0 || chain >= (int)ctx->chains.size()) return fail(ctx, HMC_ERR_ARG, "chain index out of range");
+    return HMC_OK;
+}
+
+static int check_ptrs(hmc_ctx* ctx, std::initializer_list<const void*> ps) {
+    for (const void* p : ps) {
+        if (!p) return fail(ctx, HMC_ERR_ARG, "null pointer argument");
+        if (!aligned16(p)) return fail(ctx, HMC_ERR_ARG, "pointer not 16-byte aligned");
+    }
+    return HMC_OK;
+}
+
+static int check_nrhs(hmc_ctx* ctx, int nrhs) {
+    if (nrhs < 1 || nrhs > ctx->kmax) return fail(ctx, HMC_ERR_ARG, "nrhs must be in [1, nrhs_max]");
+    return HMC_OK;
+}
+
+template <typename T> static int dalloc(hmc_ctx* ctx, T** p, int64_t count) {
+    HMC_CUDA(ctx, cudaMalloc((void**)p, (size_t)count * sizeof(T)));
+    return HMC_OK;
+}
+
+static void free_all(hmc_ctx* ctx) {
+    void* ps[] = {ctx->d_r64, ctx->d_p64, ctx->d_q64, ctx->d_z64, ctx->d_X, ctx->d_pf, ctx->d_chi,
+                  ctx->d_x32, ctx->d_r32, ctx->d_p32, ctx->d_q32, ctx->d_z32, ctx->d_phi32,
+                  ctx->d_phi_save, ctx->d_pi, ctx->d_F, ctx->d_vel, ctx->d_z, ctx->d_fft,
+                  ctx->d_part, ctx->d_red, ctx->d_cg, ctx->d_u32};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    if (ctx->h_cg) cudaFreeHost(ctx->h_cg);
+    if (ctx->h_red) cudaFreeHost(ctx->h_red);
+    free_plans(ctx);
+}
+
+// synchronise and copy `count` reduced scalars d_red[0..count) to host
+static int fetch_red(hmc_ctx* ctx, int count, double* dst) {
+    HMC_CUDA(ctx, cudaMemcpyAsync(ctx->h_red, ctx->d_red, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    HMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < count; ++i) dst[i] = ctx->h_red[i];
+    return HMC_OK;
+}
+
+extern "C" {
+
+const char* hmc_last_error(const hmc_ctx* ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
+
+int hmc_counters(const hmc_ctx* ctx, int64_t* kernel_launches) {
+    if (!ctx || !kernel_launches) return fail(nullptr, HMC_ERR_ARG, "hmc_counters: null argument");
+    *kernel_launches = ctx->launches;
+    return HMC_OK;
+}
+
+int hmc_init(const hmc_params* p, int n_chains, const hmc_chain* chains, void* cuda_stream, hmc_ctx** out) {
+    if (!p || !out) return fail(nullptr, HMC_ERR_ARG, "hmc_init: null argument");
+    *out = nullptr;
+    if (n_chains < 1) return fail(nullptr, HMC_ERR_ARG, "hmc_init: n_chains must be >= 1");
+    if (p->nrhs_max < 1 || p->nrhs_max > 64) return fail(nullptr, HMC_ERR_ARG, "hmc_init: nrhs_max must be in [1, 64]");
+    if (p->solver_mode != HMC_SOLVER_FP64 && p->solver_mode != HMC_SOLVER_MIXED)
+        return fail(nullptr, HMC_ERR_ARG, "hmc_init: unknown solver_mode");
+    if (!(p->dtau > 0.0) || !(p->c > 0.0)) return fail(nullptr, HMC_ERR_ARG, "hmc_init: dtau and c must be positive");
+    hmc_ctx* ctx = new (std::nothrow) hmc_ctx();
+    if (!ctx) return fail(nullptr, HMC_ERR_ARG, "hmc_init: out of host memory");
+    ctx->p = *p;
+    if (ctx->p.cg_tol <= 0.0) ctx->p.cg_tol = 1e-10;
+    if (ctx->p.cg_maxit <= 0) ctx->p.cg_maxit = 100000;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->kmax = p->nrhs_max;
+    for (int c = 0; c < n_chains; ++c) {
+        const int L = chains ? chains[c].L : p->L;
+        const int Nt = chains ? chains[c].Nt : p->Nt;
+        const double r = chains ? chains[c].r : p->r;
+        if (L < 2 || (L & 1) || L > 4096 || Nt < 2 || Nt > 65536) {
+            delete ctx;
+            return fail(nullptr, HMC_ERR_ARG, "hmc_init: need even L in [2, 4096] and Nt in [2, 65536]");
+        }
+        ChainDesc d;
+        d.lat.L = L;
+        d.lat.Nt = Nt;
+        d.lat.V = (int64_t)Nt * L * L;
+        d.r = r;
+        ctx->chains.push_back(d);
+        if (d.lat.V > ctx->vmax) ctx->vmax = d.lat.V;
+    }
+    int dev = 0;
+    int rc = HMC_OK;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        rc = cuda_check(nullptr, e, "hmc_init: device query");
+        delete ctx;
+        return rc;
+    }
+    const int64_t nf = (int64_t)ctx->kmax * 4 * ctx->vmax;   // complex entries per workspace vector
+    const int64_t nb = 3 * ctx->vmax;
+    ctx->part_cap = 4 * (int64_t)ctx->kmax * 512;
+    const int64_t need_a = (int64_t)ctx->kmax * (ctx->vmax / 16 + 1024);
+    const int64_t need_m = 3 * ctx->vmax / 256 + 1024;
+    if (need_a > ctx->part_cap) ctx->part_cap = need_a;
+    if (need_m > ctx->part_cap) ctx->part_cap = need_m;
+    const bool mixed = p->solver_mode == HMC_SOLVER_MIXED;
+    if ((rc = dalloc(ctx, &ctx->d_r64, nf)) || (rc = dalloc(ctx, &ctx->d_p64, mixed ? 1 : nf)) ||
+        (rc = dalloc(ctx, &ctx->d_q64, nf)) || (rc = dalloc(ctx, &ctx->d_z64, mixed ? 1 : nf)) ||
+        (rc = dalloc(ctx, &ctx->d_X, nf)) || (rc = dalloc(ctx, &ctx->d_pf, nf)) ||
+        (rc = dalloc(ctx, &ctx->d_chi, nf)) || (rc = dalloc(ctx, &ctx->d_x32, mixed ? nf : 1)) ||
+        (rc = dalloc(ctx, &ctx->d_r32, mixed ? nf : 1)) || (rc = dalloc(ctx, &ctx->d_p32, mixed ? nf : 1)) ||
+        (rc = dalloc(ctx, &ctx->d_q32, mixed ? nf : 1)) || (rc = dalloc(ctx, &ctx->d_z32, mixed ? nf : 1)) ||
+        (rc = dalloc(ctx, &ctx->d_phi32, nb)) || (rc = dalloc(ctx, &ctx->d_phi_save, nb)) ||
+        (rc = dalloc(ctx, &ctx->d_pi, nb)) || (rc = dalloc(ctx, &ctx->d_F, nb)) || (rc = dalloc(ctx, &ctx->d_vel, nb)) ||
+        (rc = dalloc(ctx, &ctx->d_z, nb)) || (rc = dalloc(ctx, &ctx->d_fft, nb)) ||
+        (rc = dalloc(ctx, &ctx->d_part, ctx->part_cap)) || (rc = dalloc(ctx, &ctx->d_red, 64)) ||
+        (rc = dalloc(ctx, &ctx->d_cg, ctx->kmax)) || (rc = dalloc(ctx, &ctx->d_u32, 4))) {
+        std::string m = ctx->err;
+        free_all(ctx);
+        delete ctx;
+        return fail(nullptr, rc, m);
+    }
+    e = cudaMallocHost((void**)&ctx->h_cg, ctx->kmax * sizeof(CgScalars));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_red, 64 * sizeof(double));
+    if (e != cudaSuccess) {
+        rc = cuda_check(nullptr, e, "hmc_init: pinned host buffers");
+        free_all(ctx);
+        delete ctx;
+        return rc;
+    }
+    if ((rc = build_plans(ctx))) {
+        std::string m = ctx->err;
+        free_all(ctx);
+        delete ctx;
+        return fail(nullptr, rc, m);
+    }
+    *out = ctx;
+    return HMC_OK;
+}
+
+int hmc_destroy(hmc_ctx* ctx) {
+    if (!ctx) return HMC_OK;
+    cudaStreamSynchronize(ctx->stream);
+    free_all(ctx);
+    delete ctx;
+    return HMC_OK;
+}
+
+int apply_M(hmc_ctx* ctx, int chain, int prec, const void* phi, const void* x, void* y, int dagger, int nrhs) {
+    int rc;
+    if ((rc = check_chain(ctx, chain)) || (rc = check_nrhs(ctx, nrhs)) || (rc = check_ptrs(ctx, {phi, x, y}))) return rc;
+    if (x == y) return fail(ctx, HMC_ERR_ARG, "apply_M: x and y must not overlap");
+    const Lat& lat = ctx->chains[chain].lat;
+    if (prec == HMC_FP64)
+        return launch_apply_D<double>(ctx, lat, (const double*)phi, (const double2*)x, (double2*)y, dagger, nrhs);
+    if (prec == HMC_FP32)
+        return launch_apply_D<float>(ctx, lat, (const float*)phi, (const float2*)x, (float2*)y, dagger, nrhs);
+    return fail(ctx, HMC_ERR_ARG, "apply_M: unknown precision");
+}
+
+int apply_MdagM(hmc_ctx* ctx, int chain, int prec, const void* phi, const void* x, void* y, int nrhs, double* norm2) {
+    int rc;
+    if ((rc = check_chain(ctx, chain)) || (rc = check_nrhs(ctx, nrhs)) || (rc = check_ptrs(ctx, {phi, x, y}))) return rc;
+    if (x == y) return fail(ctx, HMC_ERR_ARG, "apply_MdagM: x and y must not overlap");
+    const Lat& lat = ctx->chains[chain].lat;
+    double* part = norm2 ? ctx->d_part : nullptr;
+    int nb = 0;
+    if (prec == HMC_FP64) rc = launch_apply_A<double>(ctx, lat, (const double*)phi, (const double2*)x, (double2*)y, nrhs, part, &nb);
+    else if (prec == HMC_FP32) rc = launch_apply_A<float>(ctx, lat, (const float*)phi, (const float2*)x, (float2*)y, nrhs, part, &nb);
+    else return fail(ctx, HMC_ERR_ARG, "apply_MdagM: unknown precision");
+    if (rc || !norm2) return rc;
+    if ((rc = reduce_rows(ctx, part, nrhs, nb, ctx->d_red))) return rc;
+    return fetch_red(ctx, nrhs, norm2);
+}
+
+int apply_precond(hmc_ctx* ctx, int chain, int prec, const void* x, void* y, int nrhs) {
+    int rc;
+    if ((rc = check_chain(ctx, chain)) || (rc = check_nrhs(ctx, nrhs)) || (rc = check_ptrs(ctx, {x, y}))) return rc;
+    const Lat& lat = ctx->chains[chain].lat;
+    if (prec == HMC_FP64) return launch_precond<double>(ctx, lat, (const double2*)x, (double2*)y, nrhs);
+    if (prec == HMC_FP32) return launch_precond<float>(ctx, lat, (const float2*)x, (float2*)y, nrhs);
+    return fail(ctx, HMC_ERR_ARG, "apply_precond: unknown precision");
+}
+
+int cg_solve(hmc_ctx* ctx, int chain, const void* phi, const void* b, void* x, int nrhs, double tol, int maxit,
+             int precond, hmc_cg_stats* st) {
+    int rc;
+    if ((rc = check_chain(ctx, chain)) || (rc = check_nrhs(ctx, nrhs)) || (rc = check_ptrs(ctx, {phi, b, x}))) return rc;
+    if (b == x) return fail(ctx, HMC_ERR_ARG, "cg_solve: b and x must not overlap");
+    if (tol <= 0.0) tol = ctx->p.cg_tol;
+    if (maxit <= 0) maxit = ctx->p.cg_maxit;
+    return cg_run(ctx, chain, (const double*)phi, (const double2*)b, (double2*)x, nrhs, tol, maxit, precond ? 1 : 0, st);
+}
+
+}  // extern "C"
+
+// F, S_pf and S_b at phi for the pseudofermions pf; X receives A^{-1} pf.
+static int force_impl(hmc_ctx* ctx, int chain, const double* phi, const double2* pf, int nrhs, double* F,
+                      int include_boson, int precond, double* s_pf, double* s_b, hmc_cg_stats* st) {
+    const ChainDesc& ch = ctx->chains[chain];
+    int rc = cg_run(ctx, chain, phi, pf, ctx->d_X, nrhs, ctx->p.cg_tol, ctx->p.cg_maxit, precond, st);
+    if (rc) return rc;
+    int nb = 0;
+    if ((rc = launch_force(ctx, ch.lat, ch.r, phi, ctx->d_X, pf, nrhs, F, include_boson, ctx->d_part, &nb))) return rc;
+    if (!s_pf && !s_b) return HMC_OK;
+    if ((rc = reduce_rows(ctx, ctx->d_part, 2, nb, ctx->d_red))) return rc;
+    double v[2];
+    if ((rc = fetch_red(ctx, 2, v))) return rc;
+    if (s_pf) *s_pf = v[0];
+    if (s_b) *s_b = v[1];
+    return HMC_OK;
+}
+
+extern "C" int force(hmc_ctx* ctx, int chain, const void* phi, const void* phi_pf, int nrhs, void* F, double* S_pf,
+                     int include_boson, int precond, double* S_b, hmc_cg_stats* st) {
+    int rc;
+    if ((rc = check_chain(ctx, chain)) || (rc = check_nrhs(ctx, nrhs)) || (rc = check_ptrs(ctx, {phi, phi_pf, F}))) return rc;
+    double sb = 0.0;
+    rc = force_impl(ctx, chain, (const double*)phi, (const double2*)phi_pf, nrhs, (double*)F, include_boson,
+                    precond, S_pf, (S_b || include_boson) ? &sb : nullptr, st);
+    if (rc) return rc;
+    if (S_b) {
+        if (!include_boson) {
+            // S_B was not part of the force pass: evaluate it separately
+            int nb = 0;
+            const ChainDesc& ch = ctx->chains[chain];
+            if ((rc = launch_boson(ctx, ch.lat, ch.r, (const double*)phi, nullptr, ctx->d_part, &nb))) return rc;
+            if ((rc = reduce_rows(ctx, ctx->d_part, 1, nb, ctx->d_red))) return rc;
+            if ((rc = fetch_red(ctx, 1, &sb))) return rc;
+        }
+        *S_b = sb;
+    }
+    return HMC_OK;
+}
+
+extern "C" int metric_apply(hmc_ctx* ctx, int chain, int op, const void* sig, const void* in, void* out, double* scalar) {
+    int rc;
+    if ((rc = check_chain(ctx, chain)) || (rc = check_ptrs(ctx, {sig, in}))) return rc;
+    if (op < HMC_METRIC_MOMENTUM || op > HMC_METRIC_ACCUM) return fail(ctx, HMC_ERR_ARG, "metric_apply: unknown op");
+    if (op == HMC_METRIC_KINETIC) {
+        if (!scalar) return fail(ctx, HMC_ERR_ARG, "metric_apply: kinetic needs a scalar output");
+    } else if ((rc = check_ptrs(ctx, {out}))) {
+        return rc;
+    }
+    const Lat& lat = ctx->chains[chain].lat;
+    if ((rc = metric_op(ctx, lat, op, (const double*)sig, (const double*)in, (double*)out, 0.0, ctx->d_red))) return rc;
+    if (op == HMC_METRIC_KINETIC) return fetch_red(ctx, 1, scalar);
+    return HMC_OK;
+}
+
+extern "C" int philox_raw(hmc_ctx* ctx, uint64_t key, const uint32_t ctr[4], int64_t nblocks, void* out) {
+    if (!ctx || !ctr || !out || nblocks < 0) return fail(ctx, HMC_ERR_ARG, "philox_raw: bad argument");
+    if (nblocks == 0) return HMC_OK;
+    U4 c;
+    for (int q = 0; q < 4; ++q) c.v[q] = ctr[q];
+    k_philox_raw<<<(unsigned)((nblocks + 255) / 256), 256, 0, ctx->stream>>>(key, c, nblocks, (uint32_t*)out);
+    HMC_LAUNCH(ctx, "k_philox_raw");
+    return HMC_OK;
+}
+
+static int gen_normal(hmc_ctx* ctx, uint64_t seed, uint64_t counter, uint64_t jbase, int64_t n, int cplx, double* out) {
+    const int64_t nreal = cplx ? 2 * n : n;
+    const int64_t nblk = (nreal + 1) / 2;
+    if (nblk == 0) return HMC_OK;
+    k_philox_normal<<<(unsigned)((nblk + 255) / 256), 256, 0, ctx->stream>>>(seed, counter, jbase, n, cplx, out);
+    HMC_LAUNCH(ctx, "k_philox_normal");
+    return HMC_OK;
+}
+
+extern "C" int philox_normal(hmc_ctx* ctx, uint64_t seed, uint64_t counter, int64_t n, int complex_out, void* out) {
+    if (!ctx || n < 0) return fail(ctx, HMC_ERR_ARG, "philox_normal: bad argument");
+    int rc;
+    if ((rc = check_ptrs(ctx, {out}))) return rc;
+    return gen_normal(ctx, seed, counter, 0, n, complex_out ? 1 : 0, (double*)out);
+}
+
+// ---- trajectory ----------------------------------------------------------------------------------
+static int run_chain(hmc_ctx* ctx, int c, const hmc_traj_in* in, double out_e[6], double* dH, int* acc,
+                     int* iters, double* worst) {
+    const ChainDesc& ch = ctx->chains[c];
+    const Lat& lat = ch.lat;
+    const int64_t nb = 3 * lat.V;
+    const unsigned gb = (unsigned)((nb + 255) / 256);
+    const int K = in->nrhs;
+    double* phi = (double*)in->phi[c];
+    const double* sig = (const double*)in->sigma_hat[c];
+    cudaStream_t sm = ctx->stream;
+    int rc;
+    HMC_CUDA(ctx, cudaMemcpyAsync(ctx->d_phi_save, phi, nb * sizeof(double), cudaMemcpyDeviceToDevice, sm));
+
+    // noise
+    const double2* chi;
+    const double* z;
+    double u;
+    if (in->noise == HMC_NOISE_EXPLICIT) {
+        chi = (const double2*)in->chi[c];
+        z = (const double*)in->z[c];
+        u = in->u[c];
+    } else {
+        const uint64_t key = in->seed + 0x9E3779B97F4A7C15ull * (uint64_t)c;
+        if ((rc = gen_normal(ctx, key, in->counter, 0, (int64_t)K * 4 * lat.V, 1, (double*)ctx->d_chi))) return rc;
+        if ((rc = gen_normal(ctx, key, in->counter, 1ull << 48, nb, 0, ctx->d_z))) return rc;
+        k_philox_uniform<<<1, 1, 0, sm>>>(key, in->counter, 2ull << 48, ctx->d_red + 32);
+        HMC_LAUNCH(ctx, "k_philox_uniform");
+        HMC_CUDA(ctx, cudaMemcpyAsync(ctx->h_red + 32, ctx->d_red + 32, sizeof(double), cudaMemcpyDeviceToHost, sm));
+        HMC_CUDA(ctx, cudaStreamSynchronize(sm));
+        u = ctx->h_red[32];
+        chi = ctx->d_chi;
+        z = ctx->d_z;
+    }
+
+    // heatbath varphi = D chi, momentum, initial energies
+    if ((rc = launch_apply_D<double>(ctx, lat, phi, chi, ctx->d_pf, 0, K))) return rc;
+    if ((rc = metric_op(ctx, lat, HMC_METRIC_MOMENTUM, sig, z, ctx->d_pi, 0.0, nullptr))) return rc;
+    if ((rc = metric_op(ctx, lat, HMC_METRIC_KINETIC, sig, ctx->d_pi, nullptr, 0.0, ctx->d_red))) return rc;
+    int nbb = 0;
+    if ((rc = launch_boson(ctx, lat, ch.r, phi, nullptr, ctx->d_part, &nbb))) return rc;
+    if ((rc = reduce_rows(ctx, ctx->d_part, 1, nbb, ctx->d_red + 1))) return rc;
+    {
+        const unsigned g = 1024;
+        k_norm2<<<g, 256, 0, sm>>>((const double*)chi, (int64_t)K * 8 * lat.V, ctx->d_part);
+        HMC_LAUNCH(ctx, "k_norm2");
+        if ((rc = reduce_rows(ctx, ctx->d_part, 1, g, ctx->d_red + 2))) return rc;
+    }
+    double e0[3];
+    if ((rc = fetch_red(ctx, 3, e0))) return rc;
+
+    // leapfrog: kick eps/2, (drift eps, kick eps) x n, last kick eps/2
+    const double eps = in->eps;
+    int tot_it = 0;
+    double wr = 0.0, s_pf = 0.0, s_b = 0.0;
+    hmc_cg_stats st;
+    auto do_force = [&](bool want) -> int {
+        int r2 = force_impl(ctx, c, phi, ctx->d_pf, K, ctx->d_F, 1, in->precond, want ? &s_pf : nullptr,
+                            want ? &s_b : nullptr, &st);
+        tot_it += st.iterations;
+        if (st.true_rel_resid > wr) wr = st.true_rel_resid;
+        return r2;
+    };
+    rc = do_force(false);
+    if (!rc) {
+        k_axpy<<<gb, 256, 0, sm>>>(0.5 * eps, ctx->d_F, ctx->d_pi, nb);
+        HMC_LAUNCH(ctx, "k_axpy");
+        for (int i = 1; i <= in->n_leap && !rc; ++i) {
+            if ((rc = metric_op(ctx, lat, HMC_METRIC_VELOCITY, sig, ctx->d_pi, phi, eps, nullptr))) break;
+            if ((rc = do_force(i == in->n_leap))) break;
+            k_axpy<<<gb, 256, 0, sm>>>(i < in->n_leap ? eps : 0.5 * eps, ctx->d_F, ctx->d_pi, nb);
+            HMC_LAUNCH(ctx, "k_axpy");
+        }
+        if (in->n_leap == 0 && !rc) rc = do_force(true);
+    }
+    if (!rc) rc = metric_op(ctx, lat, HMC_METRIC_KINETIC, sig, ctx->d_pi, nullptr, 0.0, ctx->d_red);
+    double k1 = 0.0;
+    if (!rc) rc = fetch_red(ctx, 1, &k1);
+    *iters = tot_it;
+    *worst = wr;
+    if (rc) {
+        cudaMemcpyAsync(phi, ctx->d_phi_save, nb * sizeof(double), cudaMemcpyDeviceToDevice, sm);
+        cudaStreamSynchronize(sm);
+        return rc;
+    }
+    out_e[0] = e0[0]; out_e[1] = e0[1]; out_e[2] = e0[2];
+    out_e[3] = k1; out_e[4] = s_b; out_e[5] = s_pf;
+    const double h = (k1 + s_b + s_pf) - (e0[0] + e0[1] + e0[2]);
+    *dH = h;
+    if (!std::isfinite(h)) {
+        cudaMemcpyAsync(phi, ctx->d_phi_save, nb * sizeof(double), cudaMemcpyDeviceToDevice, sm);
+        cudaStreamSynchronize(sm);
+        *acc = 0;
+        return fail(ctx, HMC_ERR_NONFINITE, "trajectory: non-finite energy change");
+    }
+    *acc = u < std::exp(-h) ? 1 : 0;
+    if (!*acc) HMC_CUDA(ctx, cudaMemcpyAsync(phi, ctx->d_phi_save, nb * sizeof(double), cudaMemcpyDeviceToDevice, sm));
+    HMC_CUDA(ctx, cudaStreamSynchronize(sm));
+    return HMC_OK;
+}
+
+extern "C" int trajectory(hmc_ctx* ctx, const hmc_traj_in* in, hmc_traj_out* out) {
+    if (!ctx || !in) return fail(ctx, HMC_ERR_ARG, "trajectory: null argument");
+    int rc;
+    if ((rc = check_nrhs(ctx, in->nrhs))) return rc;
+    if (in->n_leap < 0 || !(in->eps >= 0.0)) return fail(ctx, HMC_ERR_ARG, "trajectory: bad eps or n_leap");
+    if (!in->phi || !in->sigma_hat) return fail(ctx, HMC_ERR_ARG, "trajectory: null phi or sigma_hat array");
+    if (in->noise != HMC_NOISE_EXPLICIT && in->noise != HMC_NOISE_PHILOX) return fail(ctx, HMC_ERR_ARG, "trajectory: unknown noise mode");
+    if (in->noise == HMC_NOISE_EXPLICIT && (!in->chi || !in->z || !in->u))
+        return fail(ctx, HMC_ERR_ARG, "trajectory: explicit noise needs chi, z and u");
+    const int nc = (int)ctx->chains.size();
+    for (int c = 0; c < nc; ++c) {
+        if ((rc = check_ptrs(ctx, {in->phi[c], in->sigma_hat[c]}))) return rc;
+        if (in->noise == HMC_NOISE_EXPLICIT && (rc = check_ptrs(ctx, {in->chi[c], in->z[c]}))) return rc;
+    }
+    int first_err = HMC_OK;
+    for (int c = 0; c < nc; ++c) {
+        double e[6] = {0, 0, 0, 0, 0, 0}, dh = 0.0, worst = 0.0;
+        int acc = 0, it = 0;
+        rc = run_chain(ctx, c, in, e, &dh, &acc, &it, &worst);
+        if (rc && !first_err) first_err = rc;
+        if (out) {
+            if (out->dH) out->dH[c] = dh;
+            if (out->accepted) out->accepted[c] = acc;
+            if (out->energies) for (int q = 0; q < 6; ++q) out->energies[6 * c + q] = e[q];
+            if (out->cg_iterations) out->cg_iterations[c] = it;
+            if (out->max_true_resid) out->max_true_resid[c] = worst;
+        }
+    }
+    return first_err;
+}

@@ -1,0 +1,154 @@
+// Host-side context and cross-file kernel launchers of libhmc.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace hmc {
+
+struct FftPlan {
+    int n = 0;
+    std::vector<int> radix;      // factors, applied in order
+    double2* tw64 = nullptr;     // e^{-2 pi i k / n}, k < n (device)
+    float2* tw32 = nullptr;
+};
+
+struct PcTables {
+    int L = 0, Nt = 0;
+    double* cosk = nullptr;     // cos(2 pi m / L)
+    double2* eitw = nullptr;    // e^{i w_n}, w_n = (2n + 1) pi / Nt
+    double2* twist = nullptr;   // e^{i pi t / Nt}
+};
+
+struct ChainDesc {
+    Lat lat;
+    double r;
+};
+
+// Per-RHS solver scalars, device resident (kernels read alpha/beta from here).
+struct CgScalars {
+    double rr;        // <r, z> (or <r, r> without preconditioner) of the current iterate
+    double rr_new;
+    double pAp;
+    double alpha;
+    double beta;
+    double r2;        // <r, r> (stopping test)
+    double r2_max;    // largest ||r||^2 since the last reliable update
+    double b2;        // <b, b>
+    double r2true;    // ||b - A x||^2 at the last true-residual evaluation
+    int active;       // 1 while this RHS iterates
+    int iters;
+    int need_ru;      // set when a true-residual (reliable) update is due
+    int nonfinite;    // set when a norm is NaN or Inf
+};
+
+}  // namespace hmc
+
+struct hmc_ctx {
+    hmc_params p{};
+    cudaStream_t stream = nullptr;
+    std::vector<hmc::ChainDesc> chains;
+    int64_t vmax = 0;
+    int kmax = 1;
+    std::string err;
+    int num_sms = 0;
+    int64_t launches = 0;         // kernels launched (tracing)
+
+    // FFT plans keyed by length
+    std::vector<hmc::FftPlan> plans;
+    std::vector<hmc::PcTables> pcs;
+
+    // fermion workspace (complex, K * 4 * vmax entries each)
+    double2* d_r64 = nullptr;     // FP64 residual / true residual
+    double2* d_p64 = nullptr;
+    double2* d_q64 = nullptr;
+    double2* d_z64 = nullptr;
+    double2* d_X = nullptr;       // solve output used by force
+    double2* d_pf = nullptr;      // pseudofermion fields of a trajectory
+    double2* d_chi = nullptr;     // heatbath noise (Philox mode)
+    float2* d_x32 = nullptr;
+    float2* d_r32 = nullptr;
+    float2* d_p32 = nullptr;
+    float2* d_q32 = nullptr;
+    float2* d_z32 = nullptr;
+    float* d_phi32 = nullptr;     // 3 * vmax
+
+    // boson workspace (3 * vmax doubles each)
+    double* d_phi_save = nullptr;
+    double* d_pi = nullptr;
+    double* d_F = nullptr;
+    double* d_vel = nullptr;
+    double* d_z = nullptr;
+    double2* d_fft = nullptr;     // 3 * vmax complex128
+
+    // reductions
+    double* d_part = nullptr;     // partial sums, part_cap doubles
+    int64_t part_cap = 0;
+    double* d_red = nullptr;      // reduced scalars, 64 doubles
+    hmc::CgScalars* d_cg = nullptr;   // kmax entries
+    hmc::CgScalars* h_cg = nullptr;   // pinned mirror
+    double* h_red = nullptr;          // pinned, 64 doubles
+    uint32_t* d_u32 = nullptr;        // 4 words scratch for uniforms
+};
+
+namespace hmc {
+
+// status helpers
+int fail(hmc_ctx* ctx, int code, const std::string& msg);
+int cuda_check(hmc_ctx* ctx, cudaError_t e, const char* what);
+#define HMC_CUDA(ctx, call)                                              \
+    do {                                                                 \
+        cudaError_t _e = (call);                                         \
+        if (_e != cudaSuccess) return ::hmc::cuda_check(ctx, _e, #call); \
+    } while (0)
+#define HMC_LAUNCH(ctx, what)                                             \
+    do {                                                                  \
+        ++(ctx)->launches;                                                \
+        cudaError_t _e = cudaGetLastError();                              \
+        if (_e != cudaSuccess) return ::hmc::cuda_check(ctx, _e, what);   \
+    } while (0)
+
+template <typename R> Coef<R> make_coef(const hmc_params& p);
+
+// stencil.cu
+template <typename R>
+int launch_apply_D(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x, cplx<R>* y,
+                   int dagger, int nrhs);
+// y = A x; if part != nullptr, per-block partial sums of ||D^dag x||^2 are written to
+// part[k * nblk + b] and *nblk_out receives nblk.
+// cgs (may be null): right-hand sides whose cgs[k].active is 0 are skipped.
+template <typename R>
+int launch_apply_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x, cplx<R>* y,
+                   int nrhs, double* part, int* nblk_out, const CgScalars* cgs = nullptr);
+// fermion (+ boson) force and the action pieces, see force() in hmc.h.
+int launch_force(hmc_ctx* ctx, const Lat& lat, double r, const double* phi, const double2* X,
+                 const double2* pf, int nrhs, double* F, int include_boson, double* part,
+                 int* nblk_out);
+int launch_boson(hmc_ctx* ctx, const Lat& lat, double r, const double* phi, double* F,
+                 double* part, int* nblk_out);
+
+// fft.cu
+FftPlan* get_plan(hmc_ctx* ctx, int n);
+int build_plans(hmc_ctx* ctx);
+void free_plans(hmc_ctx* ctx);
+// in-place unitary FFT of complex data viewed as [outer][n][inner] along the middle axis;
+// dir = -1 forward (e^{-2 pi i}), +1 inverse.
+template <typename R>
+int fft_axis(hmc_ctx* ctx, cplx<R>* data, int64_t outer, int n, int64_t inner, int dir);
+template <typename R>
+int launch_precond(hmc_ctx* ctx, const Lat& lat, const cplx<R>* x, cplx<R>* y, int nrhs);
+int metric_op(hmc_ctx* ctx, const Lat& lat, int op, const double* sig, const double* in,
+              double* out, double eps, double* scalar_dev);
+
+// reductions: sum nblk partials for each of k rows into out[k] (device)
+int reduce_rows(hmc_ctx* ctx, const double* part, int k, int nblk, double* out);
+
+// cg.cu
+int cg_run(hmc_ctx* ctx, int chain, const double* phi, const double2* b, double2* x, int nrhs,
+           double tol, int maxit, int precond, hmc_cg_stats* st);
+
+}  // namespace hmc

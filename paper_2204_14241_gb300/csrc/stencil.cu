@@ -1,0 +1,420 @@
+// Fermion-matrix stencils (Eq. D_formula), the fused normal operator A = D D^dagger
+// (Eq. linsys), and the fused force kernel (Eq. hamiltonseq with S = S_B + S_PF).
+#include "internal.h"
+
+namespace hmc {
+
+template <typename R> Coef<R> make_coef(const hmc_params& p) {
+    Coef<R> c;
+    for (int a = 0; a < 2; ++a) {
+        c.diag[a] = (R)(-1.0 - p.dtau * p.mu[a]);
+        c.hx[a] = (R)(-p.dtau * p.t_h[a]);
+        c.hy[a] = (R)(-p.dtau * p.t_v[a]);
+    }
+    c.cpl = (R)(p.dtau * p.g);
+    return c;
+}
+template Coef<float> make_coef<float>(const hmc_params&);
+template Coef<double> make_coef<double>(const hmc_params&);
+
+// ---------------------------------------------------------------------------------------
+// y = D x or D^dagger x, one thread per site, neighbours through the read-only cache.
+template <typename R, bool DAG>
+__global__ void __launch_bounds__(256) k_apply_D(Lat lat, Coef<R> cf, const R* __restrict__ phi,
+                                                 const Site<R>* __restrict__ x,
+                                                 Site<R>* __restrict__ y) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= lat.V) return;
+    const int64_t V = lat.V;
+    const int L = lat.L;
+    const Site<R>* xk = x + blockIdx.y * V;
+    const int xx = (int)(s % L);
+    const int64_t rest = s / L;
+    const int yy = (int)(rest % L);
+    const int t = (int)(rest / L);
+    const int64_t row = s - xx, slice = (int64_t)t * L * L;
+    const int tn = DAG ? tprev(t, lat.Nt) : tnext(t, lat.Nt);
+    const R tsign = DAG ? (t == 0 ? R(-1) : R(1)) : (t == lat.Nt - 1 ? R(-1) : R(1));
+    const R eta = ((xx + yy) & 1) ? R(-1) : R(1);
+    Site<R> o = site_op<R>(cf, load_site(xk + s), load_site(xk + row + wrap_dec(xx, L)),
+                           load_site(xk + row + wrap_inc(xx, L)),
+                           load_site(xk + slice + (int64_t)wrap_dec(yy, L) * L + xx),
+                           load_site(xk + slice + (int64_t)wrap_inc(yy, L) * L + xx),
+                           load_site(xk + (int64_t)tn * L * L + (s - slice)), tsign,
+                           __ldg(phi + s), __ldg(phi + V + s), __ldg(phi + 2 * V + s), eta);
+    store_site(y + blockIdx.y * V + s, o);
+}
+
+template <typename R>
+int launch_apply_D(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x, cplx<R>* y,
+                   int dagger, int nrhs) {
+    if (nrhs <= 0) return HMC_OK;
+    dim3 grid((unsigned)((lat.V + 255) / 256), nrhs);
+    Coef<R> cf = make_coef<R>(ctx->p);
+    auto xs = reinterpret_cast<const Site<R>*>(x);
+    auto ys = reinterpret_cast<Site<R>*>(y);
+    if (dagger) k_apply_D<R, true><<<grid, 256, 0, ctx->stream>>>(lat, cf, phi, xs, ys);
+    else        k_apply_D<R, false><<<grid, 256, 0, ctx->stream>>>(lat, cf, phi, xs, ys);
+    HMC_LAUNCH(ctx, "k_apply_D");
+    return HMC_OK;
+}
+template int launch_apply_D<float>(hmc_ctx*, const Lat&, const float*, const float2*, float2*, int, int);
+template int launch_apply_D<double>(hmc_ctx*, const Lat&, const double*, const double2*, double2*, int, int);
+
+// ---------------------------------------------------------------------------------------
+// Fused y = D (D^dagger x). A block owns a TX x TY tile of sites and marches through a
+// chunk of time slices. For output slice t it needs t_ = D^dagger x on the tile plus a
+// one-site ring at slice t and on the tile at slice t+1; t_ at slice t+1 in turn needs x at
+// t+1 on a two-site ring and x at t on the one-site ring. Each step loads x(t+1) once into
+// shared memory, computes t_(t+1) on the ring, and emits y(t); x and t_ are double
+// buffered. Shared memory holds each site as 16-byte planes (conflict-free vector access).
+template <typename R> struct Planes {
+    static constexpr int NP = sizeof(Site<R>) / 16;   // 2 for float, 4 for double
+};
+
+template <typename R>
+__device__ __forceinline__ void sm_store(uint4* base, int n, int i, const Site<R>& s) {
+    const uint4* v = reinterpret_cast<const uint4*>(&s);
+#pragma unroll
+    for (int q = 0; q < Planes<R>::NP; ++q) base[q * n + i] = v[q];
+}
+template <typename R>
+__device__ __forceinline__ Site<R> sm_load(const uint4* base, int n, int i) {
+    Site<R> s;
+    uint4* v = reinterpret_cast<uint4*>(&s);
+#pragma unroll
+    for (int q = 0; q < Planes<R>::NP; ++q) v[q] = base[q * n + i];
+    return s;
+}
+
+struct ATile {
+    int TX, TY, C;        // tile extent and time-chunk length
+    int ntx, nty, nchunk; // tiles along x, y and chunks along t
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_apply_A(Lat lat, Coef<R> cf, ATile tl,
+                                                 const R* __restrict__ phi,
+                                                 const Site<R>* __restrict__ x,
+                                                 Site<R>* __restrict__ y, double* __restrict__ part,
+                                                 const CgScalars* __restrict__ cgs) {
+    if (cgs && !cgs[blockIdx.z].active) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int TX = tl.TX, TY = tl.TY;
+    const int HX2 = TX + 4, HY2 = TY + 4, N2 = HX2 * HY2;
+    const int HX1 = TX + 2, HY1 = TY + 2, N1 = HX1 * HY1;
+    uint4* xa = reinterpret_cast<uint4*>(smem_raw);
+    uint4* xb = xa + Planes<R>::NP * N2;
+    uint4* ta = xb + Planes<R>::NP * N2;
+    uint4* tb = ta + Planes<R>::NP * N1;
+    R* ph = reinterpret_cast<R*>(tb + Planes<R>::NP * N1);   // [3][N1]
+    __shared__ double red[8];
+
+    const int L = lat.L, Nt = lat.Nt;
+    const int64_t V = lat.V, LL = (int64_t)L * L;
+    const int tile = blockIdx.x;
+    const int x0 = (tile % tl.ntx) * TX, y0 = (tile / tl.ntx) * TY;
+    const int t0 = blockIdx.y * tl.C;
+    const int t1 = min(t0 + tl.C, Nt);
+    const int k = blockIdx.z;
+    const Site<R>* xk = x + k * V;
+    Site<R>* yk = y + k * V;
+
+    auto gx = [&](int i) { int v = (x0 + i) % L; return v < 0 ? v + L : v; };
+    auto gy = [&](int j) { int v = (y0 + j) % L; return v < 0 ? v + L : v; };
+    // x at slice t on the two-site ring into buffer dst (halo2 coordinates); ring1only limits
+    // the load to the one-site ring
+    auto load_x = [&](uint4* dst, int t, bool ring1only) {
+        const int64_t base = (int64_t)t * LL;
+        for (int i = threadIdx.x; i < N2; i += blockDim.x) {
+            const int hx = i % HX2, hy = i / HX2;
+            if (ring1only && (hx == 0 || hy == 0 || hx == HX2 - 1 || hy == HY2 - 1)) continue;
+            const int X = gx(hx - 2), Y = gy(hy - 2);
+            sm_store<R>(dst, N2, i, load_site(xk + base + (int64_t)Y * L + X));
+        }
+    };
+    auto load_phi = [&](int t) {
+        const int64_t base = (int64_t)t * LL;
+        for (int i = threadIdx.x; i < N1; i += blockDim.x) {
+            const int hx = i % HX1, hy = i / HX1;
+            const int64_t s = base + (int64_t)gy(hy - 1) * L + gx(hx - 1);
+            ph[i] = __ldg(phi + s);
+            ph[N1 + i] = __ldg(phi + V + s);
+            ph[2 * N1 + i] = __ldg(phi + 2 * V + s);
+        }
+    };
+    // t_(t) = D^dagger x on the one-site ring from x(t) (cur) and x(t-1) (prev)
+    auto make_t = [&](uint4* dst, const uint4* cur, const uint4* prev, int t) {
+        const R tsign = (t == 0) ? R(-1) : R(1);   // b(t-1)
+        for (int i = threadIdx.x; i < N1; i += blockDim.x) {
+            const int hx = i % HX1, hy = i / HX1;
+            const int c = (hy + 1) * HX2 + hx + 1;
+            const int X = gx(hx - 1), Y = gy(hy - 1);
+            const R eta = ((X + Y) & 1) ? R(-1) : R(1);
+            Site<R> o = site_op<R>(cf, sm_load<R>(cur, N2, c), sm_load<R>(cur, N2, c - 1),
+                                   sm_load<R>(cur, N2, c + 1), sm_load<R>(cur, N2, c - HX2),
+                                   sm_load<R>(cur, N2, c + HX2), sm_load<R>(prev, N2, c), tsign,
+                                   ph[i], ph[N1 + i], ph[2 * N1 + i], eta);
+            sm_store<R>(dst, N1, i, o);
+        }
+    };
+
+    // prologue: t_(t0) on the ring
+    load_x(xa, t0, false);
+    load_x(xb, tprev(t0, Nt), true);
+    load_phi(t0);
+    __syncthreads();
+    make_t(ta, xa, xb, t0);
+    __syncthreads();
+
+    uint4 *xc = xa, *xn = xb, *tc = ta, *tn = tb;
+    double acc = 0.0;
+    for (int t = t0; t < t1; ++t) {
+        const int tp = tnext(t, Nt);
+        load_x(xn, tp, false);
+        load_phi(tp);
+        __syncthreads();
+        make_t(tn, xn, xc, tp);
+        __syncthreads();
+        // y(t) = D t_ on the tile
+        const R tsign = (t == Nt - 1) ? R(-1) : R(1);   // b(t)
+        const int64_t base = (int64_t)t * LL;
+        for (int i = threadIdx.x; i < TX * TY; i += blockDim.x) {
+            const int ix = i % TX, iy = i / TX;
+            const int X = x0 + ix, Y = y0 + iy;
+            if (X >= L || Y >= L) continue;
+            const int c = (iy + 1) * HX1 + ix + 1;
+            const int64_t s = base + (int64_t)Y * L + X;
+            const R eta = ((X + Y) & 1) ? R(-1) : R(1);
+            const Site<R> tcen = sm_load<R>(tc, N1, c);
+            Site<R> o = site_op<R>(cf, tcen, sm_load<R>(tc, N1, c - 1), sm_load<R>(tc, N1, c + 1),
+                                   sm_load<R>(tc, N1, c - HX1), sm_load<R>(tc, N1, c + HX1),
+                                   sm_load<R>(tn, N1, c), tsign, __ldg(phi + s),
+                                   __ldg(phi + V + s), __ldg(phi + 2 * V + s), eta);
+            store_site(yk + s, o);
+            if (part) {
+                R n2 = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) n2 += tcen.c[q].x * tcen.c[q].x + tcen.c[q].y * tcen.c[q].y;
+                acc += (double)n2;
+            }
+        }
+        uint4* sw = xc; xc = xn; xn = sw;
+        sw = tc; tc = tn; tn = sw;
+    }
+    if (part) {
+        const double tot = block_sum(acc, red);
+        if (threadIdx.x == 0)
+            part[(int64_t)k * (gridDim.x * gridDim.y) + blockIdx.y * gridDim.x + blockIdx.x] = tot;
+    }
+}
+
+static int largest_divisor_le(int L, int cap) {
+    for (int d = cap < L ? cap : L; d >= 1; --d)
+        if (L % d == 0) return d;
+    return 1;
+}
+
+static ATile choose_tile(const hmc_ctx* ctx, const Lat& lat, int nrhs, size_t site_bytes) {
+    ATile t;
+    t.TX = largest_divisor_le(lat.L, site_bytes > 32 ? 16 : 32);
+    if (lat.L % 16 == 0 && site_bytes <= 32) t.TX = 16;
+    int cap = (site_bytes > 32 ? 128 : 256) / t.TX;
+    t.TY = largest_divisor_le(lat.L, cap < 1 ? 1 : cap);
+    t.ntx = (lat.L + t.TX - 1) / t.TX;
+    t.nty = (lat.L + t.TY - 1) / t.TY;
+    const int64_t tiles = (int64_t)t.ntx * t.nty * nrhs;
+    const int64_t target = (int64_t)ctx->num_sms * 8;
+    int C = (int)((lat.Nt * tiles + target - 1) / target);
+    if (C < 4) C = 4;
+    if (C > lat.Nt) C = lat.Nt;
+    t.C = C;
+    t.nchunk = (lat.Nt + C - 1) / C;
+    return t;
+}
+
+template <typename R>
+static size_t a_smem_bytes(const ATile& t) {
+    const int N2 = (t.TX + 4) * (t.TY + 4), N1 = (t.TX + 2) * (t.TY + 2);
+    return (size_t)2 * N2 * sizeof(Site<R>) + (size_t)2 * N1 * sizeof(Site<R>) + (size_t)3 * N1 * sizeof(R);
+}
+
+template <typename R>
+int launch_apply_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x, cplx<R>* y,
+                   int nrhs, double* part, int* nblk_out, const CgScalars* cgs) {
+    if (nrhs <= 0) return HMC_OK;
+    ATile tl = choose_tile(ctx, lat, nrhs, sizeof(Site<R>));
+    const size_t sm = a_smem_bytes<R>(tl);
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[sizeof(R) == 8]) {
+        HMC_CUDA(ctx, cudaFuncSetAttribute(k_apply_A<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr_set[sizeof(R) == 8] = true;
+    }
+    dim3 grid(tl.ntx * tl.nty, tl.nchunk, nrhs);
+    if (part && (int64_t)grid.x * grid.y * nrhs > ctx->part_cap)
+        return fail(ctx, HMC_ERR_ARG, "apply_A: reduction buffer too small");
+    k_apply_A<R><<<grid, 256, sm, ctx->stream>>>(lat, make_coef<R>(ctx->p), tl, phi,
+                                                 reinterpret_cast<const Site<R>*>(x),
+                                                 reinterpret_cast<Site<R>*>(y), part, cgs);
+    HMC_LAUNCH(ctx, "k_apply_A");
+    if (nblk_out) *nblk_out = grid.x * grid.y;
+    return HMC_OK;
+}
+template int launch_apply_A<float>(hmc_ctx*, const Lat&, const float*, const float2*, float2*, int, double*, int*, const CgScalars*);
+template int launch_apply_A<double>(hmc_ctx*, const Lat&, const double*, const double2*, double2*, int, double*, int*, const CgScalars*);
+
+// ---------------------------------------------------------------------------------------
+// Boson pieces: -dS_B/dphi and the S_B density (forward differences, see oracle reading).
+struct BosonCoef {
+    double dtau, kt, r, u;   // kt = 1 / (c^2 dtau^2)
+};
+
+__device__ __forceinline__ void boson_site(const Lat& lat, const BosonCoef& bc,
+                                           const double* __restrict__ phi, int64_t s, int xx,
+                                           int yy, int t, double F[3], double& dens) {
+    const int L = lat.L;
+    const int64_t V = lat.V, LL = (int64_t)L * L;
+    const int64_t row = s - xx, slice = (int64_t)t * LL, inplane = s - slice;
+    const int64_t sxp = row + wrap_inc(xx, L), sxm = row + wrap_dec(xx, L);
+    const int64_t syp = slice + (int64_t)wrap_inc(yy, L) * L + xx;
+    const int64_t sym = slice + (int64_t)wrap_dec(yy, L) * L + xx;
+    const int64_t stp = (int64_t)tnext(t, lat.Nt) * LL + inplane;
+    const int64_t stm = (int64_t)tprev(t, lat.Nt) * LL + inplane;
+    double p[3], q2 = 0.0, kin = 0.0, grad = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { p[a] = __ldg(phi + a * V + s); q2 += p[a] * p[a]; }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double* pa = phi + a * V;
+        const double ptp = __ldg(pa + stp), ptm = __ldg(pa + stm);
+        const double pxp = __ldg(pa + sxp), pxm = __ldg(pa + sxm);
+        const double pyp = __ldg(pa + syp), pym = __ldg(pa + sym);
+        const double dtp = ptp - p[a], dxp = pxp - p[a], dyp = pyp - p[a];
+        kin += dtp * dtp;
+        grad += dxp * dxp + dyp * dyp;
+        const double lap_t = 2.0 * p[a] - ptp - ptm;
+        const double lap_xy = 4.0 * p[a] - pxp - pxm - pyp - pym;
+        F[a] = -bc.dtau * (2.0 * bc.kt * lap_t + lap_xy + bc.r * p[a] + bc.u * q2 * p[a]);
+    }
+    dens = bc.dtau * (bc.kt * kin + 0.5 * grad + 0.5 * bc.r * q2 + 0.25 * bc.u * q2 * q2);
+}
+
+// Force: F = -dS_B/dphi (optional) + sum_k 2 dtau g eta Re[X^dag (sigma^x (x) sigma^a) Y],
+// Y = D^dagger X computed on the fly. Partials: [0, nblk) = sum_k 2 Re<pf, X> - |Y|^2,
+// [nblk, 2 nblk) = S_B density.
+__global__ void __launch_bounds__(256) k_force(Lat lat, Coef<double> cf, BosonCoef bc,
+                                               const double* __restrict__ phi,
+                                               const Site<double>* __restrict__ X,
+                                               const Site<double>* __restrict__ pf, int nrhs,
+                                               double* __restrict__ F, int include_boson,
+                                               double* __restrict__ part) {
+    __shared__ double red[8];
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double spf = 0.0, sb = 0.0;
+    if (s < lat.V) {
+        const int64_t V = lat.V;
+        const int L = lat.L;
+        const int xx = (int)(s % L);
+        const int64_t rest = s / L;
+        const int yy = (int)(rest % L);
+        const int t = (int)(rest / L);
+        const int64_t row = s - xx, slice = (int64_t)t * L * L;
+        const int64_t sxm = row + wrap_dec(xx, L), sxp = row + wrap_inc(xx, L);
+        const int64_t sym = slice + (int64_t)wrap_dec(yy, L) * L + xx;
+        const int64_t syp = slice + (int64_t)wrap_inc(yy, L) * L + xx;
+        const int64_t stm = (int64_t)tprev(t, lat.Nt) * L * L + (s - slice);
+        const double tsign = t == 0 ? -1.0 : 1.0;
+        const double eta = ((xx + yy) & 1) ? -1.0 : 1.0;
+        const double p1 = __ldg(phi + s), p2 = __ldg(phi + V + s), p3 = __ldg(phi + 2 * V + s);
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < nrhs; ++k) {
+            const Site<double>* Xk = X + k * V;
+            const Site<double> xc = load_site(Xk + s);
+            const Site<double> Y = site_op<double>(cf, xc, load_site(Xk + sxm), load_site(Xk + sxp),
+                                                   load_site(Xk + sym), load_site(Xk + syp),
+                                                   load_site(Xk + stm), tsign, p1, p2, p3, eta);
+            const Site<double> pk = load_site(pf + k * V + s);
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const double2 x0 = xc.c[a * 2], x1 = xc.c[a * 2 + 1];
+                const double2 y0 = Y.c[(1 - a) * 2], y1 = Y.c[(1 - a) * 2 + 1];
+                const double2 z01 = cmulconj(x0, y1), z10 = cmulconj(x1, y0);
+                const double2 z00 = cmulconj(x0, y0), z11 = cmulconj(x1, y1);
+                acc[0] += z01.x + z10.x;          // sigma^1
+                acc[1] += z01.y - z10.y;          // sigma^2: Re(-i z01 + i z10)
+                acc[2] += z00.x - z11.x;          // sigma^3
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                spf += 2.0 * (pk.c[q].x * xc.c[q].x + pk.c[q].y * xc.c[q].y)
+                       - (Y.c[q].x * Y.c[q].x + Y.c[q].y * Y.c[q].y);
+            }
+        }
+        const double f = 2.0 * cf.cpl * eta;
+        double Fb[3] = {0.0, 0.0, 0.0};
+        if (include_boson) boson_site(lat, bc, phi, s, xx, yy, t, Fb, sb);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) F[a * V + s] = f * acc[a] + Fb[a];
+    }
+    const double a = block_sum(spf, red);
+    const double b = block_sum(sb, red);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = a;
+        part[gridDim.x + blockIdx.x] = b;
+    }
+}
+
+static BosonCoef boson_coef(const hmc_params& p, double r) {
+    BosonCoef b;
+    b.dtau = p.dtau;
+    b.kt = 1.0 / (p.c * p.c * p.dtau * p.dtau);
+    b.r = r;
+    b.u = p.u;
+    return b;
+}
+
+int launch_force(hmc_ctx* ctx, const Lat& lat, double r, const double* phi, const double2* X,
+                 const double2* pf, int nrhs, double* F, int include_boson, double* part,
+                 int* nblk_out) {
+    const int nblk = (int)((lat.V + 255) / 256);
+    if (2 * (int64_t)nblk > ctx->part_cap) return fail(ctx, HMC_ERR_ARG, "force: reduction buffer too small");
+    k_force<<<nblk, 256, 0, ctx->stream>>>(lat, make_coef<double>(ctx->p), boson_coef(ctx->p, r), phi,
+                                           reinterpret_cast<const Site<double>*>(X),
+                                           reinterpret_cast<const Site<double>*>(pf), nrhs, F,
+                                           include_boson, part);
+    HMC_LAUNCH(ctx, "k_force");
+    *nblk_out = nblk;
+    return HMC_OK;
+}
+
+__global__ void __launch_bounds__(256) k_boson(Lat lat, BosonCoef bc, const double* __restrict__ phi,
+                                               double* __restrict__ F, double* __restrict__ part) {
+    __shared__ double red[8];
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double sb = 0.0;
+    if (s < lat.V) {
+        const int L = lat.L;
+        const int xx = (int)(s % L);
+        const int64_t rest = s / L;
+        double Fb[3];
+        boson_site(lat, bc, phi, s, xx, (int)(rest % L), (int)(rest / L), Fb, sb);
+        if (F) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) F[a * lat.V + s] = Fb[a];
+        }
+    }
+    const double b = block_sum(sb, red);
+    if (threadIdx.x == 0) part[blockIdx.x] = b;
+}
+
+int launch_boson(hmc_ctx* ctx, const Lat& lat, double r, const double* phi, double* F,
+                 double* part, int* nblk_out) {
+    const int nblk = (int)((lat.V + 255) / 256);
+    if (nblk > ctx->part_cap) return fail(ctx, HMC_ERR_ARG, "boson: reduction buffer too small");
+    k_boson<<<nblk, 256, 0, ctx->stream>>>(lat, boson_coef(ctx->p, r), phi, F, part);
+    HMC_LAUNCH(ctx, "k_boson");
+    *nblk_out = nblk;
+    return HMC_OK;
+}
+
+}  // namespace hmc

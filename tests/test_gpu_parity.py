@@ -1,0 +1,308 @@
+"""GPU parity: every step of the hot path, called through the C ABI (libhmc via the ctypes
+binding), against the FP64 oracle on the same seeded inputs.
+
+Tolerances (relative to the largest reference entry unless stated):
+* FP64 operator applications: 1e-12 (a few hundred roundings of O(1) terms).
+* FP32 operator applications: 1e-5 (the bar for the mixed mode; FP32 unit roundoff is 6e-8 and
+  each output sums ~20 terms).
+* Solves: the oracle's FP64 true residual of the GPU solution is <= 1.5 * tol in both modes.
+* Force: 1e-7 relative at solver tolerance 1e-12; S_PF (variational form, error quadratic in
+  the residual): 1e-10 relative.
+* Trajectory: |dH_gpu - dH_oracle| < 1e-8 and phi' within 1e-9.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle.model import Params
+from oracle import fermion, solver, boson, hmc as ohmc
+from paper_2204_14241_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+COUPLINGS = dict(dtau=0.1, t_h=(1.0, 0.5), t_v=(0.5, 1.0), mu=(-0.5, -0.5), g=1.0, r=0.5, u=1.0, c=3.0)
+CASES = [(4, 8), (6, 7), (20, 12), (12, 24)]
+
+
+def ctx_for(L, Nt, solver_mode="fp64", nrhs=2, tol=1e-12, chains=None):
+    from paper_2204_14241_gb300.hmc import Context
+    return Context(L, Nt, solver=solver_mode, nrhs_max=nrhs, cg_tol=tol, chains=chains, **COUPLINGS)
+
+
+def oparams(L, Nt, r=None):
+    kw = dict(COUPLINGS)
+    if r is not None:
+        kw["r"] = r
+    return Params(L=L, Nt=Nt, **kw)
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return t.to(dtype) if dtype is not None else t
+
+
+def to_paper_vecs(t):
+    a = t.detach().cpu().numpy().astype(np.complex128)
+    return [I.to_paper_fermion(a[k]) for k in range(a.shape[0])]
+
+
+def rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+@pytest.mark.parametrize("L,Nt", CASES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_apply_D_and_Ddag(L, Nt, prec):
+    ctx = ctx_for(L, Nt)
+    P = oparams(L, Nt)
+    rdt, cdt = (torch.float64, torch.complex128) if prec == "fp64" else (torch.float32, torch.complex64)
+    phi = dev(I.gaussian_field(1, L, Nt), rdt)
+    x = dev(I.fermion_noise(2, 2, L, Nt), cdt)
+    phi_o = I.to_paper_boson(phi.double().cpu().numpy())
+    xs = to_paper_vecs(x)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    for dagger in (False, True):
+        y = ctx.apply_M(phi, x, dagger=dagger)
+        ys = to_paper_vecs(y)
+        for k in range(2):
+            ref = (fermion.apply_Ddag if dagger else fermion.apply_D)(P, phi_o, xs[k])
+            assert rel(ys[k], ref) < tol, (dagger, k)
+
+
+@pytest.mark.parametrize("L,Nt", CASES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_apply_A_fused(L, Nt, prec):
+    ctx = ctx_for(L, Nt)
+    P = oparams(L, Nt)
+    rdt, cdt = (torch.float64, torch.complex128) if prec == "fp64" else (torch.float32, torch.complex64)
+    phi = dev(I.gaussian_field(3, L, Nt), rdt)
+    x = dev(I.fermion_noise(4, 2, L, Nt), cdt)
+    phi_o = I.to_paper_boson(phi.double().cpu().numpy())
+    xs = to_paper_vecs(x)
+    y, norms = ctx.apply_MdagM(phi, x, norms=True)
+    ys = to_paper_vecs(y)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    for k in range(2):
+        assert rel(ys[k], fermion.apply_A(P, phi_o, xs[k])) < tol
+        t = fermion.apply_Ddag(P, phi_o, xs[k])
+        n2 = np.vdot(t, t).real
+        assert abs(norms[k] - n2) < tol * n2
+
+
+@pytest.mark.parametrize("L,Nt", CASES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_preconditioner(L, Nt, prec):
+    ctx = ctx_for(L, Nt)
+    P = oparams(L, Nt)
+    cdt = torch.complex128 if prec == "fp64" else torch.complex64
+    x = dev(I.fermion_noise(5, 2, L, Nt), cdt)
+    y = ctx.apply_precond(x)
+    xs, ys = to_paper_vecs(x), to_paper_vecs(y)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    for k in range(2):
+        assert rel(ys[k], solver.apply_precond(P, xs[k])) < tol
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("precond", [False, True])
+@pytest.mark.parametrize("L,Nt", [(6, 7), (12, 24)])
+def test_cg_solve(mode, precond, L, Nt):
+    tol = 1e-10
+    ctx = ctx_for(L, Nt, mode, tol=tol)
+    P = oparams(L, Nt)
+    phi = dev(I.gaussian_field(6, L, Nt))
+    b = dev(I.fermion_noise(7, 2, L, Nt))
+    x, st = ctx.cg_solve(phi, b, precond=precond)
+    assert st["converged"] and st["true_rel_resid"] <= tol
+    phi_o = I.to_paper_boson(phi.cpu().numpy())
+    for xk, bk in zip(to_paper_vecs(x), to_paper_vecs(b)):
+        res = bk - fermion.apply_A(P, phi_o, xk)
+        assert np.linalg.norm(res) <= 1.5 * tol * np.linalg.norm(bk)
+    if mode == "mixed":
+        assert st["reliable_updates"] >= 1
+
+
+def test_cg_matches_dense_solution():
+    L, Nt = 4, 8
+    ctx = ctx_for(L, Nt, "mixed", tol=1e-12)
+    P = oparams(L, Nt)
+    phi = dev(I.gaussian_field(8, L, Nt))
+    b = dev(I.fermion_noise(9, 1, L, Nt))
+    x, st = ctx.cg_solve(phi, b, precond=True)
+    ref = solver.dense_solve(P, I.to_paper_boson(phi.cpu().numpy()), to_paper_vecs(b)[0])
+    assert rel(to_paper_vecs(x)[0], ref) < 1e-9
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("nrhs", [1, 2])
+def test_force(mode, nrhs):
+    L, Nt = 6, 7
+    ctx = ctx_for(L, Nt, mode, tol=1e-12)
+    P = oparams(L, Nt)
+    phi = dev(I.gaussian_field(10, L, Nt) * 0.7)
+    pf = dev(I.fermion_noise(11, nrhs, L, Nt))
+    F, spf, sb, st = ctx.force(phi, pf, include_boson=True, precond=True)
+    phi_o = I.to_paper_boson(phi.cpu().numpy())
+    Fo, spf_o, _ = ohmc.force(P, phi_o, to_paper_vecs(pf), method="dense")
+    assert rel(I.to_paper_boson(F.cpu().numpy()), Fo) < 1e-7
+    assert abs(spf - spf_o) < 1e-10 * abs(spf_o)
+    assert abs(sb - boson.action(P, phi_o)) < 1e-12 * abs(sb)
+    Ff, _, _, _ = ctx.force(phi, pf, include_boson=False, precond=False)
+    Fo_f, _, _ = ohmc.force(P, phi_o, to_paper_vecs(pf), method="dense", include_boson=False)
+    assert rel(I.to_paper_boson(Ff.cpu().numpy()), Fo_f) < 1e-7
+
+
+@pytest.mark.parametrize("L,Nt", [(4, 8), (6, 7), (20, 12)])
+def test_metric_operations(L, Nt):
+    ctx = ctx_for(L, Nt)
+    w = np.fft.fftn(I.gaussian_field(12, L, Nt), axes=(1, 2, 3), norm="ortho")
+    sig_g = (w * np.conj(w)).real + 0.1                       # even in k, positive (library layout)
+    z_g = I.gaussian_field(13, L, Nt)
+    sig_o, z_o = I.to_paper_boson(sig_g), I.to_paper_boson(z_g)
+    sig, z = dev(sig_g), dev(z_g)
+    from paper_2204_14241_gb300.hmc import METRIC_MOMENTUM, METRIC_VELOCITY, METRIC_KINETIC, METRIC_ACCUM
+    pi = ctx.metric(METRIC_MOMENTUM, sig, z)
+    pi_o = ohmc.momentum(sig_o, z_o)
+    assert rel(I.to_paper_boson(pi.cpu().numpy()), pi_o) < 1e-12
+    v = ctx.metric(METRIC_VELOCITY, sig, pi)
+    assert rel(I.to_paper_boson(v.cpu().numpy()), ohmc.velocity(sig_o, pi_o)) < 1e-12
+    k = ctx.metric(METRIC_KINETIC, sig, pi)
+    assert abs(k - ohmc.kinetic(sig_o, pi_o)) < 1e-12 * abs(k)
+    acc = ctx.metric(METRIC_ACCUM, sig, z)
+    acc = ctx.metric(METRIC_ACCUM, sig, pi, out=acc)
+    ref = ohmc.sigma_estimate([z_o, pi_o]) * 2
+    assert rel(I.to_paper_boson(acc.cpu().numpy()), ref) < 1e-12
+
+
+def test_boson_action_and_force_parity():
+    L, Nt = 6, 7
+    ctx = ctx_for(L, Nt, nrhs=1)
+    P = oparams(L, Nt)
+    phi = dev(I.gaussian_field(14, L, Nt))
+    pf = dev(np.zeros((1, Nt, L, L, 2, 2), dtype=complex))
+    F, spf, sb, _ = ctx.force(phi, pf, include_boson=True, precond=False)
+    phi_o = I.to_paper_boson(phi.cpu().numpy())
+    assert spf == 0.0
+    assert abs(sb - boson.action(P, phi_o)) < 1e-12 * abs(sb)
+    assert rel(I.to_paper_boson(F.cpu().numpy()), -boson.grad(P, phi_o)) < 1e-12
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("nrhs", [1, 2])
+def test_trajectory_matches_oracle(mode, nrhs):
+    # the small configuration: L = 4, Nt = 8, dtau = 0.1, eps = 0.05, n_leap = 10
+    L, Nt, eps, n_leap = 4, 8, 0.05, 10
+    ctx = ctx_for(L, Nt, mode, nrhs=nrhs, tol=1e-12)
+    P = oparams(L, Nt)
+    phi0 = I.gaussian_field(20, L, Nt)
+    w = np.fft.fftn(I.gaussian_field(21, L, Nt), axes=(1, 2, 3), norm="ortho")
+    sig_g = (w * np.conj(w)).real * 0.5 + 0.5
+    chi = I.fermion_noise(22, nrhs, L, Nt)
+    z = I.gaussian_field(23, L, Nt)
+    u = 0.37
+    phi = dev(phi0)
+    out = ctx.trajectory([phi], [dev(sig_g)], eps, n_leap, nrhs=nrhs, precond=True,
+                         chi=[dev(chi)], z=[dev(z)], u=[u])
+    ref = ohmc.trajectory(P, I.to_paper_boson(phi0), I.to_paper_boson(sig_g),
+                          [I.to_paper_fermion(chi[k]) for k in range(nrhs)], I.to_paper_boson(z), u, eps,
+                          n_leap, method="dense")
+    assert abs(out["dH"][0] - ref["dH"]) < 1e-8, (out["dH"], ref["dH"])
+    assert out["accepted"][0] == ref["accept"]
+    e = out["energies"][0]
+    assert abs(e[0] - ref["kinetic"][0]) < 1e-10 * abs(e[0])
+    assert abs(e[1] - ref["S_B"][0]) < 1e-10 * abs(e[1])
+    assert abs(e[2] - ref["S_PF"][0]) < 1e-10 * abs(e[2])
+    assert abs(e[5] - ref["S_PF"][1]) < 1e-9 * abs(e[5])
+    assert rel(I.to_paper_boson(phi.cpu().numpy()), ref["phi"]) < 1e-9
+
+
+def test_trajectory_two_chains_uneven():
+    chains = [(4, 8, 0.5), (6, 4, 0.8)]
+    ctx = ctx_for(4, 8, "mixed", nrhs=1, tol=1e-12, chains=chains)
+    phis, sigs, chis, zs, us, refs = [], [], [], [], [], []
+    for c, (L, Nt, r) in enumerate(chains):
+        phi0 = I.gaussian_field(30 + c, L, Nt) * 0.5
+        chi = I.fermion_noise(40 + c, 1, L, Nt)
+        z = I.gaussian_field(50 + c, L, Nt)
+        sig = np.ones((3, Nt, L, L))
+        phis.append(dev(phi0)); sigs.append(dev(sig)); chis.append(dev(chi)); zs.append(dev(z)); us.append(0.5)
+        refs.append(ohmc.trajectory(oparams(L, Nt, r), I.to_paper_boson(phi0), I.to_paper_boson(sig),
+                                    [I.to_paper_fermion(chi[0])], I.to_paper_boson(z), 0.5, 0.04, 5, method="dense"))
+    out = ctx.trajectory(phis, sigs, 0.04, 5, nrhs=1, chi=chis, z=zs, u=us)
+    for c in range(2):
+        assert abs(out["dH"][c] - refs[c]["dH"]) < 1e-8
+        assert rel(I.to_paper_boson(phis[c].cpu().numpy()), refs[c]["phi"]) < 1e-9
+
+
+def test_philox_known_answers():
+    # Random123 known-answer vectors for Philox4x32-10 (Salmon et al., SC'11)
+    ctx = ctx_for(4, 8)
+    kat = [((0, 0, 0, 0), 0, (0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8)),
+           ((0xffffffff,) * 4, 0xffffffffffffffff, (0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd)),
+           ((0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344), 0x299f31d0a4093822,
+            (0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1))]
+    for ctr, key, want in kat:
+        got = ctx.philox_raw(key, ctr, 1).cpu().tolist()
+        assert tuple(got) == want
+
+
+def test_philox_normals_statistics():
+    ctx = ctx_for(4, 8)
+    z = ctx.philox_normal(7, 3, 1_000_000).cpu().numpy()
+    assert abs(z.mean()) < 5e-3 and abs(z.var() - 1) < 5e-3
+    c = ctx.philox_normal(7, 4, 500_000, complex_out=True).cpu().numpy()
+    assert abs(np.mean(np.abs(c) ** 2) - 1) < 5e-3 and abs(np.mean(c.real * c.imag)) < 3e-3
+    z2 = ctx.philox_normal(7, 3, 1_000_000).cpu().numpy()
+    assert np.array_equal(z, z2)
+
+
+def test_philox_trajectory_reproducible():
+    L, Nt = 4, 8
+    ctx = ctx_for(L, Nt, "mixed", nrhs=1)
+    phi0 = dev(I.gaussian_field(60, L, Nt))
+    sig = dev(np.ones((3, Nt, L, L)))
+    a, b = phi0.clone(), phi0.clone()
+    o1 = ctx.trajectory([a], [sig], 0.05, 4, seed=11, counter=5)
+    o2 = ctx.trajectory([b], [sig], 0.05, 4, seed=11, counter=5)
+    assert o1["dH"] == o2["dH"] and torch.equal(a, b)
+
+
+def test_full_size_apply_A_sampled():
+    # the largest configuration: L = 80, Nt = 160, 8 right-hand sides, FP32 storage
+    L, Nt, K = 80, 160, 8
+    ctx = ctx_for(L, Nt, "mixed", nrhs=K)
+    P = oparams(L, Nt)
+    phi64 = I.smooth_field(70, L, Nt, 0.5, 2.0 / (9 * 0.01)) / np.sqrt(0.1)
+    phi = dev(phi64, torch.float32)
+    x = dev(I.fermion_noise(71, K, L, Nt), torch.complex64)
+    y, norms = ctx.apply_MdagM(phi, x, norms=True)
+    phi_o = I.to_paper_boson(phi.double().cpu().numpy())
+    xv = x.cpu().numpy().astype(np.complex128)
+    yv = y.cpu().numpy().astype(np.complex128)
+    for k in (0, K - 1):
+        ref = fermion.apply_A(P, phi_o, I.to_paper_fermion(xv[k]))
+        assert rel(I.to_paper_fermion(yv[k]), ref) < 1e-5
+        t = fermion.apply_Ddag(P, phi_o, I.to_paper_fermion(xv[k]))
+        assert abs(norms[k] - np.vdot(t, t).real) < 1e-5 * norms[k]
+
+
+def test_errors_reported():
+    from paper_2204_14241_gb300.hmc import HmcError, HMC_ERR_ARG, HMC_ERR_NOCONV, HMC_ERR_NONFINITE
+    L, Nt = 4, 8
+    ctx = ctx_for(L, Nt, "mixed", nrhs=1)
+    phi = dev(I.gaussian_field(80, L, Nt))
+    b = dev(I.fermion_noise(81, 1, L, Nt))
+    x, st = ctx.cg_solve(phi, b, maxit=1, precond=False, raise_on_noconv=False)
+    assert st["status"] == HMC_ERR_NOCONV and not st["converged"]
+    bad = phi.clone()
+    bad[0, 0, 0, 0] = float("nan")
+    with pytest.raises(HmcError) as e:
+        ctx.cg_solve(bad, b)
+    assert e.value.code == HMC_ERR_NONFINITE
+    with pytest.raises(HmcError) as e:
+        ctx._check(ctx.lib.apply_M(ctx.h, 3, 0, None, None, None, 0, 1))
+    assert e.value.code == HMC_ERR_ARG
+    # the context stays usable after every error
+    x, st = ctx.cg_solve(phi, b)
+    assert st["converged"]
