@@ -71,18 +71,6 @@ __global__ void __launch_bounds__(256) k_cg_xr(V16<R>* __restrict__ x, V16<R>* _
     if (threadIdx.x == 0) part[(int64_t)k * gridDim.x + blockIdx.x] = s;
 }
 
-// p = z + beta p
-template <typename R>
-__global__ void __launch_bounds__(256) k_cg_p(V16<R>* __restrict__ p, const V16<R>* __restrict__ z,
-                                              int64_t n16, const CgScalars* __restrict__ cgs) {
-    const int k = blockIdx.y;
-    if (!cgs[k].active) return;
-    const R beta = (R)cgs[k].beta;
-    const int64_t off = k * n16;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x)
-        p[off + i] = v_axpy(beta, p[off + i], z[off + i]);
-}
-
 __device__ __forceinline__ double row_sum(const double* part, int nblk, double* red) {
     double s = 0.0;
     for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += part[i];
@@ -234,20 +222,20 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
     const double delta2 = 0.01;                       // reliable update at ||r|| < 0.1 max||r||
     CgScalars* cgs = ctx->d_cg;
     double* part = ctx->d_part;
-    double* part2 = ctx->d_part + (int64_t)ctx->kmax * kRedBlocks;
+    double* part2 = ctx->d_part + ctx->part_cap / 2;
     const dim3 vgrid(kRedBlocks, nrhs);
 
-    C *xv, *rv, *pv, *qv, *zv;
+    C *xv, *rv, *pv, *pw, *qv, *zv;   // pv: current direction, pw: the other buffer
     const R* phiR;
     if constexpr (kMixed) {
-        xv = ctx->d_x32; rv = ctx->d_r32; pv = ctx->d_p32; qv = ctx->d_q32;
+        xv = ctx->d_x32; rv = ctx->d_r32; pv = ctx->d_p32; pw = ctx->d_p32b; qv = ctx->d_q32;
         zv = precond ? ctx->d_z32 : ctx->d_r32;
         k_phi_to32<<<(unsigned)((3 * lat.V + 255) / 256), 256, 0, sm>>>(phi64, ctx->d_phi32, 3 * lat.V);
         HMC_LAUNCH(ctx, "k_phi_to32");
         phiR = ctx->d_phi32;
         HMC_CUDA(ctx, cudaMemsetAsync(ctx->d_x32, 0, nrhs * n * sizeof(float2), sm));
     } else {
-        xv = x; rv = ctx->d_r64; pv = ctx->d_p64; qv = ctx->d_q64;
+        xv = x; rv = ctx->d_r64; pv = ctx->d_p64; pw = ctx->d_p64b; qv = ctx->d_q64;
         zv = precond ? ctx->d_z64 : ctx->d_r64;
         phiR = phi64;
     }
@@ -259,8 +247,10 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
     HMC_LAUNCH(ctx, "k_cg_start");
 
     int rc;
-    // z = P r, rz = <r, z>, p = z
-    auto restart_dir = [&](bool set_p) -> int {
+    // directions start at zero: the first fused update forms p = z + 0 * p
+    HMC_CUDA(ctx, cudaMemsetAsync(pv, 0, nrhs * n * sizeof(C), sm));
+    // z = P r, rz = <r, z>
+    auto restart_dir = [&]() -> int {
         if (precond) {
             if ((rc = launch_precond<R>(ctx, lat, rv, zv, nrhs))) return rc;
             k_dot<R><<<vgrid, 256, 0, sm>>>(reinterpret_cast<const V16<R>*>(rv), reinterpret_cast<const V16<R>*>(zv),
@@ -272,10 +262,9 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
         HMC_LAUNCH(ctx, "k_dot");
         k_cg_set_rz<<<nrhs, 256, 0, sm>>>(cgs, part, kRedBlocks);
         HMC_LAUNCH(ctx, "k_cg_set_rz");
-        if (set_p) HMC_CUDA(ctx, cudaMemcpyAsync(pv, zv, nrhs * n * sizeof(C), cudaMemcpyDeviceToDevice, sm));
         return HMC_OK;
     };
-    if ((rc = restart_dir(true))) return rc;
+    if ((rc = restart_dir())) return rc;
 
     // true-residual update for every active RHS
     int n_ru = 0;
@@ -291,7 +280,7 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
         HMC_LAUNCH(ctx, "k_residual");
         k_ru_finish<<<nrhs, 256, 0, sm>>>(cgs, part, kRedBlocks, tol2);
         HMC_LAUNCH(ctx, "k_ru_finish");
-        return restart_dir(false);
+        return restart_dir();
     };
 
     const int check_every = 8;
@@ -299,24 +288,24 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
     int it = 0;
     while (!done) {
         if (it >= maxit) break;
+        // p = z + beta p (fused into the operator), q = A p, partial <p, A p>
         int nb = 0;
-        if ((rc = launch_apply_A<R>(ctx, lat, phiR, pv, qv, nrhs, part, &nb, cgs))) return rc;
+        if ((rc = launch_apply_A<R>(ctx, lat, phiR, zv, qv, nrhs, part, &nb, cgs, pv, pw))) return rc;
+        { C* t = pv; pv = pw; pw = t; }
         k_cg_alpha<<<nrhs, 256, 0, sm>>>(cgs, part, nb);
         HMC_LAUNCH(ctx, "k_cg_alpha");
-        k_cg_xr<R><<<vgrid, 256, 0, sm>>>(reinterpret_cast<V16<R>*>(xv), reinterpret_cast<V16<R>*>(rv),
-                                          reinterpret_cast<const V16<R>*>(pv), reinterpret_cast<const V16<R>*>(qv),
-                                          n16, part, cgs);
-        HMC_LAUNCH(ctx, "k_cg_xr");
+        int nbr = kRedBlocks;
         if (precond) {
-            if ((rc = launch_precond<R>(ctx, lat, rv, zv, nrhs))) return rc;
-            k_dot<R><<<vgrid, 256, 0, sm>>>(reinterpret_cast<const V16<R>*>(rv), reinterpret_cast<const V16<R>*>(zv),
-                                            n16, part2, cgs);
-            HMC_LAUNCH(ctx, "k_dot");
+            // x += alpha p, r -= alpha q, z = P r, with ||r||^2 and <r, z>
+            if ((rc = launch_cg_update_precond<R>(ctx, lat, xv, rv, pv, qv, zv, nrhs, cgs, part, part2, &nbr))) return rc;
+        } else {
+            k_cg_xr<R><<<vgrid, 256, 0, sm>>>(reinterpret_cast<V16<R>*>(xv), reinterpret_cast<V16<R>*>(rv),
+                                              reinterpret_cast<const V16<R>*>(pv), reinterpret_cast<const V16<R>*>(qv),
+                                              n16, part, cgs);
+            HMC_LAUNCH(ctx, "k_cg_xr");
         }
-        k_cg_beta<<<nrhs, 256, 0, sm>>>(cgs, part, precond ? part2 : nullptr, kRedBlocks, tol2, delta2, kMixed);
+        k_cg_beta<<<nrhs, 256, 0, sm>>>(cgs, part, precond ? part2 : nullptr, nbr, tol2, delta2, kMixed);
         HMC_LAUNCH(ctx, "k_cg_beta");
-        k_cg_p<R><<<vgrid, 256, 0, sm>>>(reinterpret_cast<V16<R>*>(pv), reinterpret_cast<const V16<R>*>(zv), n16, cgs);
-        HMC_LAUNCH(ctx, "k_cg_p");
         ++it;
         if (it % check_every == 0 || it >= maxit) {
             HMC_CUDA(ctx, cudaMemcpyAsync(ctx->h_cg, cgs, nrhs * sizeof(CgScalars), cudaMemcpyDeviceToHost, sm));

@@ -112,9 +112,11 @@ __device__ __forceinline__ void tile_origin(const FftTile& ft, int64_t& o0, int6
     i0 = (blockIdx.x % ft.nib) * ft.IC;
 }
 
+// out-of-place when src != data (each tile reads src and writes data)
 template <typename R>
-__global__ void __launch_bounds__(256) k_fft(cplx<R>* __restrict__ data, FftTile ft, StagePlan sp,
-                                             const cplx<R>* __restrict__ tw, int dir, R scale) {
+__global__ void __launch_bounds__(256) k_fft(const cplx<R>* src, cplx<R>* data, FftTile ft, StagePlan sp,
+                                             const cplx<R>* __restrict__ tw, int dir, R scale,
+                                             const CgScalars* __restrict__ cgs, int64_t opr) {
     using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nl = ft.OB * ft.IC, n = sp.n;
@@ -127,7 +129,8 @@ __global__ void __launch_bounds__(256) k_fft(cplx<R>* __restrict__ data, FftTile
         const int ic = e % ft.IC, rest = e / ft.IC;
         const int j = rest % n, ob = rest / n;
         const int64_t o = o0 + ob, i = i0 + ic;
-        if (o < ft.outer && i < ft.inner) a[j * nl + ob * ft.IC + ic] = data[(o * n + j) * ft.inner + i];
+        if (o < ft.outer && i < ft.inner && !(cgs && !cgs[o / opr].active))
+            a[j * nl + ob * ft.IC + ic] = src[(o * n + j) * ft.inner + i];
     }
     __syncthreads();
     C* res = run_stages<C>(a, b, sp, nl, tw, dir);
@@ -135,8 +138,69 @@ __global__ void __launch_bounds__(256) k_fft(cplx<R>* __restrict__ data, FftTile
         const int ic = e % ft.IC, rest = e / ft.IC;
         const int j = rest % n, ob = rest / n;
         const int64_t o = o0 + ob, i = i0 + ic;
-        if (o < ft.outer && i < ft.inner) data[(o * n + j) * ft.inner + i] = cscale(res[j * nl + ob * ft.IC + ic], scale);
+        if (o < ft.outer && i < ft.inner && !(cgs && !cgs[o / opr].active))
+            data[(o * n + j) * ft.inner + i] = cscale(res[j * nl + ob * ft.IC + ic], scale);
     }
+}
+
+// x-axis FFT passes fused with the CG vector work, one right-hand side per blockIdx.y, data
+// [nrhs][Nt * L][L][4]. Lines are (row, component); a tile holds OB whole rows.
+//  MODE 1 (forward): x += alpha p, r -= alpha q (written back), partial ||r||^2, then the
+//         forward FFT of r along x into out.
+//  MODE 2 (inverse): inverse FFT along x of in, written to out, and partial Re<r, out>.
+template <typename R, int MODE>
+__global__ void __launch_bounds__(256) k_fft_x_cg(const cplx<R>* in, cplx<R>* out, cplx<R>* __restrict__ xv,
+                                                  cplx<R>* __restrict__ rv, const cplx<R>* __restrict__ pv,
+                                                  const cplx<R>* __restrict__ qv, int64_t rows, int OB,
+                                                  StagePlan sp, const cplx<R>* __restrict__ tw,
+                                                  const CgScalars* __restrict__ cgs, double* __restrict__ part) {
+    using C = cplx<R>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[8];
+    const int k = blockIdx.y;
+    if (!cgs[k].active) return;
+    const int n = sp.n, nl = OB * 4;
+    C* a = reinterpret_cast<C*>(smem_raw);
+    C* b = a + (int64_t)n * nl;
+    const int64_t base = ((int64_t)k * rows + (int64_t)blockIdx.x * OB) * n * 4;   // first element of the tile
+    const int64_t nrow = min((int64_t)OB, rows - (int64_t)blockIdx.x * OB);
+    const int tot = (int)(nrow * n * 4);
+    const R alpha = (R)cgs[k].alpha;
+    double acc = 0.0;
+    // element e of the tile: row ob = e / (4n), j = (e / 4) % n, component c = e % 4
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        const int c = e & 3, j = (e >> 2) % n, ob = (e >> 2) / n;
+        const int64_t g = base + e;
+        C v;
+        if constexpr (MODE == 1) {
+            C xx = xv[g], r = rv[g];
+            const C pp = pv[g], qq = qv[g];
+            xx.x += alpha * pp.x; xx.y += alpha * pp.y;
+            r.x -= alpha * qq.x; r.y -= alpha * qq.y;
+            xv[g] = xx;
+            rv[g] = r;
+            acc += (double)(r.x * r.x + r.y * r.y);
+            v = r;
+        } else {
+            v = in[g];
+        }
+        a[j * nl + ob * 4 + c] = v;
+    }
+    __syncthreads();
+    C* res = run_stages<C>(a, b, sp, nl, tw, MODE == 1 ? -1 : +1);
+    const R scale = (R)(1.0 / sqrt((double)n));
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        const int c = e & 3, j = (e >> 2) % n, ob = (e >> 2) / n;
+        const int64_t g = base + e;
+        const C v = cscale(res[j * nl + ob * 4 + c], scale);
+        out[g] = v;
+        if constexpr (MODE == 2) {
+            const C r = rv[g];
+            acc += (double)(r.x * v.x + r.y * v.y);
+        }
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) part[(int64_t)k * gridDim.x + blockIdx.x] = acc;
 }
 
 // Preconditioner pass along tau on data [nrhs][Nt][L*L*4] already Fourier transformed in
@@ -154,7 +218,7 @@ struct PrecondCoef {
 template <typename R>
 __global__ void __launch_bounds__(256) k_precond_tau(cplx<R>* __restrict__ data, FftTile ft,
                                                      StagePlan sp, const cplx<R>* __restrict__ tw,
-                                                     PrecondCoef pc, R scale2) {
+                                                     PrecondCoef pc, R scale2, const CgScalars* __restrict__ cgs) {
     using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nl = ft.OB * ft.IC, n = sp.n;
@@ -168,7 +232,7 @@ __global__ void __launch_bounds__(256) k_precond_tau(cplx<R>* __restrict__ data,
         const int j = rest % n, ob = rest / n;
         const int64_t o = o0 + ob, i = i0 + ic;
         C v = mk<C>(0.0, 0.0);
-        if (o < ft.outer && i < ft.inner) {
+        if (o < ft.outer && i < ft.inner && !(cgs && !cgs[o].active)) {
             v = data[(o * n + j) * ft.inner + i];
             const double2 w = pc.twist[j];
             C wc = mk<C>(w.x, -w.y);
@@ -202,7 +266,7 @@ __global__ void __launch_bounds__(256) k_precond_tau(cplx<R>* __restrict__ data,
         const int ic = e % ft.IC, rest = e / ft.IC;
         const int j = rest % n, ob = rest / n;
         const int64_t o = o0 + ob, i = i0 + ic;
-        if (o < ft.outer && i < ft.inner) {
+        if (o < ft.outer && i < ft.inner && !(cgs && !cgs[o].active)) {
             const double2 w = pc.twist[j];
             C v = cmul(res2[j * nl + ob * ft.IC + ic], mk<C>(w.x, w.y));
             data[(o * n + j) * ft.inner + i] = cscale(v, scale2);
@@ -337,7 +401,8 @@ template <> const float2* tw_of<float>(const FftPlan* p) { return p->tw32; }
 template <> const double2* tw_of<double>(const FftPlan* p) { return p->tw64; }
 
 template <typename R>
-int fft_axis(hmc_ctx* ctx, cplx<R>* data, int64_t outer, int n, int64_t inner, int dir) {
+int fft_axis(hmc_ctx* ctx, cplx<R>* data, int64_t outer, int n, int64_t inner, int dir, const cplx<R>* src,
+             const CgScalars* cgs, int64_t opr) {
     const FftPlan* p = get_plan(ctx, n);
     if (!p) return fail(ctx, HMC_ERR_STATE, "no FFT plan for length " + std::to_string(n));
     FftTile ft = make_tile<R>(outer, n, inner);
@@ -348,25 +413,19 @@ int fft_axis(hmc_ctx* ctx, cplx<R>* data, int64_t outer, int n, int64_t inner, i
         attr[sizeof(R) == 8] = true;
     }
     const int64_t nblk = ((outer + ft.OB - 1) / ft.OB) * ft.nib;
-    k_fft<R><<<(unsigned)nblk, 256, sm, ctx->stream>>>(data, ft, stage_plan(p), tw_of<R>(p), dir,
-                                                      (R)(1.0 / std::sqrt((double)n)));
+    k_fft<R><<<(unsigned)nblk, 256, sm, ctx->stream>>>(src ? src : data, data, ft, stage_plan(p), tw_of<R>(p), dir,
+                                                      (R)(1.0 / std::sqrt((double)n)), cgs, opr > 0 ? opr : 1);
     HMC_LAUNCH(ctx, "k_fft");
     return HMC_OK;
 }
-template int fft_axis<float>(hmc_ctx*, float2*, int64_t, int, int64_t, int);
-template int fft_axis<double>(hmc_ctx*, double2*, int64_t, int, int64_t, int);
+template int fft_axis<float>(hmc_ctx*, float2*, int64_t, int, int64_t, int, const float2*, const CgScalars*, int64_t);
+template int fft_axis<double>(hmc_ctx*, double2*, int64_t, int, int64_t, int, const double2*, const CgScalars*,
+                              int64_t);
 
-// y = P x: copy to y, x and y FFTs forward, the fused tau pass, x and y FFTs inverse.
+// The fused tau pass of the preconditioner on data [nrhs][Nt][L * L * 4] (Fourier space in x, y).
 template <typename R>
-int launch_precond(hmc_ctx* ctx, const Lat& lat, const cplx<R>* x, cplx<R>* y, int nrhs) {
+int precond_tau(hmc_ctx* ctx, const Lat& lat, cplx<R>* y, int nrhs, const CgScalars* cgs) {
     const int L = lat.L, Nt = lat.Nt;
-    const int64_t n4 = 4 * lat.V * (int64_t)nrhs;
-    if (x != y) HMC_CUDA(ctx, cudaMemcpyAsync(y, x, n4 * sizeof(cplx<R>), cudaMemcpyDeviceToDevice, ctx->stream));
-    int rc;
-    // forward along x then y (unitary)
-    if ((rc = fft_axis<R>(ctx, y, (int64_t)nrhs * Nt * L, L, 4, -1))) return rc;
-    if ((rc = fft_axis<R>(ctx, y, (int64_t)nrhs * Nt, L, 4 * (int64_t)L, -1))) return rc;
-    // tau pass
     const FftPlan* p = get_plan(ctx, Nt);
     PcTables* pt = get_pc(ctx, L, Nt);
     if (!p || !pt) return fail(ctx, HMC_ERR_STATE, "no preconditioner plan for this lattice");
@@ -384,22 +443,74 @@ int launch_precond(hmc_ctx* ctx, const Lat& lat, const cplx<R>* x, cplx<R>* y, i
     pc.twist = pt->twist;
     FftTile ft = make_tile<R>(nrhs, Nt, 4 * (int64_t)L * L);
     const size_t sm = 2 * (size_t)Nt * ft.OB * ft.IC * sizeof(cplx<R>);
-    static bool attr[2] = {false, false};
-    if (!attr[sizeof(R) == 8]) {
+    static bool attr = false;
+    if (!attr) {
         HMC_CUDA(ctx, cudaFuncSetAttribute(k_precond_tau<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-        attr[sizeof(R) == 8] = true;
+        attr = true;
     }
     const int64_t nblk = ((ft.outer + ft.OB - 1) / ft.OB) * ft.nib;
     k_precond_tau<R><<<(unsigned)nblk, 256, sm, ctx->stream>>>(y, ft, stage_plan(p), tw_of<R>(p), pc,
-                                                              (R)(1.0 / (double)Nt));
+                                                              (R)(1.0 / (double)Nt), cgs);
     HMC_LAUNCH(ctx, "k_precond_tau");
-    // inverse along y then x
+    return HMC_OK;
+}
+
+// y = P x: FFT along x (reading x, writing y), along y, the fused tau pass, inverse y and x.
+template <typename R>
+int launch_precond(hmc_ctx* ctx, const Lat& lat, const cplx<R>* x, cplx<R>* y, int nrhs) {
+    const int L = lat.L, Nt = lat.Nt;
+    int rc;
+    if ((rc = fft_axis<R>(ctx, y, (int64_t)nrhs * Nt * L, L, 4, -1, x))) return rc;
+    if ((rc = fft_axis<R>(ctx, y, (int64_t)nrhs * Nt, L, 4 * (int64_t)L, -1))) return rc;
+    if ((rc = precond_tau<R>(ctx, lat, y, nrhs, nullptr))) return rc;
     if ((rc = fft_axis<R>(ctx, y, (int64_t)nrhs * Nt, L, 4 * (int64_t)L, +1))) return rc;
     if ((rc = fft_axis<R>(ctx, y, (int64_t)nrhs * Nt * L, L, 4, +1))) return rc;
     return HMC_OK;
 }
 template int launch_precond<float>(hmc_ctx*, const Lat&, const float2*, float2*, int);
 template int launch_precond<double>(hmc_ctx*, const Lat&, const double2*, double2*, int);
+
+// One preconditioned-CG vector step for every active RHS (see cg.cu): x += alpha p,
+// r -= alpha q with partial ||r||^2 into part_r2, z = P r with partial <r, z> into part_rz.
+// Both partial arrays hold rows of *nblk_out entries per RHS.
+template <typename R>
+int launch_cg_update_precond(hmc_ctx* ctx, const Lat& lat, cplx<R>* x, cplx<R>* r, const cplx<R>* p,
+                             const cplx<R>* q, cplx<R>* z, int nrhs, const CgScalars* cgs, double* part_r2,
+                             double* part_rz, int* nblk_out) {
+    const int L = lat.L, Nt = lat.Nt;
+    const FftPlan* pl = get_plan(ctx, L);
+    if (!pl) return fail(ctx, HMC_ERR_STATE, "no FFT plan for length " + std::to_string(L));
+    const int64_t rows = (int64_t)Nt * L;
+    const int want = (sizeof(R) == 8 ? 2048 : 4096) / L / 4;
+    int OB = 1;
+    while (OB * 2 <= (want < 1 ? 1 : want)) OB *= 2;
+    const int64_t nblk = (rows + OB - 1) / OB;
+    if (nblk * nrhs > ctx->part_cap / 2) return fail(ctx, HMC_ERR_ARG, "cg update: reduction buffer too small");
+    const size_t sm = 2 * (size_t)L * OB * 4 * sizeof(cplx<R>);
+    static bool attr = false;
+    if (!attr) {
+        HMC_CUDA(ctx, cudaFuncSetAttribute(k_fft_x_cg<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        HMC_CUDA(ctx, cudaFuncSetAttribute(k_fft_x_cg<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        attr = true;
+    }
+    const dim3 grid((unsigned)nblk, nrhs);
+    const StagePlan sp = stage_plan(pl);
+    k_fft_x_cg<R, 1><<<grid, 256, sm, ctx->stream>>>(nullptr, z, x, r, p, q, rows, OB, sp, tw_of<R>(pl), cgs, part_r2);
+    HMC_LAUNCH(ctx, "k_fft_x_cg<1>");
+    int rc;
+    if ((rc = fft_axis<R>(ctx, z, (int64_t)nrhs * Nt, L, 4 * (int64_t)L, -1, nullptr, cgs, Nt))) return rc;
+    if ((rc = precond_tau<R>(ctx, lat, z, nrhs, cgs))) return rc;
+    if ((rc = fft_axis<R>(ctx, z, (int64_t)nrhs * Nt, L, 4 * (int64_t)L, +1, nullptr, cgs, Nt))) return rc;
+    k_fft_x_cg<R, 2><<<grid, 256, sm, ctx->stream>>>(z, z, nullptr, r, nullptr, nullptr, rows, OB, sp, tw_of<R>(pl), cgs,
+                                                      part_rz);
+    HMC_LAUNCH(ctx, "k_fft_x_cg<2>");
+    *nblk_out = (int)nblk;
+    return HMC_OK;
+}
+template int launch_cg_update_precond<float>(hmc_ctx*, const Lat&, float2*, float2*, const float2*, const float2*,
+                                             float2*, int, const CgScalars*, double*, double*, int*);
+template int launch_cg_update_precond<double>(hmc_ctx*, const Lat&, double2*, double2*, const double2*,
+                                              const double2*, double2*, int, const CgScalars*, double*, double*, int*);
 
 // ---- metric -----------------------------------------------------------------------------
 __global__ void k_pack_real(const double* __restrict__ in, double2* __restrict__ out, int64_t n) {

@@ -145,7 +145,7 @@ template <typename T> static int dalloc(hmc_ctx* ctx, T** p, int64_t count) {
 }
 
 static void free_all(hmc_ctx* ctx) {
-    void* ps[] = {ctx->d_r64, ctx->d_p64, ctx->d_q64, ctx->d_z64, ctx->d_X, ctx->d_pf, ctx->d_chi,
+    void* ps[] = {ctx->d_r64, ctx->d_p64, ctx->d_p64b, ctx->d_p32b, ctx->d_q64, ctx->d_z64, ctx->d_X, ctx->d_pf, ctx->d_chi,
                   ctx->d_x32, ctx->d_r32, ctx->d_p32, ctx->d_q32, ctx->d_z32, ctx->d_phi32,
                   ctx->d_phi_save, ctx->d_pi, ctx->d_F, ctx->d_vel, ctx->d_z, ctx->d_fft,
                   ctx->d_part, ctx->d_red, ctx->d_cg, ctx->d_u32};
@@ -223,6 +223,7 @@ int hmc_init(const hmc_params* p, int n_chains, const hmc_chain* chains, void* c
     if (need_m > ctx->part_cap) ctx->part_cap = need_m;
     const bool mixed = p->solver_mode == HMC_SOLVER_MIXED;
     if ((rc = dalloc(ctx, &ctx->d_r64, nf)) || (rc = dalloc(ctx, &ctx->d_p64, mixed ? 1 : nf)) ||
+        (rc = dalloc(ctx, &ctx->d_p64b, mixed ? 1 : nf)) || (rc = dalloc(ctx, &ctx->d_p32b, mixed ? nf : 1)) ||
         (rc = dalloc(ctx, &ctx->d_q64, nf)) || (rc = dalloc(ctx, &ctx->d_z64, mixed ? 1 : nf)) ||
         (rc = dalloc(ctx, &ctx->d_X, nf)) || (rc = dalloc(ctx, &ctx->d_pf, nf)) ||
         (rc = dalloc(ctx, &ctx->d_chi, nf)) || (rc = dalloc(ctx, &ctx->d_x32, mixed ? nf : 1)) ||

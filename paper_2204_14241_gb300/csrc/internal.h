@@ -65,6 +65,7 @@ struct hmc_ctx {
     // fermion workspace (complex, K * 4 * vmax entries each)
     double2* d_r64 = nullptr;     // FP64 residual / true residual
     double2* d_p64 = nullptr;
+    double2* d_p64b = nullptr;    // second direction buffer (ping-pong)
     double2* d_q64 = nullptr;
     double2* d_z64 = nullptr;
     double2* d_X = nullptr;       // solve output used by force
@@ -73,6 +74,7 @@ struct hmc_ctx {
     float2* d_x32 = nullptr;
     float2* d_r32 = nullptr;
     float2* d_p32 = nullptr;
+    float2* d_p32b = nullptr;
     float2* d_q32 = nullptr;
     float2* d_z32 = nullptr;
     float* d_phi32 = nullptr;     // 3 * vmax
@@ -120,10 +122,12 @@ int launch_apply_D(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x,
                    int dagger, int nrhs);
 // y = A x; if part != nullptr, per-block partial sums of ||D^dag x||^2 are written to
 // part[k * nblk + b] and *nblk_out receives nblk.
-// cgs (may be null): right-hand sides whose cgs[k].active is 0 are skipped.
+// cgs (may be null): right-hand sides whose cgs[k].active is 0 are skipped. With pnew set,
+// the operand is p = x + cgs[k].beta * pold, written to pnew for every site, and y = A p.
 template <typename R>
 int launch_apply_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x, cplx<R>* y,
-                   int nrhs, double* part, int* nblk_out, const CgScalars* cgs = nullptr);
+                   int nrhs, double* part, int* nblk_out, const CgScalars* cgs = nullptr,
+                   const cplx<R>* pold = nullptr, cplx<R>* pnew = nullptr);
 // fermion (+ boson) force and the action pieces, see force() in hmc.h.
 int launch_force(hmc_ctx* ctx, const Lat& lat, double r, const double* phi, const double2* X,
                  const double2* pf, int nrhs, double* F, int include_boson, double* part,
@@ -135,12 +139,21 @@ int launch_boson(hmc_ctx* ctx, const Lat& lat, double r, const double* phi, doub
 FftPlan* get_plan(hmc_ctx* ctx, int n);
 int build_plans(hmc_ctx* ctx);
 void free_plans(hmc_ctx* ctx);
-// in-place unitary FFT of complex data viewed as [outer][n][inner] along the middle axis;
-// dir = -1 forward (e^{-2 pi i}), +1 inverse.
+// unitary FFT of complex data viewed as [outer][n][inner] along the middle axis, in place
+// (src == nullptr) or from src into data; dir = -1 forward (e^{-2 pi i}), +1 inverse.
+// cgs (may be null) with opr = outer indices per right-hand side: lines of inactive RHS are
+// neither read nor written.
 template <typename R>
-int fft_axis(hmc_ctx* ctx, cplx<R>* data, int64_t outer, int n, int64_t inner, int dir);
+int fft_axis(hmc_ctx* ctx, cplx<R>* data, int64_t outer, int n, int64_t inner, int dir,
+             const cplx<R>* src = nullptr, const CgScalars* cgs = nullptr, int64_t opr = 1);
 template <typename R>
 int launch_precond(hmc_ctx* ctx, const Lat& lat, const cplx<R>* x, cplx<R>* y, int nrhs);
+// x += alpha p, r -= alpha q, z = P r for every active RHS with partial sums of ||r||^2 and
+// <r, z> (rows of *nblk_out entries per RHS in part_r2 / part_rz).
+template <typename R>
+int launch_cg_update_precond(hmc_ctx* ctx, const Lat& lat, cplx<R>* x, cplx<R>* r, const cplx<R>* p,
+                             const cplx<R>* q, cplx<R>* z, int nrhs, const CgScalars* cgs, double* part_r2,
+                             double* part_rz, int* nblk_out);
 int metric_op(hmc_ctx* ctx, const Lat& lat, int op, const double* sig, const double* in,
               double* out, double eps, double* scalar_dev);
 

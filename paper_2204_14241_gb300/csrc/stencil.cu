@@ -92,12 +92,17 @@ struct ATile {
     int ntx, nty, nchunk; // tiles along x, y and chunks along t
 };
 
+// With pnew != nullptr the kernel also performs the CG direction update: the operand is
+// p = x + beta_k * pold (x holding z), formed as it is loaded, and the block writes p for the
+// sites it owns (tile interior, slices [t0, t1)) to pnew; y = A p. pold and pnew must differ.
 template <typename R>
 __global__ void __launch_bounds__(256) k_apply_A(Lat lat, Coef<R> cf, ATile tl,
                                                  const R* __restrict__ phi,
                                                  const Site<R>* __restrict__ x,
                                                  Site<R>* __restrict__ y, double* __restrict__ part,
-                                                 const CgScalars* __restrict__ cgs) {
+                                                 const CgScalars* __restrict__ cgs,
+                                                 const Site<R>* __restrict__ pold,
+                                                 Site<R>* __restrict__ pnew) {
     if (cgs && !cgs[blockIdx.z].active) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int TX = tl.TX, TY = tl.TY;
@@ -119,18 +124,33 @@ __global__ void __launch_bounds__(256) k_apply_A(Lat lat, Coef<R> cf, ATile tl,
     const int k = blockIdx.z;
     const Site<R>* xk = x + k * V;
     Site<R>* yk = y + k * V;
+    const R beta = pnew ? (R)cgs[k].beta : R(0);
+    const Site<R>* pok = pnew ? pold + k * V : nullptr;
+    Site<R>* pnk = pnew ? pnew + k * V : nullptr;
 
     auto gx = [&](int i) { int v = (x0 + i) % L; return v < 0 ? v + L : v; };
     auto gy = [&](int j) { int v = (y0 + j) % L; return v < 0 ? v + L : v; };
     // x at slice t on the two-site ring into buffer dst (halo2 coordinates); ring1only limits
     // the load to the one-site ring
-    auto load_x = [&](uint4* dst, int t, bool ring1only) {
+    auto load_x = [&](uint4* dst, int t, bool ring1only, bool own) {
         const int64_t base = (int64_t)t * LL;
         for (int i = threadIdx.x; i < N2; i += blockDim.x) {
             const int hx = i % HX2, hy = i / HX2;
             if (ring1only && (hx == 0 || hy == 0 || hx == HX2 - 1 || hy == HY2 - 1)) continue;
             const int X = gx(hx - 2), Y = gy(hy - 2);
-            sm_store<R>(dst, N2, i, load_site(xk + base + (int64_t)Y * L + X));
+            const int64_t s = base + (int64_t)Y * L + X;
+            Site<R> v = load_site(xk + s);
+            if (pnew) {
+                const Site<R> po = load_site(pok + s);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    v.c[q].x += beta * po.c[q].x;
+                    v.c[q].y += beta * po.c[q].y;
+                }
+                if (own && hx >= 2 && hy >= 2 && hx < TX + 2 && hy < TY + 2 && x0 + hx - 2 < L && y0 + hy - 2 < L)
+                    store_site(pnk + s, v);
+            }
+            sm_store<R>(dst, N2, i, v);
         }
     };
     auto load_phi = [&](int t) {
@@ -160,8 +180,8 @@ __global__ void __launch_bounds__(256) k_apply_A(Lat lat, Coef<R> cf, ATile tl,
     };
 
     // prologue: t_(t0) on the ring
-    load_x(xa, t0, false);
-    load_x(xb, tprev(t0, Nt), true);
+    load_x(xa, t0, false, true);
+    load_x(xb, tprev(t0, Nt), true, false);
     load_phi(t0);
     __syncthreads();
     make_t(ta, xa, xb, t0);
@@ -171,7 +191,7 @@ __global__ void __launch_bounds__(256) k_apply_A(Lat lat, Coef<R> cf, ATile tl,
     double acc = 0.0;
     for (int t = t0; t < t1; ++t) {
         const int tp = tnext(t, Nt);
-        load_x(xn, tp, false);
+        load_x(xn, tp, false, t + 1 < t1);
         load_phi(tp);
         __syncthreads();
         make_t(tn, xn, xc, tp);
@@ -241,8 +261,10 @@ static size_t a_smem_bytes(const ATile& t) {
 
 template <typename R>
 int launch_apply_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x, cplx<R>* y,
-                   int nrhs, double* part, int* nblk_out, const CgScalars* cgs) {
+                   int nrhs, double* part, int* nblk_out, const CgScalars* cgs,
+                   const cplx<R>* pold, cplx<R>* pnew) {
     if (nrhs <= 0) return HMC_OK;
+    if (pnew && (!cgs || !pold || pold == pnew)) return fail(ctx, HMC_ERR_ARG, "apply_A: bad direction-update buffers");
     ATile tl = choose_tile(ctx, lat, nrhs, sizeof(Site<R>));
     const size_t sm = a_smem_bytes<R>(tl);
     static bool attr_set[2] = {false, false};
@@ -255,13 +277,17 @@ int launch_apply_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x,
         return fail(ctx, HMC_ERR_ARG, "apply_A: reduction buffer too small");
     k_apply_A<R><<<grid, 256, sm, ctx->stream>>>(lat, make_coef<R>(ctx->p), tl, phi,
                                                  reinterpret_cast<const Site<R>*>(x),
-                                                 reinterpret_cast<Site<R>*>(y), part, cgs);
+                                                 reinterpret_cast<Site<R>*>(y), part, cgs,
+                                                 reinterpret_cast<const Site<R>*>(pold),
+                                                 reinterpret_cast<Site<R>*>(pnew));
     HMC_LAUNCH(ctx, "k_apply_A");
     if (nblk_out) *nblk_out = grid.x * grid.y;
     return HMC_OK;
 }
-template int launch_apply_A<float>(hmc_ctx*, const Lat&, const float*, const float2*, float2*, int, double*, int*, const CgScalars*);
-template int launch_apply_A<double>(hmc_ctx*, const Lat&, const double*, const double2*, double2*, int, double*, int*, const CgScalars*);
+template int launch_apply_A<float>(hmc_ctx*, const Lat&, const float*, const float2*, float2*, int, double*, int*,
+                                   const CgScalars*, const float2*, float2*);
+template int launch_apply_A<double>(hmc_ctx*, const Lat&, const double*, const double2*, double2*, int, double*, int*,
+                                    const CgScalars*, const double2*, double2*);
 
 // ---------------------------------------------------------------------------------------
 // Boson pieces: -dS_B/dphi and the S_B density (forward differences, see oracle reading).
