@@ -332,6 +332,29 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile_solve(args):
+    """A capture-sized sample of the workload for ncu: on the full lattice, one 8-RHS
+    preconditioned solve cut at a fixed iteration count, run twice (the second is the one to
+    capture), plus one fused A apply. Prints the solve statistics."""
+    import torch
+    from paper_2204_14241_gb300.hmc import Context
+    from paper_2204_14241_gb300 import inputs as I
+    phi_np, _ = synthetic_inputs(chain_seed(args.seed, 0))
+    phi = torch.from_numpy(phi_np).cuda()
+    b = torch.from_numpy(I.fermion_noise(2, NRHS, L, NT)).cuda()
+    ctx = Context(L, NT, solver="mixed", nrhs_max=NRHS, cg_tol=TOL, **COUPLINGS)
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st = ctx.cg_solve(phi, b, precond=True, maxit=args.profile_solve, raise_on_noconv=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_solve": args.profile_solve, "seconds": time.perf_counter() - t0, **st}))
+    x = b.to(torch.complex64)
+    ctx.apply_MdagM(phi.float(), x)
+    torch.cuda.synchronize()
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -340,8 +363,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-solve", type=int, default=0,
+                    help="run only a capture-sized sample: one solve cut at this many iterations")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_solve:
+        run_profile_solve(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

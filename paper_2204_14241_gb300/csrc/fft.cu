@@ -9,6 +9,7 @@
 #include <cmath>
 
 #include "internal.h"
+#include "fft_ct.h"
 
 namespace hmc {
 
@@ -340,6 +341,19 @@ static int add_pc(hmc_ctx* ctx, int L, int Nt) {
     HMC_CUDA(ctx, cudaMemcpy(t.cosk, ck.data(), L * sizeof(double), cudaMemcpyHostToDevice));
     HMC_CUDA(ctx, cudaMemcpy(t.eitw, ew.data(), Nt * sizeof(double2), cudaMemcpyHostToDevice));
     HMC_CUDA(ctx, cudaMemcpy(t.twist, tw.data(), Nt * sizeof(double2), cudaMemcpyHostToDevice));
+    std::vector<float> ck32(L);
+    std::vector<float2> ew32(Nt), tw32(Nt);
+    for (int m = 0; m < L; ++m) ck32[m] = (float)ck[m];
+    for (int n = 0; n < Nt; ++n) {
+        ew32[n] = make_float2((float)ew[n].x, (float)ew[n].y);
+        tw32[n] = make_float2((float)tw[n].x, (float)tw[n].y);
+    }
+    HMC_CUDA(ctx, cudaMalloc(&t.cosk32, L * sizeof(float)));
+    HMC_CUDA(ctx, cudaMalloc(&t.eitw32, Nt * sizeof(float2)));
+    HMC_CUDA(ctx, cudaMalloc(&t.twist32, Nt * sizeof(float2)));
+    HMC_CUDA(ctx, cudaMemcpy(t.cosk32, ck32.data(), L * sizeof(float), cudaMemcpyHostToDevice));
+    HMC_CUDA(ctx, cudaMemcpy(t.eitw32, ew32.data(), Nt * sizeof(float2), cudaMemcpyHostToDevice));
+    HMC_CUDA(ctx, cudaMemcpy(t.twist32, tw32.data(), Nt * sizeof(float2), cudaMemcpyHostToDevice));
     ctx->pcs.push_back(t);
     return HMC_OK;
 }
@@ -364,6 +378,9 @@ void free_plans(hmc_ctx* ctx) {
         cudaFree(t.cosk);
         cudaFree(t.eitw);
         cudaFree(t.twist);
+        cudaFree(t.cosk32);
+        cudaFree(t.eitw32);
+        cudaFree(t.twist32);
     }
     ctx->pcs.clear();
 }
@@ -403,6 +420,9 @@ template <> const double2* tw_of<double>(const FftPlan* p) { return p->tw64; }
 template <typename R>
 int fft_axis(hmc_ctx* ctx, cplx<R>* data, int64_t outer, int n, int64_t inner, int dir, const cplx<R>* src,
              const CgScalars* cgs, int64_t opr) {
+    if constexpr (sizeof(R) == 4) {
+        if (fftc_can(n, inner)) return fftc_axis(ctx, data, outer, n, inner, dir, src, cgs, opr);
+    }
     const FftPlan* p = get_plan(ctx, n);
     if (!p) return fail(ctx, HMC_ERR_STATE, "no FFT plan for length " + std::to_string(n));
     FftTile ft = make_tile<R>(outer, n, inner);
@@ -429,6 +449,9 @@ int precond_tau(hmc_ctx* ctx, const Lat& lat, cplx<R>* y, int nrhs, const CgScal
     const FftPlan* p = get_plan(ctx, Nt);
     PcTables* pt = get_pc(ctx, L, Nt);
     if (!p || !pt) return fail(ctx, HMC_ERR_STATE, "no preconditioner plan for this lattice");
+    if constexpr (sizeof(R) == 4) {
+        if (fftc_can(Nt, 4 * (int64_t)L * L)) return fftc_precond_tau(ctx, lat, y, nrhs, cgs, pt);
+    }
     PrecondCoef pc;
     pc.dtau = ctx->p.dtau;
     for (int a = 0; a < 2; ++a) {
@@ -493,11 +516,23 @@ int launch_cg_update_precond(hmc_ctx* ctx, const Lat& lat, cplx<R>* x, cplx<R>* 
         HMC_CUDA(ctx, cudaFuncSetAttribute(k_fft_x_cg<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
         attr = true;
     }
+    int rc;
+    if constexpr (sizeof(R) == 4) {
+        if (fftc_supported(L)) {
+            if ((rc = fftc_x_cg(ctx, lat, kFftcXUpd, nullptr, z, x, r, p, q, nrhs, cgs, part_r2, nblk_out))) return rc;
+            if ((rc = fft_axis<R>(ctx, z, (int64_t)nrhs * Nt, L, 4 * (int64_t)L, -1, nullptr, cgs, Nt))) return rc;
+            if ((rc = precond_tau<R>(ctx, lat, z, nrhs, cgs))) return rc;
+            if ((rc = fft_axis<R>(ctx, z, (int64_t)nrhs * Nt, L, 4 * (int64_t)L, +1, nullptr, cgs, Nt))) return rc;
+            int nb2 = 0;
+            if ((rc = fftc_x_cg(ctx, lat, kFftcXDot, z, z, nullptr, r, nullptr, nullptr, nrhs, cgs, part_rz, &nb2)))
+                return rc;
+            return HMC_OK;
+        }
+    }
     const dim3 grid((unsigned)nblk, nrhs);
     const StagePlan sp = stage_plan(pl);
     k_fft_x_cg<R, 1><<<grid, 256, sm, ctx->stream>>>(nullptr, z, x, r, p, q, rows, OB, sp, tw_of<R>(pl), cgs, part_r2);
     HMC_LAUNCH(ctx, "k_fft_x_cg<1>");
-    int rc;
     if ((rc = fft_axis<R>(ctx, z, (int64_t)nrhs * Nt, L, 4 * (int64_t)L, -1, nullptr, cgs, Nt))) return rc;
     if ((rc = precond_tau<R>(ctx, lat, z, nrhs, cgs))) return rc;
     if ((rc = fft_axis<R>(ctx, z, (int64_t)nrhs * Nt, L, 4 * (int64_t)L, +1, nullptr, cgs, Nt))) return rc;

@@ -22,6 +22,9 @@ struct PcTables {
     double* cosk = nullptr;     // cos(2 pi m / L)
     double2* eitw = nullptr;    // e^{i w_n}, w_n = (2n + 1) pi / Nt
     double2* twist = nullptr;   // e^{i pi t / Nt}
+    float* cosk32 = nullptr;    // float copies for the FP32 path
+    float2* eitw32 = nullptr;
+    float2* twist32 = nullptr;
 };
 
 struct ChainDesc {

@@ -65,9 +65,11 @@ template int launch_apply_D<double>(hmc_ctx*, const Lat&, const double*, const d
 // Fused y = D (D^dagger x). A block owns a TX x TY tile of sites and marches through a
 // chunk of time slices. For output slice t it needs t_ = D^dagger x on the tile plus a
 // one-site ring at slice t and on the tile at slice t+1; t_ at slice t+1 in turn needs x at
-// t+1 on a two-site ring and x at t on the one-site ring. Each step loads x(t+1) once into
-// shared memory, computes t_(t+1) on the ring, and emits y(t); x and t_ are double
-// buffered. Shared memory holds each site as 16-byte planes (conflict-free vector access).
+// t+1 on a two-site ring and x at t on the one-site ring. Each step stores x(t+1) (held in
+// registers) into shared memory, issues the global loads of x(t+2) into registers so that
+// they are in flight while it computes t_(t+1) on the ring and y(t) on the tile. x and t_
+// are double buffered in shared memory, phi triple buffered. Shared memory holds each site
+// as 16-byte planes (conflict-free vector access).
 template <typename R> struct Planes {
     static constexpr int NP = sizeof(Site<R>) / 16;   // 2 for float, 4 for double
 };
@@ -92,18 +94,22 @@ struct ATile {
     int ntx, nty, nchunk; // tiles along x, y and chunks along t
 };
 
+constexpr int kAThreads = 256;
+template <typename R> struct APf { static constexpr int N = sizeof(R) == 4 ? 2 : 1; };  // halo sites per thread
+
 // With pnew != nullptr the kernel also performs the CG direction update: the operand is
 // p = x + beta_k * pold (x holding z), formed as it is loaded, and the block writes p for the
 // sites it owns (tile interior, slices [t0, t1)) to pnew; y = A p. pold and pnew must differ.
 template <typename R>
-__global__ void __launch_bounds__(256) k_apply_A(Lat lat, Coef<R> cf, ATile tl,
-                                                 const R* __restrict__ phi,
-                                                 const Site<R>* __restrict__ x,
-                                                 Site<R>* __restrict__ y, double* __restrict__ part,
-                                                 const CgScalars* __restrict__ cgs,
-                                                 const Site<R>* __restrict__ pold,
-                                                 Site<R>* __restrict__ pnew) {
+__global__ void __launch_bounds__(kAThreads, sizeof(R) == 4 ? 3 : 2) k_apply_A(Lat lat, Coef<R> cf, ATile tl,
+                                                       const R* __restrict__ phi,
+                                                       const Site<R>* __restrict__ x,
+                                                       Site<R>* __restrict__ y, double* __restrict__ part,
+                                                       const CgScalars* __restrict__ cgs,
+                                                       const Site<R>* __restrict__ pold,
+                                                       Site<R>* __restrict__ pnew) {
     if (cgs && !cgs[blockIdx.z].active) return;
+    constexpr int NPF = APf<R>::N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int TX = tl.TX, TY = tl.TY;
     const int HX2 = TX + 4, HY2 = TY + 4, N2 = HX2 * HY2;
@@ -112,8 +118,8 @@ __global__ void __launch_bounds__(256) k_apply_A(Lat lat, Coef<R> cf, ATile tl,
     uint4* xb = xa + Planes<R>::NP * N2;
     uint4* ta = xb + Planes<R>::NP * N2;
     uint4* tb = ta + Planes<R>::NP * N1;
-    R* ph = reinterpret_cast<R*>(tb + Planes<R>::NP * N1);   // [3][N1]
-    __shared__ double red[8];
+    R* phb = reinterpret_cast<R*>(tb + Planes<R>::NP * N1);   // 3 buffers of [3][N1]
+    __shared__ double red[kAThreads / 32];
 
     const int L = lat.L, Nt = lat.Nt;
     const int64_t V = lat.V, LL = (int64_t)L * L;
@@ -130,43 +136,61 @@ __global__ void __launch_bounds__(256) k_apply_A(Lat lat, Coef<R> cf, ATile tl,
 
     auto gx = [&](int i) { int v = (x0 + i) % L; return v < 0 ? v + L : v; };
     auto gy = [&](int j) { int v = (y0 + j) % L; return v < 0 ? v + L : v; };
-    // x at slice t on the two-site ring into buffer dst (halo2 coordinates); ring1only limits
-    // the load to the one-site ring
-    auto load_x = [&](uint4* dst, int t, bool ring1only, bool own) {
+    auto ring2 = [&](int i) { const int hx = i % HX2, hy = i / HX2;
+                              return hx == 0 || hy == 0 || hx == HX2 - 1 || hy == HY2 - 1; };
+
+    // register prefetch of one slice: the halo2 sites tid + j * kAThreads, and phi on halo1
+    Site<R> rz[NPF], rp[NPF];
+    R rph[NPF][3];
+    auto fetch = [&](int t) {
         const int64_t base = (int64_t)t * LL;
-        for (int i = threadIdx.x; i < N2; i += blockDim.x) {
-            const int hx = i % HX2, hy = i / HX2;
-            if (ring1only && (hx == 0 || hy == 0 || hx == HX2 - 1 || hy == HY2 - 1)) continue;
-            const int X = gx(hx - 2), Y = gy(hy - 2);
-            const int64_t s = base + (int64_t)Y * L + X;
-            Site<R> v = load_site(xk + s);
-            if (pnew) {
-                const Site<R> po = load_site(pok + s);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    v.c[q].x += beta * po.c[q].x;
-                    v.c[q].y += beta * po.c[q].y;
-                }
-                if (own && hx >= 2 && hy >= 2 && hx < TX + 2 && hy < TY + 2 && x0 + hx - 2 < L && y0 + hy - 2 < L)
-                    store_site(pnk + s, v);
+        for (int j = 0; j < NPF; ++j) {
+            const int i = threadIdx.x + j * kAThreads;
+            if (i < N2) {
+                const int64_t s = base + (int64_t)gy(i / HX2 - 2) * L + gx(i % HX2 - 2);
+                rz[j] = load_site(xk + s);
+                if (pnew) rp[j] = load_site(pok + s);
             }
-            sm_store<R>(dst, N2, i, v);
+            if (i < N1) {
+                const int64_t s = base + (int64_t)gy(i / HX1 - 1) * L + gx(i % HX1 - 1);
+                rph[j][0] = __ldg(phi + s);
+                rph[j][1] = __ldg(phi + V + s);
+                rph[j][2] = __ldg(phi + 2 * V + s);
+            }
         }
     };
-    auto load_phi = [&](int t) {
+    // store the prefetched slice t (p = z + beta pold, written to pnew where owned)
+    auto commit = [&](uint4* dst, R* ph, int t, bool own, bool ring1only) {
         const int64_t base = (int64_t)t * LL;
-        for (int i = threadIdx.x; i < N1; i += blockDim.x) {
-            const int hx = i % HX1, hy = i / HX1;
-            const int64_t s = base + (int64_t)gy(hy - 1) * L + gx(hx - 1);
-            ph[i] = __ldg(phi + s);
-            ph[N1 + i] = __ldg(phi + V + s);
-            ph[2 * N1 + i] = __ldg(phi + 2 * V + s);
+#pragma unroll
+        for (int j = 0; j < NPF; ++j) {
+            const int i = threadIdx.x + j * kAThreads;
+            if (i < N2 && !(ring1only && ring2(i))) {
+                Site<R> v = rz[j];
+                if (pnew) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        v.c[q].x += beta * rp[j].c[q].x;
+                        v.c[q].y += beta * rp[j].c[q].y;
+                    }
+                    const int hx = i % HX2, hy = i / HX2;
+                    if (own && hx >= 2 && hy >= 2 && hx < TX + 2 && hy < TY + 2 && x0 + hx - 2 < L && y0 + hy - 2 < L)
+                        store_site(pnk + base + (int64_t)(y0 + hy - 2) * L + (x0 + hx - 2), v);
+                }
+                sm_store<R>(dst, N2, i, v);
+            }
+            if (i < N1 && ph) {
+                ph[i] = rph[j][0];
+                ph[N1 + i] = rph[j][1];
+                ph[2 * N1 + i] = rph[j][2];
+            }
         }
     };
     // t_(t) = D^dagger x on the one-site ring from x(t) (cur) and x(t-1) (prev)
-    auto make_t = [&](uint4* dst, const uint4* cur, const uint4* prev, int t) {
+    auto make_t = [&](uint4* dst, const uint4* cur, const uint4* prev, const R* ph, int t) {
         const R tsign = (t == 0) ? R(-1) : R(1);   // b(t-1)
-        for (int i = threadIdx.x; i < N1; i += blockDim.x) {
+        for (int i = threadIdx.x; i < N1; i += kAThreads) {
             const int hx = i % HX1, hy = i / HX1;
             const int c = (hy + 1) * HX2 + hx + 1;
             const int X = gx(hx - 1), Y = gy(hy - 1);
@@ -179,27 +203,33 @@ __global__ void __launch_bounds__(256) k_apply_A(Lat lat, Coef<R> cf, ATile tl,
         }
     };
 
-    // prologue: t_(t0) on the ring
-    load_x(xa, t0, false, true);
-    load_x(xb, tprev(t0, Nt), true, false);
-    load_phi(t0);
+    // prologue: x(t0) on the two-site ring, x(t0 - 1) on the one-site ring, t_(t0)
+    fetch(t0);
+    commit(xa, phb, t0, true, false);
+    fetch(tprev(t0, Nt));
+    commit(xb, nullptr, tprev(t0, Nt), false, true);
     __syncthreads();
-    make_t(ta, xa, xb, t0);
+    make_t(ta, xa, xb, phb, t0);
+    fetch(tnext(t0, Nt));
     __syncthreads();
 
     uint4 *xc = xa, *xn = xb, *tc = ta, *tn = tb;
-    double acc = 0.0;
+    int pc = 0;   // phi(t) is in buffer pc of the three at phb
+    float acc = 0.f;
     for (int t = t0; t < t1; ++t) {
         const int tp = tnext(t, Nt);
-        load_x(xn, tp, false, t + 1 < t1);
-        load_phi(tp);
+        const int pn = pc == 2 ? 0 : pc + 1;
+        R* phn = phb + pn * 3 * N1;
+        commit(xn, phn, tp, t + 1 < t1, false);
+        if (t + 1 < t1) fetch(tnext(tp, Nt));
         __syncthreads();
-        make_t(tn, xn, xc, tp);
+        make_t(tn, xn, xc, phn, tp);
         __syncthreads();
         // y(t) = D t_ on the tile
         const R tsign = (t == Nt - 1) ? R(-1) : R(1);   // b(t)
         const int64_t base = (int64_t)t * LL;
-        for (int i = threadIdx.x; i < TX * TY; i += blockDim.x) {
+        const R* ph = phb + pc * 3 * N1;
+        for (int i = threadIdx.x; i < TX * TY; i += kAThreads) {
             const int ix = i % TX, iy = i / TX;
             const int X = x0 + ix, Y = y0 + iy;
             if (X >= L || Y >= L) continue;
@@ -209,21 +239,21 @@ __global__ void __launch_bounds__(256) k_apply_A(Lat lat, Coef<R> cf, ATile tl,
             const Site<R> tcen = sm_load<R>(tc, N1, c);
             Site<R> o = site_op<R>(cf, tcen, sm_load<R>(tc, N1, c - 1), sm_load<R>(tc, N1, c + 1),
                                    sm_load<R>(tc, N1, c - HX1), sm_load<R>(tc, N1, c + HX1),
-                                   sm_load<R>(tn, N1, c), tsign, __ldg(phi + s),
-                                   __ldg(phi + V + s), __ldg(phi + 2 * V + s), eta);
+                                   sm_load<R>(tn, N1, c), tsign, ph[c], ph[N1 + c], ph[2 * N1 + c], eta);
             store_site(yk + s, o);
             if (part) {
                 R n2 = 0;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) n2 += tcen.c[q].x * tcen.c[q].x + tcen.c[q].y * tcen.c[q].y;
-                acc += (double)n2;
+                acc += (float)n2;
             }
         }
         uint4* sw = xc; xc = xn; xn = sw;
         sw = tc; tc = tn; tn = sw;
+        pc = pn;
     }
     if (part) {
-        const double tot = block_sum(acc, red);
+        const double tot = block_sum((double)acc, red);
         if (threadIdx.x == 0)
             part[(int64_t)k * (gridDim.x * gridDim.y) + blockIdx.y * gridDim.x + blockIdx.x] = tot;
     }
@@ -241,6 +271,9 @@ static ATile choose_tile(const hmc_ctx* ctx, const Lat& lat, int nrhs, size_t si
     if (lat.L % 16 == 0 && site_bytes <= 32) t.TX = 16;
     int cap = (site_bytes > 32 ? 128 : 256) / t.TX;
     t.TY = largest_divisor_le(lat.L, cap < 1 ? 1 : cap);
+    const int n2max = (site_bytes > 32 ? 1 : 2) * kAThreads;
+    while ((t.TX + 4) * (t.TY + 4) > n2max && t.TY > 1) t.TY = largest_divisor_le(lat.L, t.TY - 1);
+    while ((t.TX + 4) * (t.TY + 4) > n2max && t.TX > 1) t.TX = largest_divisor_le(lat.L, t.TX - 1);
     t.ntx = (lat.L + t.TX - 1) / t.TX;
     t.nty = (lat.L + t.TY - 1) / t.TY;
     const int64_t tiles = (int64_t)t.ntx * t.nty * nrhs;
@@ -256,7 +289,7 @@ static ATile choose_tile(const hmc_ctx* ctx, const Lat& lat, int nrhs, size_t si
 template <typename R>
 static size_t a_smem_bytes(const ATile& t) {
     const int N2 = (t.TX + 4) * (t.TY + 4), N1 = (t.TX + 2) * (t.TY + 2);
-    return (size_t)2 * N2 * sizeof(Site<R>) + (size_t)2 * N1 * sizeof(Site<R>) + (size_t)3 * N1 * sizeof(R);
+    return (size_t)2 * N2 * sizeof(Site<R>) + (size_t)2 * N1 * sizeof(Site<R>) + (size_t)9 * N1 * sizeof(R);
 }
 
 template <typename R>
@@ -275,7 +308,7 @@ int launch_apply_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x,
     dim3 grid(tl.ntx * tl.nty, tl.nchunk, nrhs);
     if (part && (int64_t)grid.x * grid.y * nrhs > ctx->part_cap)
         return fail(ctx, HMC_ERR_ARG, "apply_A: reduction buffer too small");
-    k_apply_A<R><<<grid, 256, sm, ctx->stream>>>(lat, make_coef<R>(ctx->p), tl, phi,
+    k_apply_A<R><<<grid, kAThreads, sm, ctx->stream>>>(lat, make_coef<R>(ctx->p), tl, phi,
                                                  reinterpret_cast<const Site<R>*>(x),
                                                  reinterpret_cast<Site<R>*>(y), part, cgs,
                                                  reinterpret_cast<const Site<R>*>(pold),
