@@ -73,6 +73,9 @@ typedef struct {
     int nrhs_max;       /* most pseudofermion right-hand sides per call, >= 1 */
     double cg_tol;      /* default relative true-residual tolerance ||b - A x|| / ||b|| */
     int cg_maxit;       /* default iteration cap */
+    int initial_guess;  /* trajectory() force solves: 0 = zero start (default); 1 = chronological
+                           start from the linear extrapolation 2 X_n - X_{n-1} of the trajectory's
+                           previous two solutions (the same stopping test applies either way) */
 } hmc_params;
 
 /* Per-chain lattice (batched chains of uneven sizes). Coupling constants other than r

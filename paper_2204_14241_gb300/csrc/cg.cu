@@ -110,20 +110,23 @@ __global__ void k_cg_beta(CgScalars* cgs, const double* __restrict__ part_r2,
     }
 }
 
-// Initial scalars: b2 = ||b||^2 from part, r2 = r2_max = b2, active = b2 > 0
-__global__ void k_cg_start(CgScalars* cgs, const double* __restrict__ part, int nblk) {
+// Initial scalars: b2 = ||b||^2 from part_b2; r2 = r2_max = ||b - A x0||^2 from part_r2 (or
+// b2 for a zero start). A right-hand side is active unless b = 0 or x0 already meets tol.
+__global__ void k_cg_start(CgScalars* cgs, const double* __restrict__ part_b2, const double* __restrict__ part_r2,
+                           int nblk, double tol2) {
     __shared__ double red[8];
     const int k = blockIdx.x;
-    const double b2 = row_sum(part + (int64_t)k * nblk, nblk, red);
+    const double b2 = row_sum(part_b2 + (int64_t)k * nblk, nblk, red);
+    const double r2 = part_r2 ? row_sum(part_r2 + (int64_t)k * nblk, nblk, red) : b2;
     if (threadIdx.x == 0) {
         CgScalars c = {};
         c.b2 = b2;
-        c.r2 = b2;
-        c.r2_max = b2;
-        c.r2true = b2;
-        c.active = b2 > 0.0 ? 1 : 0;
-        c.nonfinite = isfinite(b2) ? 0 : 1;
-        if (!isfinite(b2)) c.active = 0;
+        c.r2 = r2;
+        c.r2_max = r2;
+        c.r2true = r2;
+        c.active = (b2 > 0.0 && r2 > tol2 * b2) ? 1 : 0;
+        c.nonfinite = (isfinite(b2) && isfinite(r2)) ? 0 : 1;
+        if (c.nonfinite) c.active = 0;
         cgs[k] = c;
     }
 }
@@ -212,7 +215,7 @@ __global__ void k_phi_to32(const double* __restrict__ a, float* __restrict__ b, 
 // ---- host driver ---------------------------------------------------------------------------
 template <typename R>
 static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2* b, double2* x,
-               int nrhs, double tol, int maxit, int precond, hmc_cg_stats* st) {
+               int nrhs, double tol, int maxit, int precond, hmc_cg_stats* st, bool use_x0) {
     constexpr bool kMixed = sizeof(R) == 4;
     using C = cplx<R>;
     cudaStream_t sm = ctx->stream;
@@ -239,14 +242,26 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
         zv = precond ? ctx->d_z64 : ctx->d_r64;
         phiR = phi64;
     }
-    HMC_CUDA(ctx, cudaMemsetAsync(x, 0, nrhs * n * sizeof(double2), sm));
-    // r_hi = b, ||b||^2
-    k_residual<<<vgrid, 256, 0, sm>>>(b, x, ctx->d_r64, kMixed ? ctx->d_r32 : nullptr, n, part, nullptr);
-    HMC_LAUNCH(ctx, "k_residual");
-    k_cg_start<<<nrhs, 256, 0, sm>>>(cgs, part, kRedBlocks);
+    int rc;
+    if (use_x0) {
+        // start from the caller's x: ||b||^2, r_hi = b - A x (FP64) and ||r_hi||^2
+        k_dot<double><<<vgrid, 256, 0, sm>>>(reinterpret_cast<const double2*>(b), reinterpret_cast<const double2*>(b),
+                                             n, part2, nullptr);
+        HMC_LAUNCH(ctx, "k_dot");
+        int nb0 = 0;
+        if ((rc = launch_apply_A<double>(ctx, lat, phi64, x, ctx->d_q64, nrhs, nullptr, &nb0))) return rc;
+        k_residual<<<vgrid, 256, 0, sm>>>(b, ctx->d_q64, ctx->d_r64, kMixed ? ctx->d_r32 : nullptr, n, part, nullptr);
+        HMC_LAUNCH(ctx, "k_residual");
+        k_cg_start<<<nrhs, 256, 0, sm>>>(cgs, part2, part, kRedBlocks, tol2);
+    } else {
+        // zero start: r_hi = b
+        HMC_CUDA(ctx, cudaMemsetAsync(x, 0, nrhs * n * sizeof(double2), sm));
+        k_residual<<<vgrid, 256, 0, sm>>>(b, x, ctx->d_r64, kMixed ? ctx->d_r32 : nullptr, n, part, nullptr);
+        HMC_LAUNCH(ctx, "k_residual");
+        k_cg_start<<<nrhs, 256, 0, sm>>>(cgs, part, nullptr, kRedBlocks, tol2);
+    }
     HMC_LAUNCH(ctx, "k_cg_start");
 
-    int rc;
     // directions start at zero: the first fused update forms p = z + 0 * p
     HMC_CUDA(ctx, cudaMemsetAsync(pv, 0, nrhs * n * sizeof(C), sm));
     // z = P r, rz = <r, z>
@@ -363,11 +378,11 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
 }
 
 int cg_run(hmc_ctx* ctx, int chain, const double* phi, const double2* b, double2* x, int nrhs,
-           double tol, int maxit, int precond, hmc_cg_stats* st) {
+           double tol, int maxit, int precond, hmc_cg_stats* st, bool use_x0) {
     const Lat& lat = ctx->chains[chain].lat;
     if (ctx->p.solver_mode == HMC_SOLVER_MIXED)
-        return run<float>(ctx, lat, phi, b, x, nrhs, tol, maxit, precond, st);
-    return run<double>(ctx, lat, phi, b, x, nrhs, tol, maxit, precond, st);
+        return run<float>(ctx, lat, phi, b, x, nrhs, tol, maxit, precond, st, use_x0);
+    return run<double>(ctx, lat, phi, b, x, nrhs, tol, maxit, precond, st, use_x0);
 }
 
 }  // namespace hmc

@@ -133,10 +133,15 @@ struct FftcArgs {
 };
 
 // IC = lines along the inner (contiguous) index; OB = NL / IC rows of the outer index.
+// Tiles are either IC = 4 (x axis: OB whole rows, contiguous in memory) or IC = NL (y and tau
+// axes: one outer index, NL consecutive inner indices). Each thread moves complex pairs
+// (16 bytes); all per-element index arithmetic is by compile-time constants.
 template <int N, int NL, int IC, int MODE, int DIR>
 __global__ void __launch_bounds__(kThreads) k_fftc(FftcArgs A) {
     constexpr int OB = NL / IC;
     constexpr int TOT = N * NL;
+    static_assert(IC == 4 || OB == 1, "tile shape");
+    static_assert(kThreads % (NL / 2) == 0 && NL % 2 == 0, "line pairs must tile the block");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[8];
     float2* a = reinterpret_cast<float2*>(smem_raw);
@@ -152,67 +157,97 @@ __global__ void __launch_bounds__(kThreads) k_fftc(FftcArgs A) {
     } else {
         o0 = (blockIdx.x / A.nib) * OB;
         i0 = (blockIdx.x % A.nib) * IC;
+        if constexpr (IC != 4) {
+            if (A.cgs && !A.cgs[o0 / A.opr].active) return;   // one outer index per tile
+        }
     }
-    const int64_t oend = (MODE == kXUpd || MODE == kXDot) ? (int64_t)(k + 1) * A.opr : A.outer;
     float alpha = 0.f;
     if constexpr (MODE == kXUpd) alpha = (float)A.cgs[k].alpha;
-    float acc = 0.f;   // per-thread partial (a few elements), summed in double below
+    float acc = 0.f;   // per-thread partial, summed in double below
 
-    auto live = [&](int64_t o, int64_t i) -> bool {
-        if (o >= oend || i >= A.inner) return false;
-        if constexpr (MODE == kPlain || MODE == kTau) {
-            if (A.cgs && !A.cgs[o / A.opr].active) return false;
-        }
-        return true;
-    };
-
-#pragma unroll 4
-    for (int e = threadIdx.x; e < TOT; e += kThreads) {
-        const int ic = e % IC, j = (e / IC) % N, ob = e / (IC * N);
-        const int64_t o = o0 + ob, i = i0 + ic;
-        float2 v = make_float2(0.f, 0.f);
-        if (live(o, i)) {
-            const int64_t g = (o * N + j) * A.inner + i;
+    // ---- load ------------------------------------------------------------------------------
+    // IC = 4: the tile is rows [o0, o0 + nrow) of N * 4 contiguous complex numbers.
+    // IC = NL: thread owns line pair ic = 2 (tid % (NL/2)) and rows j = tid / (NL/2) + m * JS.
+    constexpr int JS = kThreads / (NL / 2);
+    int64_t nrow = OB;
+    if constexpr (IC == 4) {
+        const int64_t oend = (MODE == kXUpd || MODE == kXDot) ? (int64_t)(k + 1) * A.opr : A.outer;
+        nrow = min((int64_t)OB, oend - o0);
+    }
+    const int icp = 2 * (threadIdx.x % (NL / 2));
+    const int j0 = threadIdx.x / (NL / 2);
+    const bool lane_live = (IC == 4) || (i0 + icp < A.inner);
+    if constexpr (IC == 4) {
+        const int64_t g0 = o0 * N * 4;
+        const int tot = (int)(nrow * N * 4);
+        for (int e = 2 * threadIdx.x; e < tot; e += 2 * kThreads) {
+            const int c = e & 3, j = (e >> 2) % N, ob = (e >> 2) / N;
+            const int64_t g = g0 + e;
+            float4 v;
             if constexpr (MODE == kXUpd) {
-                float2 xx = A.x[g], rr = A.r[g];
-                const float2 pp = A.p[g], qq = A.q[g];
-                xx.x += alpha * pp.x; xx.y += alpha * pp.y;
-                rr.x -= alpha * qq.x; rr.y -= alpha * qq.y;
-                A.x[g] = xx;
-                A.r[g] = rr;
-                acc += rr.x * rr.x + rr.y * rr.y;
+                float4 xx = *reinterpret_cast<const float4*>(A.x + g);
+                float4 rr = *reinterpret_cast<const float4*>(A.r + g);
+                const float4 pp = *reinterpret_cast<const float4*>(A.p + g);
+                const float4 qq = *reinterpret_cast<const float4*>(A.q + g);
+                xx.x += alpha * pp.x; xx.y += alpha * pp.y; xx.z += alpha * pp.z; xx.w += alpha * pp.w;
+                rr.x -= alpha * qq.x; rr.y -= alpha * qq.y; rr.z -= alpha * qq.z; rr.w -= alpha * qq.w;
+                *reinterpret_cast<float4*>(A.x + g) = xx;
+                *reinterpret_cast<float4*>(A.r + g) = rr;
+                acc += rr.x * rr.x + rr.y * rr.y + rr.z * rr.z + rr.w * rr.w;
                 v = rr;
             } else {
-                v = A.src[g];
-                if constexpr (MODE == kTau) {
-                    const float2 w = __ldg(A.twist + j);
-                    v = make_float2(v.x * w.x + v.y * w.y, v.y * w.x - v.x * w.y);   // v * conj(w)
-                }
+                v = *reinterpret_cast<const float4*>(A.src + g);
+            }
+            *reinterpret_cast<float4*>(a + j * NL + ob * 4 + c) = v;
+        }
+        if (nrow < OB) {   // zero the rows past the end (their results are discarded)
+            for (int e = (int)(nrow * N * 4) + threadIdx.x; e < OB * N * 4; e += kThreads) {
+                const int c = e & 3, j = (e >> 2) % N, ob = (e >> 2) / N;
+                a[j * NL + ob * 4 + c] = make_float2(0.f, 0.f);
             }
         }
-        a[j * NL + ob * IC + ic] = v;
+    } else {
+        const float2* src = A.src + (o0 * N + j0) * A.inner + i0 + icp;
+        const int64_t step = (int64_t)JS * A.inner;
+#pragma unroll 4
+        for (int j = j0; j < N; j += JS, src += step) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (lane_live) {
+                v = *reinterpret_cast<const float4*>(src);
+                if constexpr (MODE == kTau) {
+                    const float2 w = __ldg(A.twist + j);   // multiply by conj(w)
+                    v = make_float4(v.x * w.x + v.y * w.y, v.y * w.x - v.x * w.y,
+                                    v.z * w.x + v.w * w.y, v.w * w.x - v.z * w.y);
+                }
+            }
+            *reinterpret_cast<float4*>(a + j * NL + icp) = v;
+        }
     }
     __syncthreads();
 
+    // ---- transform -------------------------------------------------------------------------
     float2* res;
     if constexpr (MODE == kTau) {
         res = stages_ct<N, NL, 0, 1, -1>(a, b, A.tw);
         float2* other = (res == a) ? b : a;
-        // multiply by P-hat = 1 / |K-hat|^2 per (alpha, n, k)
-        for (int e = threadIdx.x; e < TOT; e += kThreads) {
-            const int line = e % NL, j = e / NL;
-            const int64_t i = i0 + (line % IC);
-            if (i < A.inner) {
-                const int alpha_b = (int)((i & 3) >> 1);
-                const int kk = (int)(i >> 2);
-                const int mx = kk % A.L, my = kk / A.L;
-                const float2 ew = __ldg(A.eitw + j);
-                const float re = ew.x + A.c0[alpha_b] + A.chx[alpha_b] * __ldg(A.cosk + mx) +
-                                 A.chy[alpha_b] * __ldg(A.cosk + my);
-                const float ph = 1.0f / (re * re + ew.y * ew.y);
-                float2 v = res[e];
-                res[e] = make_float2(v.x * ph, v.y * ph);
-            }
+        // P-hat = 1 / |K-hat|^2: the momentum part depends only on the thread's line pair
+        // (both lines share alpha and k: they are spins s = 0, 1 of one site)
+        const int64_t i = i0 + icp;
+        float base = 0.f;
+        if (lane_live) {
+            const int ab = (int)((i & 3) >> 1);
+            const int kk = (int)(i >> 2);
+            const int mx = kk % A.L, my = kk / A.L;
+            base = A.c0[ab] + A.chx[ab] * __ldg(A.cosk + mx) + A.chy[ab] * __ldg(A.cosk + my);
+        }
+#pragma unroll 4
+        for (int j = j0; j < N; j += JS) {
+            const float2 ew = __ldg(A.eitw + j);
+            const float re = ew.x + base;
+            const float ph = 1.0f / (re * re + ew.y * ew.y);
+            float4 v = *reinterpret_cast<float4*>(res + j * NL + icp);
+            v.x *= ph; v.y *= ph; v.z *= ph; v.w *= ph;
+            *reinterpret_cast<float4*>(res + j * NL + icp) = v;
         }
         __syncthreads();
         res = stages_ct<N, NL, 0, 1, +1>(res, other, A.tw);
@@ -220,23 +255,35 @@ __global__ void __launch_bounds__(kThreads) k_fftc(FftcArgs A) {
         res = stages_ct<N, NL, 0, 1, DIR>(a, b, A.tw);
     }
 
-#pragma unroll 4
-    for (int e = threadIdx.x; e < TOT; e += kThreads) {
-        const int ic = e % IC, j = (e / IC) % N, ob = e / (IC * N);
-        const int64_t o = o0 + ob, i = i0 + ic;
-        if (!live(o, i)) continue;
-        const int64_t g = (o * N + j) * A.inner + i;
-        float2 v = res[j * NL + ob * IC + ic];
-        if constexpr (MODE == kTau) {
-            const float2 w = __ldg(A.twist + j);
-            v = make_float2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
+    // ---- store -----------------------------------------------------------------------------
+    const float sc = A.scale;
+    if constexpr (IC == 4) {
+        const int64_t g0 = o0 * N * 4;
+        const int tot = (int)(nrow * N * 4);
+        for (int e = 2 * threadIdx.x; e < tot; e += 2 * kThreads) {
+            const int c = e & 3, j = (e >> 2) % N, ob = (e >> 2) / N;
+            const int64_t g = g0 + e;
+            float4 v = *reinterpret_cast<const float4*>(res + j * NL + ob * 4 + c);
+            v.x *= sc; v.y *= sc; v.z *= sc; v.w *= sc;
+            *reinterpret_cast<float4*>(A.dst + g) = v;
+            if constexpr (MODE == kXDot) {
+                const float4 rr = *reinterpret_cast<const float4*>(A.r + g);
+                acc += rr.x * v.x + rr.y * v.y + rr.z * v.z + rr.w * v.w;
+            }
         }
-        v.x *= A.scale;
-        v.y *= A.scale;
-        A.dst[g] = v;
-        if constexpr (MODE == kXDot) {
-            const float2 rr = A.r[g];
-            acc += rr.x * v.x + rr.y * v.y;
+    } else if (lane_live) {
+        float2* dst = A.dst + (o0 * N + j0) * A.inner + i0 + icp;
+        const int64_t step = (int64_t)JS * A.inner;
+#pragma unroll 4
+        for (int j = j0; j < N; j += JS, dst += step) {
+            float4 v = *reinterpret_cast<const float4*>(res + j * NL + icp);
+            if constexpr (MODE == kTau) {
+                const float2 w = __ldg(A.twist + j);
+                v = make_float4(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x,
+                                v.z * w.x - v.w * w.y, v.z * w.y + v.w * w.x);
+            }
+            v.x *= sc; v.y *= sc; v.z *= sc; v.w *= sc;
+            *reinterpret_cast<float4*>(dst) = v;
         }
     }
     if constexpr (MODE == kXUpd || MODE == kXDot) {
@@ -276,7 +323,9 @@ bool fftc_supported(int n) {
 
 static int lines_rt(int n) { return n > 96 ? 16 : 32; }
 
-bool fftc_can(int n, int64_t inner) { return fftc_supported(n) && (inner == 4 || inner >= lines_rt(n)); }
+bool fftc_can(int n, int64_t inner) {
+    return fftc_supported(n) && (inner == 4 || (inner >= lines_rt(n) && inner % 2 == 0));
+}
 
 // Plain axis pass (IC = lines if inner >= lines, else IC = 4 with inner == 4).
 int fftc_axis(hmc_ctx* ctx, float2* data, int64_t outer, int n, int64_t inner, int dir, const float2* src,

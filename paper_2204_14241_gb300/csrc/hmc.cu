@@ -104,6 +104,15 @@ __global__ void k_axpy(double a, const double* __restrict__ x, double* __restric
     if (i < n) y[i] += a * x[i];
 }
 
+// b = 2 a - b (linear extrapolation of two solutions)
+__global__ void k_extrap(const double2* __restrict__ a, double2* __restrict__ b, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        const double2 u = a[i], v = b[i];
+        b[i] = make_double2(2.0 * u.x - v.x, 2.0 * u.y - v.y);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_norm2(const double* __restrict__ a, int64_t n, double* __restrict__ part) {
     __shared__ double red[8];
     double s = 0.0;
@@ -145,7 +154,7 @@ template <typename T> static int dalloc(hmc_ctx* ctx, T** p, int64_t count) {
 }
 
 static void free_all(hmc_ctx* ctx) {
-    void* ps[] = {ctx->d_r64, ctx->d_p64, ctx->d_p64b, ctx->d_p32b, ctx->d_q64, ctx->d_z64, ctx->d_X, ctx->d_pf, ctx->d_chi,
+    void* ps[] = {ctx->d_r64, ctx->d_p64, ctx->d_p64b, ctx->d_p32b, ctx->d_q64, ctx->d_z64, ctx->d_X, ctx->d_Xprev, ctx->d_pf, ctx->d_chi,
                   ctx->d_x32, ctx->d_r32, ctx->d_p32, ctx->d_q32, ctx->d_z32, ctx->d_phi32,
                   ctx->d_phi_save, ctx->d_pi, ctx->d_F, ctx->d_vel, ctx->d_z, ctx->d_fft,
                   ctx->d_part, ctx->d_red, ctx->d_cg, ctx->d_u32};
@@ -225,7 +234,7 @@ int hmc_init(const hmc_params* p, int n_chains, const hmc_chain* chains, void* c
     if ((rc = dalloc(ctx, &ctx->d_r64, nf)) || (rc = dalloc(ctx, &ctx->d_p64, mixed ? 1 : nf)) ||
         (rc = dalloc(ctx, &ctx->d_p64b, mixed ? 1 : nf)) || (rc = dalloc(ctx, &ctx->d_p32b, mixed ? nf : 1)) ||
         (rc = dalloc(ctx, &ctx->d_q64, nf)) || (rc = dalloc(ctx, &ctx->d_z64, mixed ? 1 : nf)) ||
-        (rc = dalloc(ctx, &ctx->d_X, nf)) || (rc = dalloc(ctx, &ctx->d_pf, nf)) ||
+        (rc = dalloc(ctx, &ctx->d_X, nf)) || (rc = dalloc(ctx, &ctx->d_Xprev, p->initial_guess ? nf : 1)) || (rc = dalloc(ctx, &ctx->d_pf, nf)) ||
         (rc = dalloc(ctx, &ctx->d_chi, nf)) || (rc = dalloc(ctx, &ctx->d_x32, mixed ? nf : 1)) ||
         (rc = dalloc(ctx, &ctx->d_r32, mixed ? nf : 1)) || (rc = dalloc(ctx, &ctx->d_p32, mixed ? nf : 1)) ||
         (rc = dalloc(ctx, &ctx->d_q32, mixed ? nf : 1)) || (rc = dalloc(ctx, &ctx->d_z32, mixed ? nf : 1)) ||
@@ -313,14 +322,16 @@ int cg_solve(hmc_ctx* ctx, int chain, const void* phi, const void* b, void* x, i
 
 }  // extern "C"
 
-// F, S_pf and S_b at phi for the pseudofermions pf; X receives A^{-1} pf.
+// F, S_pf and S_b at phi for the pseudofermions pf; X receives A^{-1} pf (starting from the
+// contents of X when use_x0).
 static int force_impl(hmc_ctx* ctx, int chain, const double* phi, const double2* pf, int nrhs, double* F,
-                      int include_boson, int precond, double* s_pf, double* s_b, hmc_cg_stats* st) {
+                      int include_boson, int precond, double* s_pf, double* s_b, hmc_cg_stats* st,
+                      double2* X, bool use_x0) {
     const ChainDesc& ch = ctx->chains[chain];
-    int rc = cg_run(ctx, chain, phi, pf, ctx->d_X, nrhs, ctx->p.cg_tol, ctx->p.cg_maxit, precond, st);
+    int rc = cg_run(ctx, chain, phi, pf, X, nrhs, ctx->p.cg_tol, ctx->p.cg_maxit, precond, st, use_x0);
     if (rc) return rc;
     int nb = 0;
-    if ((rc = launch_force(ctx, ch.lat, ch.r, phi, ctx->d_X, pf, nrhs, F, include_boson, ctx->d_part, &nb))) return rc;
+    if ((rc = launch_force(ctx, ch.lat, ch.r, phi, X, pf, nrhs, F, include_boson, ctx->d_part, &nb))) return rc;
     if (!s_pf && !s_b) return HMC_OK;
     if ((rc = reduce_rows(ctx, ctx->d_part, 2, nb, ctx->d_red))) return rc;
     double v[2];
@@ -336,7 +347,7 @@ extern "C" int force(hmc_ctx* ctx, int chain, const void* phi, const void* phi_p
     if ((rc = check_chain(ctx, chain)) || (rc = check_nrhs(ctx, nrhs)) || (rc = check_ptrs(ctx, {phi, phi_pf, F}))) return rc;
     double sb = 0.0;
     rc = force_impl(ctx, chain, (const double*)phi, (const double2*)phi_pf, nrhs, (double*)F, include_boson,
-                    precond, S_pf, (S_b || include_boson) ? &sb : nullptr, st);
+                    precond, S_pf, (S_b || include_boson) ? &sb : nullptr, st, ctx->d_X, false);
     if (rc) return rc;
     if (S_b) {
         if (!include_boson) {
@@ -449,9 +460,25 @@ static int run_chain(hmc_ctx* ctx, int c, const hmc_traj_in* in, double out_e[6]
     int tot_it = 0;
     double wr = 0.0, s_pf = 0.0, s_b = 0.0;
     hmc_cg_stats st;
+    // solution buffers: xa holds the latest solution, xb the one before (initial guesses)
+    double2 *xa = ctx->d_X, *xb = ctx->initial_guess_buf();
+    int nsol = 0;
+    const int64_t nfv = (int64_t)K * 4 * lat.V;
     auto do_force = [&](bool want) -> int {
+        const bool guess = ctx->p.initial_guess && nsol >= 1;
+        double2* xo = guess ? xb : xa;
+        if (guess) {
+            if (nsol >= 2) {
+                k_extrap<<<(unsigned)((nfv + 255) / 256), 256, 0, sm>>>(xa, xb, nfv);
+                HMC_LAUNCH(ctx, "k_extrap");
+            } else {
+                HMC_CUDA(ctx, cudaMemcpyAsync(xb, xa, nfv * sizeof(double2), cudaMemcpyDeviceToDevice, sm));
+            }
+        }
         int r2 = force_impl(ctx, c, phi, ctx->d_pf, K, ctx->d_F, 1, in->precond, want ? &s_pf : nullptr,
-                            want ? &s_b : nullptr, &st);
+                            want ? &s_b : nullptr, &st, xo, guess);
+        if (guess) { xb = xa; xa = xo; }
+        ++nsol;
         tot_it += st.iterations;
         if (st.true_rel_resid > wr) wr = st.true_rel_resid;
         return r2;

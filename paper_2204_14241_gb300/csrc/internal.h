@@ -72,6 +72,7 @@ struct hmc_ctx {
     double2* d_q64 = nullptr;
     double2* d_z64 = nullptr;
     double2* d_X = nullptr;       // solve output used by force
+    double2* d_Xprev = nullptr;   // previous solution (chronological initial guess)
     double2* d_pf = nullptr;      // pseudofermion fields of a trajectory
     double2* d_chi = nullptr;     // heatbath noise (Philox mode)
     float2* d_x32 = nullptr;
@@ -98,6 +99,8 @@ struct hmc_ctx {
     hmc::CgScalars* h_cg = nullptr;   // pinned mirror
     double* h_red = nullptr;          // pinned, 64 doubles
     uint32_t* d_u32 = nullptr;        // 4 words scratch for uniforms
+
+    double2* initial_guess_buf() { return p.initial_guess ? d_Xprev : d_X; }
 };
 
 namespace hmc {
@@ -163,8 +166,8 @@ int metric_op(hmc_ctx* ctx, const Lat& lat, int op, const double* sig, const dou
 // reductions: sum nblk partials for each of k rows into out[k] (device)
 int reduce_rows(hmc_ctx* ctx, const double* part, int k, int nblk, double* out);
 
-// cg.cu
+// cg.cu; with use_x0 the solve starts from the contents of x instead of zero
 int cg_run(hmc_ctx* ctx, int chain, const double* phi, const double2* b, double2* x, int nrhs,
-           double tol, int maxit, int precond, hmc_cg_stats* st);
+           double tol, int maxit, int precond, hmc_cg_stats* st, bool use_x0 = false);
 
 }  // namespace hmc

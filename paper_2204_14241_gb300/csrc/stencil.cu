@@ -101,7 +101,7 @@ template <typename R> struct APf { static constexpr int N = sizeof(R) == 4 ? 2 :
 // p = x + beta_k * pold (x holding z), formed as it is loaded, and the block writes p for the
 // sites it owns (tile interior, slices [t0, t1)) to pnew; y = A p. pold and pnew must differ.
 template <typename R>
-__global__ void __launch_bounds__(kAThreads, sizeof(R) == 4 ? 3 : 2) k_apply_A(Lat lat, Coef<R> cf, ATile tl,
+__global__ void __launch_bounds__(kAThreads, 2) k_apply_A(Lat lat, Coef<R> cf, ATile tl,
                                                        const R* __restrict__ phi,
                                                        const Site<R>* __restrict__ x,
                                                        Site<R>* __restrict__ y, double* __restrict__ part,
@@ -136,27 +136,60 @@ __global__ void __launch_bounds__(kAThreads, sizeof(R) == 4 ? 3 : 2) k_apply_A(L
 
     auto gx = [&](int i) { int v = (x0 + i) % L; return v < 0 ? v + L : v; };
     auto gy = [&](int j) { int v = (y0 + j) % L; return v < 0 ? v + L : v; };
-    auto ring2 = [&](int i) { const int hx = i % HX2, hy = i / HX2;
-                              return hx == 0 || hy == 0 || hx == HX2 - 1 || hy == HY2 - 1; };
 
-    // register prefetch of one slice: the halo2 sites tid + j * kAThreads, and phi on halo1
+    // Per-thread geometry, fixed for the whole march: in-plane offsets (y * L + x) of this
+    // thread's two-site-ring sites (x loads), one-site-ring sites (phi loads and t_ outputs)
+    // and of its tile site (y output). -1 marks "none".
+    int h2o[NPF], h1o[NPF], mtc[NPF];
+    bool h2own[NPF], h2ring[NPF];
+    R mte[NPF];
+#pragma unroll
+    for (int j = 0; j < NPF; ++j) {
+        const int i = threadIdx.x + j * kAThreads;
+        h2o[j] = -1; h1o[j] = -1; mtc[j] = 0; h2own[j] = false; h2ring[j] = false; mte[j] = R(1);
+        if (i < N2) {
+            const int hx = i % HX2, hy = i / HX2;
+            h2o[j] = gy(hy - 2) * L + gx(hx - 2);
+            h2own[j] = hx >= 2 && hy >= 2 && hx < TX + 2 && hy < TY + 2 && x0 + hx - 2 < L && y0 + hy - 2 < L;
+            h2ring[j] = hx == 0 || hy == 0 || hx == HX2 - 1 || hy == HY2 - 1;
+        }
+        if (i < N1) {
+            const int hx = i % HX1, hy = i / HX1;
+            const int X = gx(hx - 1), Y = gy(hy - 1);
+            h1o[j] = Y * L + X;
+            mtc[j] = (hy + 1) * HX2 + hx + 1;
+            mte[j] = ((X + Y) & 1) ? R(-1) : R(1);
+        }
+    }
+    int yo = -1, yc = 0;
+    R ye = R(1);
+    if (threadIdx.x < TX * TY) {
+        const int ix = threadIdx.x % TX, iy = threadIdx.x / TX;
+        const int X = x0 + ix, Y = y0 + iy;
+        if (X < L && Y < L) {
+            yo = Y * L + X;
+            yc = (iy + 1) * HX1 + ix + 1;
+            ye = ((X + Y) & 1) ? R(-1) : R(1);
+        }
+    }
+
+    // register prefetch of one slice: x on this thread's two-site-ring sites, phi on its
+    // one-site-ring sites
     Site<R> rz[NPF], rp[NPF];
     R rph[NPF][3];
     auto fetch = [&](int t) {
         const int64_t base = (int64_t)t * LL;
 #pragma unroll
         for (int j = 0; j < NPF; ++j) {
-            const int i = threadIdx.x + j * kAThreads;
-            if (i < N2) {
-                const int64_t s = base + (int64_t)gy(i / HX2 - 2) * L + gx(i % HX2 - 2);
-                rz[j] = load_site(xk + s);
-                if (pnew) rp[j] = load_site(pok + s);
+            if (h2o[j] >= 0) {
+                rz[j] = load_site(xk + base + h2o[j]);
+                if (pnew) rp[j] = load_site(pok + base + h2o[j]);
             }
-            if (i < N1) {
-                const int64_t s = base + (int64_t)gy(i / HX1 - 1) * L + gx(i % HX1 - 1);
-                rph[j][0] = __ldg(phi + s);
-                rph[j][1] = __ldg(phi + V + s);
-                rph[j][2] = __ldg(phi + 2 * V + s);
+            if (h1o[j] >= 0) {
+                const R* pp = phi + base + h1o[j];
+                rph[j][0] = __ldg(pp);
+                rph[j][1] = __ldg(pp + V);
+                rph[j][2] = __ldg(pp + 2 * V);
             }
         }
     };
@@ -166,7 +199,7 @@ __global__ void __launch_bounds__(kAThreads, sizeof(R) == 4 ? 3 : 2) k_apply_A(L
 #pragma unroll
         for (int j = 0; j < NPF; ++j) {
             const int i = threadIdx.x + j * kAThreads;
-            if (i < N2 && !(ring1only && ring2(i))) {
+            if (h2o[j] >= 0 && !(ring1only && h2ring[j])) {
                 Site<R> v = rz[j];
                 if (pnew) {
 #pragma unroll
@@ -174,13 +207,11 @@ __global__ void __launch_bounds__(kAThreads, sizeof(R) == 4 ? 3 : 2) k_apply_A(L
                         v.c[q].x += beta * rp[j].c[q].x;
                         v.c[q].y += beta * rp[j].c[q].y;
                     }
-                    const int hx = i % HX2, hy = i / HX2;
-                    if (own && hx >= 2 && hy >= 2 && hx < TX + 2 && hy < TY + 2 && x0 + hx - 2 < L && y0 + hy - 2 < L)
-                        store_site(pnk + base + (int64_t)(y0 + hy - 2) * L + (x0 + hx - 2), v);
+                    if (own && h2own[j]) store_site(pnk + base + h2o[j], v);
                 }
                 sm_store<R>(dst, N2, i, v);
             }
-            if (i < N1 && ph) {
+            if (h1o[j] >= 0 && ph) {
                 ph[i] = rph[j][0];
                 ph[N1 + i] = rph[j][1];
                 ph[2 * N1 + i] = rph[j][2];
@@ -190,15 +221,15 @@ __global__ void __launch_bounds__(kAThreads, sizeof(R) == 4 ? 3 : 2) k_apply_A(L
     // t_(t) = D^dagger x on the one-site ring from x(t) (cur) and x(t-1) (prev)
     auto make_t = [&](uint4* dst, const uint4* cur, const uint4* prev, const R* ph, int t) {
         const R tsign = (t == 0) ? R(-1) : R(1);   // b(t-1)
-        for (int i = threadIdx.x; i < N1; i += kAThreads) {
-            const int hx = i % HX1, hy = i / HX1;
-            const int c = (hy + 1) * HX2 + hx + 1;
-            const int X = gx(hx - 1), Y = gy(hy - 1);
-            const R eta = ((X + Y) & 1) ? R(-1) : R(1);
+#pragma unroll
+        for (int j = 0; j < NPF; ++j) {
+            if (h1o[j] < 0) continue;
+            const int i = threadIdx.x + j * kAThreads;
+            const int c = mtc[j];
             Site<R> o = site_op<R>(cf, sm_load<R>(cur, N2, c), sm_load<R>(cur, N2, c - 1),
                                    sm_load<R>(cur, N2, c + 1), sm_load<R>(cur, N2, c - HX2),
                                    sm_load<R>(cur, N2, c + HX2), sm_load<R>(prev, N2, c), tsign,
-                                   ph[i], ph[N1 + i], ph[2 * N1 + i], eta);
+                                   ph[i], ph[N1 + i], ph[2 * N1 + i], mte[j]);
             sm_store<R>(dst, N1, i, o);
         }
     };
@@ -215,7 +246,7 @@ __global__ void __launch_bounds__(kAThreads, sizeof(R) == 4 ? 3 : 2) k_apply_A(L
 
     uint4 *xc = xa, *xn = xb, *tc = ta, *tn = tb;
     int pc = 0;   // phi(t) is in buffer pc of the three at phb
-    float acc = 0.f;
+    R acc = 0;   // per-thread partial in the operator's precision
     for (int t = t0; t < t1; ++t) {
         const int tp = tnext(t, Nt);
         const int pn = pc == 2 ? 0 : pc + 1;
@@ -226,26 +257,20 @@ __global__ void __launch_bounds__(kAThreads, sizeof(R) == 4 ? 3 : 2) k_apply_A(L
         make_t(tn, xn, xc, phn, tp);
         __syncthreads();
         // y(t) = D t_ on the tile
-        const R tsign = (t == Nt - 1) ? R(-1) : R(1);   // b(t)
-        const int64_t base = (int64_t)t * LL;
-        const R* ph = phb + pc * 3 * N1;
-        for (int i = threadIdx.x; i < TX * TY; i += kAThreads) {
-            const int ix = i % TX, iy = i / TX;
-            const int X = x0 + ix, Y = y0 + iy;
-            if (X >= L || Y >= L) continue;
-            const int c = (iy + 1) * HX1 + ix + 1;
-            const int64_t s = base + (int64_t)Y * L + X;
-            const R eta = ((X + Y) & 1) ? R(-1) : R(1);
+        if (yo >= 0) {
+            const R tsign = (t == Nt - 1) ? R(-1) : R(1);   // b(t)
+            const R* ph = phb + pc * 3 * N1;
+            const int c = yc;
             const Site<R> tcen = sm_load<R>(tc, N1, c);
             Site<R> o = site_op<R>(cf, tcen, sm_load<R>(tc, N1, c - 1), sm_load<R>(tc, N1, c + 1),
                                    sm_load<R>(tc, N1, c - HX1), sm_load<R>(tc, N1, c + HX1),
-                                   sm_load<R>(tn, N1, c), tsign, ph[c], ph[N1 + c], ph[2 * N1 + c], eta);
-            store_site(yk + s, o);
+                                   sm_load<R>(tn, N1, c), tsign, ph[c], ph[N1 + c], ph[2 * N1 + c], ye);
+            store_site(yk + (int64_t)t * LL + yo, o);
             if (part) {
                 R n2 = 0;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) n2 += tcen.c[q].x * tcen.c[q].x + tcen.c[q].y * tcen.c[q].y;
-                acc += (float)n2;
+                acc += n2;
             }
         }
         uint4* sw = xc; xc = xn; xn = sw;
@@ -271,7 +296,8 @@ static ATile choose_tile(const hmc_ctx* ctx, const Lat& lat, int nrhs, size_t si
     if (lat.L % 16 == 0 && site_bytes <= 32) t.TX = 16;
     int cap = (site_bytes > 32 ? 128 : 256) / t.TX;
     t.TY = largest_divisor_le(lat.L, cap < 1 ? 1 : cap);
-    const int n2max = (site_bytes > 32 ? 1 : 2) * kAThreads;
+    const int n2max = (site_bytes > 32 ? 1 : 2) * kAThreads;   // each thread stages at most NPF sites
+    // (TY <= kAThreads / TX keeps the tile within one site per thread)
     while ((t.TX + 4) * (t.TY + 4) > n2max && t.TY > 1) t.TY = largest_divisor_le(lat.L, t.TY - 1);
     while ((t.TX + 4) * (t.TY + 4) > n2max && t.TX > 1) t.TX = largest_divisor_le(lat.L, t.TX - 1);
     t.ntx = (lat.L + t.TX - 1) / t.TX;

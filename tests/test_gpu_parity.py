@@ -25,9 +25,10 @@ COUPLINGS = dict(dtau=0.1, t_h=(1.0, 0.5), t_v=(0.5, 1.0), mu=(-0.5, -0.5), g=1.
 CASES = [(4, 8), (6, 7), (20, 12), (12, 24)]
 
 
-def ctx_for(L, Nt, solver_mode="fp64", nrhs=2, tol=1e-12, chains=None):
+def ctx_for(L, Nt, solver_mode="fp64", nrhs=2, tol=1e-12, chains=None, guess=0):
     from paper_2204_14241_gb300.hmc import Context
-    return Context(L, Nt, solver=solver_mode, nrhs_max=nrhs, cg_tol=tol, chains=chains, **COUPLINGS)
+    return Context(L, Nt, solver=solver_mode, nrhs_max=nrhs, cg_tol=tol, chains=chains, initial_guess=guess,
+                   **COUPLINGS)
 
 
 def oparams(L, Nt, r=None):
@@ -188,12 +189,13 @@ def test_boson_action_and_force_parity():
     assert rel(I.to_paper_boson(F.cpu().numpy()), -boson.grad(P, phi_o)) < 1e-12
 
 
-@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("mode,guess", [("fp64", 0), ("mixed", 0), ("mixed", 1)])
 @pytest.mark.parametrize("nrhs", [1, 2])
-def test_trajectory_matches_oracle(mode, nrhs):
-    # the small configuration: L = 4, Nt = 8, dtau = 0.1, eps = 0.05, n_leap = 10
+def test_trajectory_matches_oracle(mode, guess, nrhs):
+    # the small configuration: L = 4, Nt = 8, dtau = 0.1, eps = 0.05, n_leap = 10; guess = 1 starts
+    # each force solve from the extrapolated previous solutions (same stopping test)
     L, Nt, eps, n_leap = 4, 8, 0.05, 10
-    ctx = ctx_for(L, Nt, mode, nrhs=nrhs, tol=1e-12)
+    ctx = ctx_for(L, Nt, mode, nrhs=nrhs, tol=1e-12, guess=guess)
     P = oparams(L, Nt)
     phi0 = I.gaussian_field(20, L, Nt)
     w = np.fft.fftn(I.gaussian_field(21, L, Nt), axes=(1, 2, 3), norm="ortho")
