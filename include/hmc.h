@@ -143,9 +143,11 @@ int force(hmc_ctx* ctx, int chain, const void* phi, const void* phi_pf, int nrhs
  *   HMC_METRIC_VELOCITY: out = F^{-1}(sigma . F in)          (d phi / dt = M^{-1} pi)
  *   HMC_METRIC_KINETIC:  *scalar = (1/2) sum sigma |F in|^2  (out unused)
  *   HMC_METRIC_ACCUM:    out += |F in|^2                     (Eq. covest numerator)
+ *   HMC_METRIC_MNORM:    *scalar = sum |F in|^2 / sigma      (in^T M in, M = Sigma^{-1}: the squared
+ *                                                             jump distance of Eq. ESJD; out unused)
  * in, out: [3][V] double; sig: [3][V] double; scalar: host. */
 enum hmc_metric_op { HMC_METRIC_MOMENTUM = 0, HMC_METRIC_VELOCITY = 1, HMC_METRIC_KINETIC = 2,
-                     HMC_METRIC_ACCUM = 3 };
+                     HMC_METRIC_ACCUM = 3, HMC_METRIC_MNORM = 4 };
 int metric_apply(hmc_ctx* ctx, int chain, int op, const void* sig, const void* in, void* out,
                  double* scalar);
 
@@ -175,6 +177,7 @@ typedef struct {
     double* energies;
     int* cg_iterations;      /* total inner CG iterations over the trajectory */
     double* max_true_resid;  /* worst final true relative residual of any solve */
+    double* jump2;           /* (phi' - phi)^T M (phi' - phi) of the proposal, accepted or not */
 } hmc_traj_out;
 
 /* One HMC update of every chain. Returns HMC_ERR_NOCONV / HMC_ERR_NONFINITE if a solve

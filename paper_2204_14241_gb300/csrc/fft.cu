@@ -553,7 +553,8 @@ __global__ void k_pack_real(const double* __restrict__ in, double2* __restrict__
     if (i < n) out[i] = make_double2(in[i], 0.0);
 }
 
-// mode 0: v *= sig; 1: v /= sqrt(sig); 2: partial sums of 0.5 sig |v|^2; 3: acc += |v|^2
+// mode 0: v *= sig; 1: v /= sqrt(sig); 2: partial sums of 0.5 sig |v|^2; 3: acc += |v|^2;
+// 4: partial sums of |v|^2 / sig
 __global__ void __launch_bounds__(256) k_spectral(double2* __restrict__ v, const double* __restrict__ sig,
                                                   int64_t n, int mode, double* __restrict__ acc,
                                                   double* __restrict__ part) {
@@ -570,11 +571,13 @@ __global__ void __launch_bounds__(256) k_spectral(double2* __restrict__ v, const
             v[i] = make_double2(a.x * s, a.y * s);
         } else if (mode == 2) {
             e = 0.5 * sig[i] * (a.x * a.x + a.y * a.y);
+        } else if (mode == 4) {
+            e = (a.x * a.x + a.y * a.y) / sig[i];
         } else {
             acc[i] += a.x * a.x + a.y * a.y;
         }
     }
-    if (mode == 2) {
+    if (mode == 2 || mode == 4) {
         const double t = block_sum(e, red);
         if (threadIdx.x == 0) part[blockIdx.x] = t;
     }
@@ -604,9 +607,9 @@ int metric_op(hmc_ctx* ctx, const Lat& lat, int op, const double* sig, const dou
     HMC_LAUNCH(ctx, "k_pack_real");
     int rc;
     if ((rc = fft3_real_field(ctx, lat, v, -1))) return rc;
-    if (op == HMC_METRIC_KINETIC) {
+    if (op == HMC_METRIC_KINETIC || op == HMC_METRIC_MNORM) {
         if (nb > ctx->part_cap) return fail(ctx, HMC_ERR_ARG, "metric: reduction buffer too small");
-        k_spectral<<<nb, 256, 0, ctx->stream>>>(v, sig, n, 2, nullptr, ctx->d_part);
+        k_spectral<<<nb, 256, 0, ctx->stream>>>(v, sig, n, op == HMC_METRIC_KINETIC ? 2 : 4, nullptr, ctx->d_part);
         HMC_LAUNCH(ctx, "k_spectral");
         return reduce_rows(ctx, ctx->d_part, 1, (int)nb, scalar_dev);
     }

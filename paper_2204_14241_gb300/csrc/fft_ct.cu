@@ -22,19 +22,76 @@ struct RadixList {
     int r[12];
 };
 
+// Stage radices: powers of two in radix-16 stages, the rest of the power of two merged with
+// one odd factor where the product stays <= 20, so that most lengths take two stages.
 constexpr RadixList radices(int N) {
     RadixList l{0, {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}};
-    while (N % 4 == 0) { l.r[l.n++] = 4; N /= 4; }
-    while (N % 2 == 0) { l.r[l.n++] = 2; N /= 2; }
-    while (N % 3 == 0) { l.r[l.n++] = 3; N /= 3; }
-    while (N % 5 == 0) { l.r[l.n++] = 5; N /= 5; }
+    int p2 = 1;
+    while (N % 2 == 0) { p2 *= 2; N /= 2; }
+    int odd[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int no = 0;
+    while (N % 5 == 0) { odd[no++] = 5; N /= 5; }
+    while (N % 3 == 0) { odd[no++] = 3; N /= 3; }
+    while (p2 >= 16) { l.r[l.n++] = 16; p2 /= 16; }
+    int first = 0;
+    if (p2 > 1) {
+        if (no > 0 && p2 * odd[0] <= 20) { l.r[l.n++] = p2 * odd[0]; first = 1; }
+        else l.r[l.n++] = p2;
+    }
+    for (int i = first; i < no; ++i) {
+        if (i + 1 < no && odd[i] * odd[i + 1] <= 15) { l.r[l.n++] = odd[i] * odd[i + 1]; ++i; }
+        else l.r[l.n++] = odd[i];
+    }
     return l;
 }
 
 constexpr int kThreads = 256;
 
+// Twiddles known at compile time: cos and sin of 2 pi m / R from their Taylor series on
+// [-pi/2, pi/2] (20 terms; the series' own truncation error there is below 1e-20).
+constexpr double kPi = 3.14159265358979323846264338327950288;
+__host__ __device__ constexpr double ct_sin_series(double x) {
+    double t = x, s = x;
+    for (int n = 1; n < 20; ++n) { t *= -x * x / ((2.0 * n) * (2.0 * n + 1.0)); s += t; }
+    return s;
+}
+__host__ __device__ constexpr double ct_cos_series(double x) {
+    double t = 1.0, s = 1.0;
+    for (int n = 1; n < 20; ++n) { t *= -x * x / ((2.0 * n - 1.0) * (2.0 * n)); s += t; }
+    return s;
+}
+__host__ __device__ constexpr double ct_cos2pi(int m, int R) {
+    m %= R;
+    if (m < 0) m += R;
+    double x = 2.0 * kPi * m / R;
+    if (x > kPi) x -= 2.0 * kPi;
+    if (x > kPi / 2) return -ct_cos_series(kPi - x);
+    if (x < -kPi / 2) return -ct_cos_series(-kPi - x);
+    return ct_cos_series(x);
+}
+__host__ __device__ constexpr double ct_sin2pi(int m, int R) {
+    m %= R;
+    if (m < 0) m += R;
+    double x = 2.0 * kPi * m / R;
+    if (x > kPi) x -= 2.0 * kPi;
+    if (x > kPi / 2) return ct_sin_series(kPi - x);
+    if (x < -kPi / 2) return ct_sin_series(-kPi - x);
+    return ct_sin_series(x);
+}
+template <int R> struct TwR { float c[R], s[R]; };   // cos, sin of 2 pi m / R
+template <int R> __host__ __device__ constexpr TwR<R> make_tw() {
+    TwR<R> t{};
+    for (int m = 0; m < R; ++m) { t.c[m] = (float)ct_cos2pi(m, R); t.s[m] = (float)ct_sin2pi(m, R); }
+    return t;
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float c, float s) {   // a * (c + i s)
+    return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+
+// Prime-size DFTs on registers: v[p] <- sum_q v[q] w^{pq}, w = e^{DIR 2 pi i / R}.
 template <int R, int DIR>
-__device__ __forceinline__ void bfly(float2* v, const float2* __restrict__ tw, int N) {
+__device__ __forceinline__ void bfly_prime(float2* v) {
     if constexpr (R == 2) {
         const float2 a = v[0], b = v[1];
         v[0] = make_float2(a.x + b.x, a.y + b.y);
@@ -48,24 +105,91 @@ __device__ __forceinline__ void bfly(float2* v, const float2* __restrict__ tw, i
         v[2] = make_float2(s0.x - s2.x, s0.y - s2.y);
         v[1] = make_float2(s1.x + s3r.x, s1.y + s3r.y);
         v[3] = make_float2(s1.x - s3r.x, s1.y - s3r.y);
+    } else if constexpr (R == 3) {
+        // X1,2 = v0 - (v1 + v2)/2 +- DIR i (sqrt3/2)(v1 - v2)
+        constexpr float h = (float)ct_sin2pi(1, 3);
+        const float2 t1 = make_float2(v[1].x + v[2].x, v[1].y + v[2].y);
+        const float2 d = make_float2(DIR * h * (v[1].x - v[2].x), DIR * h * (v[1].y - v[2].y));
+        const float2 m = make_float2(v[0].x - 0.5f * t1.x, v[0].y - 0.5f * t1.y);
+        v[0] = make_float2(v[0].x + t1.x, v[0].y + t1.y);
+        v[1] = make_float2(m.x - d.y, m.y + d.x);
+        v[2] = make_float2(m.x + d.y, m.y - d.x);
+    } else if constexpr (R == 5) {
+        // pairs (1, 4) and (2, 3): X_{1,4} = m1 +- i n1, X_{2,3} = m2 +- i n2
+        constexpr float c1 = (float)ct_cos2pi(1, 5), c2 = (float)ct_cos2pi(2, 5);
+        constexpr float s1 = (float)ct_sin2pi(1, 5), s2 = (float)ct_sin2pi(2, 5);
+        const float2 a1 = make_float2(v[1].x + v[4].x, v[1].y + v[4].y);
+        const float2 a2 = make_float2(v[2].x + v[3].x, v[2].y + v[3].y);
+        const float2 b1 = make_float2(v[1].x - v[4].x, v[1].y - v[4].y);
+        const float2 b2 = make_float2(v[2].x - v[3].x, v[2].y - v[3].y);
+        const float2 m1 = make_float2(v[0].x + c1 * a1.x + c2 * a2.x, v[0].y + c1 * a1.y + c2 * a2.y);
+        const float2 m2 = make_float2(v[0].x + c2 * a1.x + c1 * a2.x, v[0].y + c2 * a1.y + c1 * a2.y);
+        const float2 n1 = make_float2(DIR * (s1 * b1.x + s2 * b2.x), DIR * (s1 * b1.y + s2 * b2.y));
+        const float2 n2 = make_float2(DIR * (s2 * b1.x - s1 * b2.x), DIR * (s2 * b1.y - s1 * b2.y));
+        v[0] = make_float2(v[0].x + a1.x + a2.x, v[0].y + a1.y + a2.y);
+        v[1] = make_float2(m1.x - n1.y, m1.y + n1.x);
+        v[4] = make_float2(m1.x + n1.y, m1.y - n1.x);
+        v[2] = make_float2(m2.x - n2.y, m2.y + n2.x);
+        v[3] = make_float2(m2.x + n2.y, m2.y - n2.x);
     } else {
+        constexpr TwR<R> T = make_tw<R>();
         float2 out[R];
-        const int step = N / R;
 #pragma unroll
         for (int p = 0; p < R; ++p) {
             float2 acc = v[0];
 #pragma unroll
             for (int q = 1; q < R; ++q) {
-                float2 w = __ldg(tw + ((p * q) % R) * step);
-                if (DIR > 0) w.y = -w.y;
-                acc.x += v[q].x * w.x - v[q].y * w.y;
-                acc.y += v[q].x * w.y + v[q].y * w.x;
+                const float2 t = cmulf(v[q], T.c[(p * q) % R], DIR * T.s[(p * q) % R]);
+                acc.x += t.x;
+                acc.y += t.y;
             }
             out[p] = acc;
         }
 #pragma unroll
         for (int p = 0; p < R; ++p) v[p] = out[p];
     }
+}
+
+// R = R1 * R2 point DFT on registers by one Cooley-Tukey split: with n = n1 + R1 n2 and
+// k = k2 + R2 k1, X[k] = sum_n1 w_R1^{n1 k1} w_R^{n1 k2} sum_n2 v[n] w_R2^{n2 k2}.
+template <int R1, int R2, int DIR>
+__device__ __forceinline__ void bfly_split(float2* v) {
+    constexpr int R = R1 * R2;
+    constexpr TwR<R> T = make_tw<R>();
+    float2 u[R];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+        float2 w[R2];
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) w[n2] = v[n1 + R1 * n2];
+        bfly_prime<R2, DIR>(w);
+#pragma unroll
+        for (int k2 = 0; k2 < R2; ++k2)
+            u[n1 * R2 + k2] = (n1 * k2 == 0) ? w[k2] : cmulf(w[k2], T.c[(n1 * k2) % R], DIR * T.s[(n1 * k2) % R]);
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+        float2 z[R1];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) z[n1] = u[n1 * R2 + k2];
+        bfly_prime<R1, DIR>(z);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) v[k2 + R2 * k1] = z[k1];
+    }
+}
+
+template <int R, int DIR>
+__device__ __forceinline__ void bfly(float2* v) {
+    if constexpr (R == 2 || R == 3 || R == 4 || R == 5) bfly_prime<R, DIR>(v);
+    else if constexpr (R == 6) bfly_split<2, 3, DIR>(v);
+    else if constexpr (R == 8) bfly_split<2, 4, DIR>(v);
+    else if constexpr (R == 9) bfly_split<3, 3, DIR>(v);
+    else if constexpr (R == 10) bfly_split<2, 5, DIR>(v);
+    else if constexpr (R == 12) bfly_split<4, 3, DIR>(v);
+    else if constexpr (R == 15) bfly_split<3, 5, DIR>(v);
+    else if constexpr (R == 16) bfly_split<4, 4, DIR>(v);
+    else if constexpr (R == 20) bfly_split<4, 5, DIR>(v);
+    else static_assert(R == 2, "unsupported radix");
 }
 
 template <int N, int NL, int R, int Ns, int DIR>
@@ -88,7 +212,7 @@ __device__ __forceinline__ void stage_ct(const float2* src, float2* dst, const f
             }
             v[r] = a;
         }
-        bfly<R, DIR>(v, tw, N);
+        bfly<R, DIR>(v);
         const int d = (j / Ns) * Ns * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) dst[(d + r * Ns) * NL + line] = v[r];

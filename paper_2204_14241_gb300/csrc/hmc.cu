@@ -366,15 +366,15 @@ extern "C" int force(hmc_ctx* ctx, int chain, const void* phi, const void* phi_p
 extern "C" int metric_apply(hmc_ctx* ctx, int chain, int op, const void* sig, const void* in, void* out, double* scalar) {
     int rc;
     if ((rc = check_chain(ctx, chain)) || (rc = check_ptrs(ctx, {sig, in}))) return rc;
-    if (op < HMC_METRIC_MOMENTUM || op > HMC_METRIC_ACCUM) return fail(ctx, HMC_ERR_ARG, "metric_apply: unknown op");
-    if (op == HMC_METRIC_KINETIC) {
+    if (op < HMC_METRIC_MOMENTUM || op > HMC_METRIC_MNORM) return fail(ctx, HMC_ERR_ARG, "metric_apply: unknown op");
+    if (op == HMC_METRIC_KINETIC || op == HMC_METRIC_MNORM) {
         if (!scalar) return fail(ctx, HMC_ERR_ARG, "metric_apply: kinetic needs a scalar output");
     } else if ((rc = check_ptrs(ctx, {out}))) {
         return rc;
     }
     const Lat& lat = ctx->chains[chain].lat;
     if ((rc = metric_op(ctx, lat, op, (const double*)sig, (const double*)in, (double*)out, 0.0, ctx->d_red))) return rc;
-    if (op == HMC_METRIC_KINETIC) return fetch_red(ctx, 1, scalar);
+    if (op == HMC_METRIC_KINETIC || op == HMC_METRIC_MNORM) return fetch_red(ctx, 1, scalar);
     return HMC_OK;
 }
 
@@ -405,8 +405,14 @@ extern "C" int philox_normal(hmc_ctx* ctx, uint64_t seed, uint64_t counter, int6
 }
 
 // ---- trajectory ----------------------------------------------------------------------------------
+// d = a - b
+__global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ d, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) d[i] = a[i] - b[i];
+}
+
 static int run_chain(hmc_ctx* ctx, int c, const hmc_traj_in* in, double out_e[6], double* dH, int* acc,
-                     int* iters, double* worst) {
+                     int* iters, double* worst, double* jump2) {
     const ChainDesc& ch = ctx->chains[c];
     const Lat& lat = ch.lat;
     const int64_t nb = 3 * lat.V;
@@ -498,6 +504,13 @@ static int run_chain(hmc_ctx* ctx, int c, const hmc_traj_in* in, double out_e[6]
     if (!rc) rc = metric_op(ctx, lat, HMC_METRIC_KINETIC, sig, ctx->d_pi, nullptr, 0.0, ctx->d_red);
     double k1 = 0.0;
     if (!rc) rc = fetch_red(ctx, 1, &k1);
+    if (!rc && jump2) {
+        // squared M-norm of the proposed jump (Eq. ESJD), accepted or not
+        k_sub<<<gb, 256, 0, sm>>>(phi, ctx->d_phi_save, ctx->d_vel, nb);
+        HMC_LAUNCH(ctx, "k_sub");
+        rc = metric_op(ctx, lat, HMC_METRIC_MNORM, sig, ctx->d_vel, nullptr, 0.0, ctx->d_red);
+        if (!rc) rc = fetch_red(ctx, 1, jump2);
+    }
     *iters = tot_it;
     *worst = wr;
     if (rc) {
@@ -537,9 +550,9 @@ extern "C" int trajectory(hmc_ctx* ctx, const hmc_traj_in* in, hmc_traj_out* out
     }
     int first_err = HMC_OK;
     for (int c = 0; c < nc; ++c) {
-        double e[6] = {0, 0, 0, 0, 0, 0}, dh = 0.0, worst = 0.0;
+        double e[6] = {0, 0, 0, 0, 0, 0}, dh = 0.0, worst = 0.0, j2 = 0.0;
         int acc = 0, it = 0;
-        rc = run_chain(ctx, c, in, e, &dh, &acc, &it, &worst);
+        rc = run_chain(ctx, c, in, e, &dh, &acc, &it, &worst, (out && out->jump2) ? &j2 : nullptr);
         if (rc && !first_err) first_err = rc;
         if (out) {
             if (out->dH) out->dH[c] = dh;
@@ -547,6 +560,7 @@ extern "C" int trajectory(hmc_ctx* ctx, const hmc_traj_in* in, hmc_traj_out* out
             if (out->energies) for (int q = 0; q < 6; ++q) out->energies[6 * c + q] = e[q];
             if (out->cg_iterations) out->cg_iterations[c] = it;
             if (out->max_true_resid) out->max_true_resid[c] = worst;
+            if (out->jump2) out->jump2[c] = j2;
         }
     }
     return first_err;

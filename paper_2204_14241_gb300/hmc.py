@@ -22,7 +22,7 @@ HMC_OK, HMC_ERR_ARG, HMC_ERR_NOCONV, HMC_ERR_NONFINITE, HMC_ERR_TIMEOUT, HMC_ERR
 FP64, FP32 = 0, 1
 SOLVER_FP64, SOLVER_MIXED = 0, 1
 NOISE_EXPLICIT, NOISE_PHILOX = 0, 1
-METRIC_MOMENTUM, METRIC_VELOCITY, METRIC_KINETIC, METRIC_ACCUM = range(4)
+METRIC_MOMENTUM, METRIC_VELOCITY, METRIC_KINETIC, METRIC_ACCUM, METRIC_MNORM = range(5)
 
 # every function declared in include/hmc.h
 EXPORTS = ("hmc_init", "hmc_destroy", "hmc_last_error", "hmc_counters", "apply_M", "apply_MdagM", "apply_precond",
@@ -67,7 +67,7 @@ class TrajIn(ctypes.Structure):
 class TrajOut(ctypes.Structure):
     _fields_ = [("dH", ctypes.POINTER(ctypes.c_double)), ("accepted", ctypes.POINTER(ctypes.c_int)),
                 ("energies", ctypes.POINTER(ctypes.c_double)), ("cg_iterations", ctypes.POINTER(ctypes.c_int)),
-                ("max_true_resid", ctypes.POINTER(ctypes.c_double))]
+                ("max_true_resid", ctypes.POINTER(ctypes.c_double)), ("jump2", ctypes.POINTER(ctypes.c_double))]
 
 
 _lib = None
@@ -241,7 +241,7 @@ class Context:
     def metric(self, op, sig, inp, out=None, chain=0):
         self._boson(sig, chain)
         self._boson(inp, chain)
-        if op == METRIC_KINETIC:
+        if op in (METRIC_KINETIC, METRIC_MNORM):
             s = ctypes.c_double()
             self._check(self.lib.metric_apply(self.h, chain, op, _ptr(sig), _ptr(inp), None, ctypes.byref(s)))
             return s.value
@@ -282,13 +282,14 @@ class Context:
         en = (ctypes.c_double * (6 * nc))()
         its = (ctypes.c_int * nc)()
         res = (ctypes.c_double * nc)()
-        to = TrajOut(dH, acc, en, its, res)
+        j2 = (ctypes.c_double * nc)()
+        to = TrajOut(dH, acc, en, its, res, j2)
         rc = self.lib.trajectory(self.h, ctypes.byref(ti), ctypes.byref(to))
         if check:
             self._check(rc)
         return {"status": rc, "dH": list(dH), "accepted": [bool(a) for a in acc],
                 "energies": [list(en[6 * c:6 * c + 6]) for c in range(nc)],
-                "cg_iterations": list(its), "max_true_resid": list(res)}
+                "cg_iterations": list(its), "max_true_resid": list(res), "jump2": list(j2)}
 
     def philox_raw(self, key, ctr, nblocks):
         out = torch.empty(4 * nblocks, dtype=torch.int64, device=self.device)

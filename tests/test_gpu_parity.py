@@ -308,3 +308,81 @@ def test_errors_reported():
     # the context stays usable after every error
     x, st = ctx.cg_solve(phi, b)
     assert st["converged"]
+
+
+def test_sdw_susceptibility_matches_oracle():
+    from oracle import observables
+    from paper_2204_14241_gb300.observables import SdwSusceptibility
+    L, Nt = 6, 7
+    ctx = ctx_for(L, Nt, nrhs=1)
+    est = SdwSusceptibility(ctx)
+    samples = [I.gaussian_field(400 + i, L, Nt) for i in range(5)]
+    for s in samples:
+        est.add(dev(s))
+    ref = observables.sdw_susceptibility([I.to_paper_boson(s) for s in samples], 0.1)   # [n, m_x, m_y]
+    got = np.swapaxes(est.value().cpu().numpy(), -1, -2)
+    assert rel(got, ref) < 1e-12
+
+
+def test_paper_preset_runs_and_matches_oracle_force():
+    from paper_2204_14241_gb300 import presets
+    from paper_2204_14241_gb300.hmc import Context
+    kw = presets.paper_nesting(2)
+    L, Nt = 6, 8
+    ctx = Context(L, Nt, solver="mixed", nrhs_max=1, cg_tol=1e-12, **kw)
+    phi = dev(I.gaussian_field(410, L, Nt) * 0.5)
+    pf = dev(I.fermion_noise(411, 1, L, Nt))
+    F, spf, _, _ = ctx.force(phi, pf, include_boson=True, precond=True)
+    P = Params(L=L, Nt=Nt, **kw)
+    Fo, spf_o, _ = ohmc.force(P, I.to_paper_boson(phi.cpu().numpy()), to_paper_vecs(pf), method="dense")
+    assert rel(I.to_paper_boson(F.cpu().numpy()), Fo) < 1e-7 and abs(spf - spf_o) < 1e-10 * abs(spf_o)
+
+
+def test_warmup_tuner_matches_oracle():
+    # Eqs. (acc_ineq) and (ESJD) driven by GPU trajectories against the oracle's tuner on the
+    # same explicit noise: identical step-size decisions, acceptance and ESJD estimates.
+    from oracle import tuning as otuning
+    from paper_2204_14241_gb300.tuning import Tuner
+    L, Nt = 4, 8
+    ctx = ctx_for(L, Nt, "mixed", nrhs=1, tol=1e-12)
+    P = oparams(L, Nt)
+    phi0 = I.gaussian_field(500, L, Nt) * 0.5
+    sig = np.ones((3, Nt, L, L))
+
+    def raw(t):
+        return I.fermion_noise(600 + t, 1, L, Nt), I.gaussian_field(700 + t, L, Nt), I.uniform(800 + t)
+
+    def gpu_noise(t):
+        chi, z, u = raw(t)
+        return dev(chi), dev(z), u
+
+    def cpu_noise(t):
+        chi, z, u = raw(t)
+        return [I.to_paper_fermion(chi[0])], I.to_paper_boson(z), u
+
+    gt = Tuner(ctx, dev(phi0), dev(sig), noise=gpu_noise)
+    ot = otuning.Tuner(P, I.to_paper_boson(phi0), I.to_paper_boson(sig), cpu_noise)
+    e_g, h_g = gt.tune_eps(0.1, rounds=2, window=3)
+    e_o, h_o = ot.tune_eps(0.1, rounds=2, window=3)
+    assert e_g == e_o
+    for a, b in zip(h_g, h_o):
+        assert a[0] == b[0] and abs(a[1] - b[1]) < 1e-7 and abs(a[2] - b[2]) < 1e-7
+    n_g, es_g = gt.tune_nmax(e_g, [1, 2, 4], per_candidate=2)
+    n_o, es_o = ot.tune_nmax(e_o, [1, 2, 4], per_candidate=2)
+    assert n_g == n_o
+    for n in es_g:
+        assert abs(es_g[n] - es_o[n]) < 1e-7 * max(1.0, abs(es_o[n]))
+    assert rel(I.to_paper_boson(gt.phi.cpu().numpy()), ot.phi) < 1e-9
+
+
+def test_mnorm_metric_op():
+    from paper_2204_14241_gb300.hmc import METRIC_MNORM
+    from oracle import tuning as otuning
+    L, Nt = 6, 7
+    ctx = ctx_for(L, Nt)
+    w = np.fft.fftn(I.gaussian_field(510, L, Nt), axes=(1, 2, 3), norm="ortho")
+    sig = (w * np.conj(w)).real + 0.2
+    d = I.gaussian_field(511, L, Nt)
+    got = ctx.metric(METRIC_MNORM, dev(sig), dev(d))
+    ref = otuning.jump_norm2(I.to_paper_boson(sig), I.to_paper_boson(d))
+    assert abs(got - ref) < 1e-12 * ref

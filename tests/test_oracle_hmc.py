@@ -188,3 +188,23 @@ def test_sigma_estimate_recovers_spectrum():
     rel = est / s[None]
     assert abs(rel.mean() - 1.0) < 0.02
     assert np.abs(rel - 1).max() < 0.35
+
+
+def test_sdw_susceptibility_free_field():
+    # Gaussian phi with per-mode variance s(k) in each component: chi = 3 s(k) dtau on average
+    from oracle import observables
+    from paper_2204_14241_gb300 import inputs
+    L, Nt, dt = 4, 6, 0.1
+    s = inputs.spectrum(L, Nt, 0.5, 2.0)
+    samples = [inputs.smooth_field(300 + i, L, Nt, 0.5, 2.0) for i in range(600)]
+    chi = observables.sdw_susceptibility(samples, dt)
+    rel = chi / (3 * s * dt)
+    assert abs(rel.mean() - 1) < 0.02 and np.abs(rel - 1).max() < 0.2
+
+
+def test_presets_follow_the_paper_table():
+    from paper_2204_14241_gb300 import presets
+    p1, p5 = presets.paper_nesting(1), presets.paper_nesting(5)
+    assert p1["t_h"][0] == 1.0 and p1["t_v"][1] == 1.0 and p1["t_v"][0] == 0.45 and p1["t_h"][1] == -0.45
+    assert p1["mu"] == (-0.47, 0.47) and p5["t_v"][0] == 0.5085 and p5["mu"] == (-0.44, 0.44)
+    assert p1["u"] == 0.0 and p1["c"] == 3.0 and abs(p1["g"] - 0.98995) < 1e-4
