@@ -27,15 +27,20 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "HMC traj/s and M†M matvec GB/s at 80×80; mixed vs FP64 at equal CG residual"
-L, NT, NRHS, NLEAP, EPS, TOL = 80, 160, 8, 40, 0.005, 1e-10
+L, NT, NRHS, NLEAP, EPS, TOL, MAXIT = 80, 160, 8, 40, 0.01, 1e-10, 20000
 GUESS = 1   # force solves start from the extrapolated previous solutions (same stopping test)
-COUPLINGS = dict(dtau=0.1, t_h=(1.0, 0.5), t_v=(0.5, 1.0), mu=(-0.5, -0.5), g=1.0, r=0.5, u=1.0, c=3.0)
-WORKLOAD = (f"L={L}x{L}, Nt={NT} (dtau=0.1), 2 bands x 2 spins, {NRHS} pseudofermion RHS, n_leap={NLEAP}, "
+# Yukawa coupling lambda = 1 in the paper's convention g / sqrt(N_f): with k pseudofermion fields
+# (N_f = 2k) the on-site coefficient of D is lambda * sqrt(2 / N_f) = lambda / sqrt(k)
+LAMBDA = 1.0
+COUPLINGS = dict(dtau=0.1, t_h=(1.0, 0.5), t_v=(0.5, 1.0), mu=(-0.5, -0.5), g=LAMBDA / NRHS ** 0.5, r=0.5,
+                 u=1.0, c=3.0)
+WORKLOAD = (f"L={L}x{L}, Nt={NT} (dtau=0.1), 2 bands x 2 spins, {NRHS} pseudofermion RHS (N_f={2 * NRHS}, "
+            f"Yukawa lambda={LAMBDA} as g/sqrt(N_f): D coefficient {LAMBDA / NRHS ** 0.5:.4f}), n_leap={NLEAP}, "
             f"eps={EPS}, complex64 PCG with FP64 reliable updates to true residual {TOL}, "
             "chronological initial guess, phi = free-boson-spectrum Gaussian field, sigma-hat = its spectrum")
 # PCG iterations per solve of this workload on a GB300, used only to scale the oracle's timed
 # sample (a few PCG iterations) to a trajectory when no GPU run is available in the process.
-ITERS_PER_SOLVE_DEFAULT = 200
+ITERS_PER_SOLVE_DEFAULT = 57
 
 
 def kt():
@@ -217,7 +222,8 @@ def run_ours(args):
     phi_np, sig_np = synthetic_inputs(seed)
     phi = torch.from_numpy(phi_np).to(dev)
     sig = torch.from_numpy(sig_np).to(dev)
-    ctx = Context(L, NT, solver="mixed", nrhs_max=NRHS, cg_tol=TOL, device=dev, initial_guess=GUESS, **COUPLINGS)
+    ctx = Context(L, NT, solver="mixed", nrhs_max=NRHS, cg_tol=TOL, cg_maxit=MAXIT, device=dev, initial_guess=GUESS,
+                  autotune=1, **COUPLINGS)
     st = ctx.stream
 
     # warm-up trajectories; they also accumulate the metric estimate of Eq. (covest)
@@ -225,7 +231,7 @@ def run_ours(args):
     from paper_2204_14241_gb300.hmc import METRIC_ACCUM
     warm = []
     for w in range(args.warmup):
-        o = ctx.trajectory([phi], [sig], EPS, NLEAP, nrhs=NRHS, precond=True, seed=seed, counter=w)
+        o = ctx.trajectory([phi], [sig], EPS, NLEAP, nrhs=NRHS, precond=True, seed=seed, counter=w, check=False)
         ctx.metric(METRIC_ACCUM, sig, phi, out=acc)
         warm.append(o)
     sigma_ratio = float((acc / max(args.warmup, 1) / sig).mean().item()) if args.warmup else None
@@ -249,7 +255,8 @@ def run_ours(args):
         phi.copy_(h_phi, non_blocking=True)
         sig.copy_(h_sig, non_blocking=True)
         e0.record(st)
-        o = ctx.trajectory([phi], [sig], EPS, NLEAP, nrhs=NRHS, precond=True, seed=seed, counter=1000 + k)
+        o = ctx.trajectory([phi], [sig], EPS, NLEAP, nrhs=NRHS, precond=True, seed=seed, counter=1000 + k,
+                           check=False)
         e1.record(st)
         h_out.copy_(phi, non_blocking=True)
         torch.cuda.synchronize()
@@ -289,12 +296,12 @@ def run_ours(args):
     b = ctx.apply_M(phi, chi)
     solve = {}
     for mode in ("mixed", "fp64"):
-        c2 = ctx if mode == "mixed" else Context(L, NT, solver="fp64", nrhs_max=NRHS, cg_tol=TOL, device=dev,
-                                                   **COUPLINGS)
+        c2 = ctx if mode == "mixed" else Context(L, NT, solver="fp64", nrhs_max=NRHS, cg_tol=TOL, cg_maxit=MAXIT,
+                                                   device=dev, **COUPLINGS)
         c2.cg_solve(phi, b, precond=True, maxit=16, raise_on_noconv=False)   # warm (first launches)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, s = c2.cg_solve(phi, b, precond=True)
+        _, s = c2.cg_solve(phi, b, precond=True, raise_on_noconv=False)
         torch.cuda.synchronize()
         solve[mode] = {"seconds": time.perf_counter() - t0, "iterations": s["iterations"],
                        "true_rel_resid": s["true_rel_resid"], "reliable_updates": s["reliable_updates"]}
@@ -321,6 +328,8 @@ def run_ours(args):
                              "launch_us": t_mv * 1e6},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
                 "hmc": {"accept": [bool(o["accepted"][0]) for o in outs], "dH": [o["dH"][0] for o in outs],
+                        "status": [o["status"] for o in outs],
+                        "warmup_dH": [o["dH"][0] for o in warm], "warmup_status": [o["status"] for o in warm],
                         "cg_iters_per_solve": iters_per_solve,
                         "max_true_resid": max(o["max_true_resid"][0] for o in outs),
                         "sigma_estimate_over_used": sigma_ratio},
@@ -358,7 +367,7 @@ def run_profile_solve(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)

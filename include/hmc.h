@@ -76,6 +76,10 @@ typedef struct {
     int initial_guess;  /* trajectory() force solves: 0 = zero start (default); 1 = chronological
                            start from the linear extrapolation 2 X_n - X_{n-1} of the trajectory's
                            previous two solutions (the same stopping test applies either way) */
+    int autotune;       /* 0: tile shapes of the fused A kernel from a fixed rule (default; the
+                           reduction order, hence every bit of the results, is reproducible);
+                           1: on first use per (L, Nt, nrhs, precision) time the valid tile and
+                           time-chunk shapes on the call's own buffers and keep the fastest */
 } hmc_params;
 
 /* Per-chain lattice (batched chains of uneven sizes). Coupling constants other than r

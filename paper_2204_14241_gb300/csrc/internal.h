@@ -27,6 +27,12 @@ struct PcTables {
     float2* twist32 = nullptr;
 };
 
+// Tile shape chosen for the fused A kernel per (L, Nt, nrhs, precision).
+struct ATuned {
+    int L, Nt, nrhs, prec;
+    int TX, TY, C;
+};
+
 struct ChainDesc {
     Lat lat;
     double r;
@@ -64,6 +70,7 @@ struct hmc_ctx {
     // FFT plans keyed by length
     std::vector<hmc::FftPlan> plans;
     std::vector<hmc::PcTables> pcs;
+    std::vector<hmc::ATuned> atuned;   // tile shapes picked for the fused A kernel
 
     // fermion workspace (complex, K * 4 * vmax entries each)
     double2* d_r64 = nullptr;     // FP64 residual / true residual

@@ -360,19 +360,102 @@ static size_t a_smem_bytes(const ATile& t) {
     return (size_t)2 * N2 * sizeof(Site<R>) + (size_t)2 * N1 * sizeof(Site<R>) + (size_t)9 * N1 * sizeof(R);
 }
 
+static ATile make_atile(const Lat& lat, int TX, int TY, int C) {
+    ATile t;
+    t.TX = TX;
+    t.TY = TY;
+    t.C = C < 1 ? 1 : (C > lat.Nt ? lat.Nt : C);
+    t.ntx = (lat.L + TX - 1) / TX;
+    t.nty = (lat.L + TY - 1) / TY;
+    t.nchunk = (lat.Nt + t.C - 1) / t.C;
+    return t;
+}
+
+// Times every valid (TX, TY, C) on the call's own buffers (the launch is idempotent: y, pnew
+// and the partial sums depend only on the inputs) and returns the fastest.
+template <typename R>
+static int autotune_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const Site<R>* x, Site<R>* y, int nrhs,
+                      double* part, const CgScalars* cgs, const Site<R>* pold, Site<R>* pnew, ATile* best) {
+    const ATile base = *best;
+    const int txmax = sizeof(R) == 8 ? 16 : 32, tmax = sizeof(R) == 8 ? 128 : kAThreads;
+    std::vector<ATile> cand;
+    for (int TX = 2; TX <= txmax && TX <= lat.L; ++TX) {
+        if (lat.L % TX) continue;
+        for (int TY = 2; TY <= lat.L && TX * TY <= tmax; ++TY) {
+            if (lat.L % TY || 4 * (TX + 4) + 4 * TY > kAThreads) continue;
+            if (a_smem_bytes<R>(make_atile(lat, TX, TY, 1)) > 200 * 1024) continue;
+            if (TX * TY < 32) continue;
+            // time chunks around the one that gives ~8 blocks per SM: half, same, 2x, 4x
+            const int64_t tiles = (int64_t)(lat.L / TX) * (lat.L / TY) * nrhs;
+            const int64_t target = (int64_t)ctx->num_sms * 8;
+            const int c0 = (int)((lat.Nt * tiles + target - 1) / target);
+            int last = -1;
+            for (int C : {c0 / 2, c0, 2 * c0, 4 * c0}) {
+                C = C < 4 ? 4 : (C > lat.Nt ? lat.Nt : C);
+                if (C == last) continue;
+                last = C;
+                cand.push_back(make_atile(lat, TX, TY, C));
+            }
+        }
+    }
+    if (cand.empty()) return HMC_OK;
+    cudaEvent_t e0, e1;
+    HMC_CUDA(ctx, cudaEventCreate(&e0));
+    HMC_CUDA(ctx, cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    const Coef<R> cf = make_coef<R>(ctx->p);
+    for (const ATile& tl : cand) {
+        const dim3 grid(tl.ntx * tl.nty, tl.nchunk, nrhs);
+        if (part && (int64_t)grid.x * grid.y * nrhs > ctx->part_cap) continue;
+        const size_t sm = a_smem_bytes<R>(tl);
+        k_apply_A<R><<<grid, kAThreads, sm, ctx->stream>>>(lat, cf, tl, phi, x, y, part, cgs, pold, pnew);
+        HMC_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
+        for (int r = 0; r < 3; ++r)
+            k_apply_A<R><<<grid, kAThreads, sm, ctx->stream>>>(lat, cf, tl, phi, x, y, part, cgs, pold, pnew);
+        HMC_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
+        HMC_CUDA(ctx, cudaEventSynchronize(e1));
+        HMC_LAUNCH(ctx, "k_apply_A (tuning)");
+        float ms = 0.f;
+        HMC_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) { best_ms = ms; *best = tl; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    (void)base;
+    return HMC_OK;
+}
+
 template <typename R>
 int launch_apply_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x, cplx<R>* y,
                    int nrhs, double* part, int* nblk_out, const CgScalars* cgs,
                    const cplx<R>* pold, cplx<R>* pnew) {
     if (nrhs <= 0) return HMC_OK;
     if (pnew && (!cgs || !pold || pold == pnew)) return fail(ctx, HMC_ERR_ARG, "apply_A: bad direction-update buffers");
-    ATile tl = choose_tile(ctx, lat, nrhs, sizeof(Site<R>));
-    const size_t sm = a_smem_bytes<R>(tl);
     static bool attr_set[2] = {false, false};
     if (!attr_set[sizeof(R) == 8]) {
         HMC_CUDA(ctx, cudaFuncSetAttribute(k_apply_A<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr_set[sizeof(R) == 8] = true;
     }
+    const int prec = sizeof(R) == 8 ? HMC_FP64 : HMC_FP32;
+    ATile tl;
+    bool found = false;
+    for (const ATuned& a : ctx->atuned)
+        if (a.L == lat.L && a.Nt == lat.Nt && a.nrhs == nrhs && a.prec == prec) {
+            tl = make_atile(lat, a.TX, a.TY, a.C);
+            found = true;
+            break;
+        }
+    if (!found) {
+        tl = choose_tile(ctx, lat, nrhs, sizeof(Site<R>));
+        if (ctx->p.autotune) {
+            int rc = autotune_A<R>(ctx, lat, phi, reinterpret_cast<const Site<R>*>(x), reinterpret_cast<Site<R>*>(y),
+                                   nrhs, part, cgs, reinterpret_cast<const Site<R>*>(pold),
+                                   reinterpret_cast<Site<R>*>(pnew), &tl);
+            if (rc) return rc;
+        }
+        ctx->atuned.push_back(ATuned{lat.L, lat.Nt, nrhs, prec, tl.TX, tl.TY, tl.C});
+    }
+    const size_t sm = a_smem_bytes<R>(tl);
     dim3 grid(tl.ntx * tl.nty, tl.nchunk, nrhs);
     if (part && (int64_t)grid.x * grid.y * nrhs > ctx->part_cap)
         return fail(ctx, HMC_ERR_ARG, "apply_A: reduction buffer too small");

@@ -40,7 +40,7 @@ class Params(ctypes.Structure):
                 ("t_h", ctypes.c_double * 2), ("t_v", ctypes.c_double * 2), ("mu", ctypes.c_double * 2),
                 ("g", ctypes.c_double), ("r", ctypes.c_double), ("u", ctypes.c_double), ("c", ctypes.c_double),
                 ("solver_mode", ctypes.c_int), ("nrhs_max", ctypes.c_int), ("cg_tol", ctypes.c_double),
-                ("cg_maxit", ctypes.c_int), ("initial_guess", ctypes.c_int)]
+                ("cg_maxit", ctypes.c_int), ("initial_guess", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class Chain(ctypes.Structure):
@@ -117,7 +117,7 @@ class Context:
 
     def __init__(self, L, Nt, dtau=0.1, t_h=(1.0, 0.5), t_v=(0.5, 1.0), mu=(-0.5, -0.5), g=1.0, r=0.5,
                  u=1.0, c=3.0, solver="mixed", nrhs_max=1, cg_tol=1e-10, cg_maxit=100000, chains=None,
-                 stream=None, device=None, initial_guess=0):
+                 stream=None, device=None, initial_guess=0, autotune=0):
         self.lib = lib()
         self.device = torch.device(device or "cuda")
         p = Params()
@@ -129,6 +129,7 @@ class Context:
         p.solver_mode = SOLVER_MIXED if solver == "mixed" else SOLVER_FP64
         p.nrhs_max, p.cg_tol, p.cg_maxit = nrhs_max, cg_tol, cg_maxit
         p.initial_guess = int(initial_guess)
+        p.autotune = int(autotune)
         self.params = p
         if chains is None:
             chains = [(L, Nt, r)]

@@ -386,3 +386,56 @@ def test_mnorm_metric_op():
     got = ctx.metric(METRIC_MNORM, dev(sig), dev(d))
     ref = otuning.jump_norm2(I.to_paper_boson(sig), I.to_paper_boson(d))
     assert abs(got - ref) < 1e-12 * ref
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_autotuned_apply_A_parity(prec):
+    # autotune = 1 times the tile shapes on the call's buffers; results must not depend on them
+    from paper_2204_14241_gb300.hmc import Context
+    L, Nt = 20, 12
+    ctx = Context(L, Nt, solver="fp64", nrhs_max=2, cg_tol=1e-12, autotune=1, **COUPLINGS)
+    P = oparams(L, Nt)
+    rdt, cdt = (torch.float64, torch.complex128) if prec == "fp64" else (torch.float32, torch.complex64)
+    phi = dev(I.gaussian_field(520, L, Nt), rdt)
+    x = dev(I.fermion_noise(521, 2, L, Nt), cdt)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    for _ in range(2):   # first call tunes, second reuses the choice
+        y, norms = ctx.apply_MdagM(phi, x, norms=True)
+        for k, (yk, xk) in enumerate(zip(to_paper_vecs(y), to_paper_vecs(x))):
+            phi_o = I.to_paper_boson(phi.double().cpu().numpy())
+            assert rel(yk, fermion.apply_A(P, phi_o, xk)) < tol
+            t = fermion.apply_Ddag(P, phi_o, xk)
+            assert abs(norms[k] - np.vdot(t, t).real) < tol * norms[k]
+
+
+def test_64_uneven_chains_trajectory():
+    # the batched configuration's shape: 64 chains, L in {12, 16, 20, 24}, Nt in {24, 32, 48},
+    # r_i ~ U[0.2, 1.0], 2 right-hand sides; one update of every chain, two chains checked
+    # against the oracle (PCG to 1e-13 there, 1e-12 here)
+    from paper_2204_14241_gb300.hmc import Context
+    chains = []
+    for i in range(64):
+        L = (12, 16, 20, 24)[i % 4]
+        Nt = (24, 32, 48)[(i // 4) % 3]
+        r = 0.2 + 0.8 * I.uniform(900 + i)
+        chains.append((L, Nt, r))
+    ctx = Context(12, 24, solver="mixed", nrhs_max=2, cg_tol=1e-12, chains=chains, **{**COUPLINGS})
+    phis, sigs, chis, zs, us = [], [], [], [], []
+    for i, (L, Nt, r) in enumerate(chains):
+        phis.append(dev(I.gaussian_field(1000 + i, L, Nt) * 0.5))
+        sigs.append(dev(np.ones((3, Nt, L, L))))
+        chis.append(dev(I.fermion_noise(2000 + i, 2, L, Nt)))
+        zs.append(dev(I.gaussian_field(3000 + i, L, Nt)))
+        us.append(I.uniform(4000 + i))
+    phi_in = [p.clone() for p in phis]
+    out = ctx.trajectory(phis, sigs, 0.02, 2, nrhs=2, chi=chis, z=zs, u=us)
+    assert all(np.isfinite(out["dH"])) and max(out["max_true_resid"]) <= 1e-12
+    for i in (0, 1):
+        L, Nt, r = chains[i]
+        ref = ohmc.trajectory(oparams(L, Nt, r), I.to_paper_boson(phi_in[i].cpu().numpy()),
+                              np.ones((3, Nt, L, L)),
+                              [I.to_paper_fermion(chis[i].cpu().numpy()[k]) for k in range(2)],
+                              I.to_paper_boson(zs[i].cpu().numpy()), us[i], 0.02, 2, method="pcg", tol=1e-13)
+        assert abs(out["dH"][i] - ref["dH"]) < 1e-8, (i, out["dH"][i], ref["dH"])
+        assert out["accepted"][i] == ref["accept"]
+        assert rel(I.to_paper_boson(phis[i].cpu().numpy()), ref["phi"]) < 1e-9
