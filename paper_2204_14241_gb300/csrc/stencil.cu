@@ -95,29 +95,25 @@ struct ATile {
 };
 
 constexpr int kAThreads = 256;
+template <typename R> struct APf { static constexpr int N = sizeof(R) == 4 ? 2 : 1; };  // halo sites per thread
 
 // With pnew != nullptr the kernel also performs the CG direction update: the operand is
 // p = x + beta_k * pold (x holding z), formed as it is loaded, and the block writes p for the
 // sites it owns (tile interior, slices [t0, t1)) to pnew; y = A p. pold and pnew must differ.
-//
-// Thread roles: thread i < TX*TY owns tile site (i % TX, i / TX) and keeps that site's x(t),
-// t_(t) and t_(t+1) in registers, so its t_ and y need only the four spatial neighbours from
-// shared memory. The remaining sites of the two-site ring (x staging) and of the one-site ring
-// (t_ outputs, phi) are a second slot handled by threads 0, 1, ...
 template <typename R>
-__global__ void __launch_bounds__(kAThreads, sizeof(R) == 4 ? 2 : 1) k_apply_A(Lat lat, Coef<R> cf, ATile tl,
-                                                          const R* __restrict__ phi,
-                                                          const Site<R>* __restrict__ x,
-                                                          Site<R>* __restrict__ y, double* __restrict__ part,
-                                                          const CgScalars* __restrict__ cgs,
-                                                          const Site<R>* __restrict__ pold,
-                                                          Site<R>* __restrict__ pnew) {
+__global__ void __launch_bounds__(kAThreads, 2) k_apply_A(Lat lat, Coef<R> cf, ATile tl,
+                                                       const R* __restrict__ phi,
+                                                       const Site<R>* __restrict__ x,
+                                                       Site<R>* __restrict__ y, double* __restrict__ part,
+                                                       const CgScalars* __restrict__ cgs,
+                                                       const Site<R>* __restrict__ pold,
+                                                       Site<R>* __restrict__ pnew) {
     if (cgs && !cgs[blockIdx.z].active) return;
+    constexpr int NPF = APf<R>::N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int TX = tl.TX, TY = tl.TY;
     const int HX2 = TX + 4, HY2 = TY + 4, N2 = HX2 * HY2;
     const int HX1 = TX + 2, HY1 = TY + 2, N1 = HX1 * HY1;
-    const int NI = TX * TY;
     uint4* xa = reinterpret_cast<uint4*>(smem_raw);
     uint4* xb = xa + Planes<R>::NP * N2;
     uint4* ta = xb + Planes<R>::NP * N2;
@@ -137,183 +133,145 @@ __global__ void __launch_bounds__(kAThreads, sizeof(R) == 4 ? 2 : 1) k_apply_A(L
     const R beta = pnew ? (R)cgs[k].beta : R(0);
     const Site<R>* pok = pnew ? pold + k * V : nullptr;
     Site<R>* pnk = pnew ? pnew + k * V : nullptr;
+
     auto gx = [&](int i) { int v = (x0 + i) % L; return v < 0 ? v + L : v; };
     auto gy = [&](int j) { int v = (y0 + j) % L; return v < 0 ? v + L : v; };
 
-    // ---- per-thread geometry, fixed for the whole march ------------------------------------
-    const int tid = threadIdx.x;
-    // slot 0: own tile site
-    const bool own = tid < NI;
-    int o_ix = 0, o_iy = 0, o_off = -1, o_c2 = 0, o_c1 = 0;
-    R o_eta = R(1);
-    bool o_valid = false;   // inside the lattice (ragged tiles)
-    if (own) {
-        o_ix = tid % TX;
-        o_iy = tid / TX;
-        const int X = gx(o_ix), Y = gy(o_iy);
-        o_valid = x0 + o_ix < L && y0 + o_iy < L;
-        o_off = Y * L + X;
-        o_c2 = (o_iy + 2) * HX2 + o_ix + 2;
-        o_c1 = (o_iy + 1) * HX1 + o_ix + 1;
-        o_eta = ((X + Y) & 1) ? R(-1) : R(1);
-    }
-    // slot 1 of the two-site ring (x staging): ring sites in row-major order
-    int r2_off = -1, r2_c = 0;
-    bool r2_outer = false;
-    {
-        const int q = tid;
-        if (q < N2 - NI) {
-            int hx, hy;
-            if (q < 2 * HX2) { hy = q / HX2; hx = q % HX2; }
-            else if (q < 2 * HX2 + 4 * TY) { const int r = q - 2 * HX2; hy = 2 + r / 4; const int c = r % 4; hx = c < 2 ? c : TX + c; }
-            else { const int r = q - 2 * HX2 - 4 * TY; hy = TY + 2 + r / HX2; hx = r % HX2; }
-            r2_off = gy(hy - 2) * L + gx(hx - 2);
-            r2_c = hy * HX2 + hx;
-            r2_outer = hx == 0 || hy == 0 || hx == HX2 - 1 || hy == HY2 - 1;
+    // Per-thread geometry, fixed for the whole march: in-plane offsets (y * L + x) of this
+    // thread's two-site-ring sites (x loads), one-site-ring sites (phi loads and t_ outputs)
+    // and of its tile site (y output). -1 marks "none".
+    int h2o[NPF], h1o[NPF], mtc[NPF];
+    bool h2own[NPF], h2ring[NPF];
+    R mte[NPF];
+#pragma unroll
+    for (int j = 0; j < NPF; ++j) {
+        const int i = threadIdx.x + j * kAThreads;
+        h2o[j] = -1; h1o[j] = -1; mtc[j] = 0; h2own[j] = false; h2ring[j] = false; mte[j] = R(1);
+        if (i < N2) {
+            const int hx = i % HX2, hy = i / HX2;
+            h2o[j] = gy(hy - 2) * L + gx(hx - 2);
+            h2own[j] = hx >= 2 && hy >= 2 && hx < TX + 2 && hy < TY + 2 && x0 + hx - 2 < L && y0 + hy - 2 < L;
+            h2ring[j] = hx == 0 || hy == 0 || hx == HX2 - 1 || hy == HY2 - 1;
+        }
+        if (i < N1) {
+            const int hx = i % HX1, hy = i / HX1;
+            const int X = gx(hx - 1), Y = gy(hy - 1);
+            h1o[j] = Y * L + X;
+            mtc[j] = (hy + 1) * HX2 + hx + 1;
+            mte[j] = ((X + Y) & 1) ? R(-1) : R(1);
         }
     }
-    // slot 1 of the one-site ring (t_ outputs and phi)
-    int r1_off = -1, r1_c1 = 0, r1_c2 = 0;
-    R r1_eta = R(1);
-    {
-        const int q = tid;
-        if (q < N1 - NI) {
-            int hx, hy;
-            if (q < HX1) { hy = 0; hx = q; }
-            else if (q < HX1 + 2 * TY) { const int r = q - HX1; hy = 1 + r / 2; hx = (r % 2) ? TX + 1 : 0; }
-            else { const int r = q - HX1 - 2 * TY; hy = TY + 1; hx = r; }
-            const int X = gx(hx - 1), Y = gy(hy - 1);
-            r1_off = Y * L + X;
-            r1_c1 = hy * HX1 + hx;
-            r1_c2 = (hy + 1) * HX2 + hx + 1;
-            r1_eta = ((X + Y) & 1) ? R(-1) : R(1);
+    int yo = -1, yc = 0;
+    R ye = R(1);
+    if (threadIdx.x < TX * TY) {
+        const int ix = threadIdx.x % TX, iy = threadIdx.x / TX;
+        const int X = x0 + ix, Y = y0 + iy;
+        if (X < L && Y < L) {
+            yo = Y * L + X;
+            yc = (iy + 1) * HX1 + ix + 1;
+            ye = ((X + Y) & 1) ? R(-1) : R(1);
         }
     }
 
-    // ---- register prefetch of one slice ------------------------------------------------------
-    Site<R> rz0, rp0, rz1, rp1;
-    R ph0[3], ph1[3];
+    // register prefetch of one slice: x on this thread's two-site-ring sites, phi on its
+    // one-site-ring sites
+    Site<R> rz[NPF], rp[NPF];
+    R rph[NPF][3];
     auto fetch = [&](int t) {
         const int64_t base = (int64_t)t * LL;
-        if (own) {
-            rz0 = load_site(xk + base + o_off);
-            if (pnew) rp0 = load_site(pok + base + o_off);
-            const R* pp = phi + base + o_off;
-            ph0[0] = __ldg(pp); ph0[1] = __ldg(pp + V); ph0[2] = __ldg(pp + 2 * V);
-        }
-        if (r2_off >= 0) {
-            rz1 = load_site(xk + base + r2_off);
-            if (pnew) rp1 = load_site(pok + base + r2_off);
-        }
-        if (r1_off >= 0) {
-            const R* pp = phi + base + r1_off;
-            ph1[0] = __ldg(pp); ph1[1] = __ldg(pp + V); ph1[2] = __ldg(pp + 2 * V);
-        }
-    };
-    auto combine = [&](Site<R> v, const Site<R>& po) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            v.c[q].x += beta * po.c[q].x;
-            v.c[q].y += beta * po.c[q].y;
-        }
-        return v;
-    };
-    // Store the prefetched slice t into dst / ph; returns the own site's value. ring1only
-    // skips the outermost ring (slice t0 - 1 is needed on the one-site ring only).
-    auto commit = [&](uint4* dst, R* ph, int t, bool own_write, bool ring1only) -> Site<R> {
-        const int64_t base = (int64_t)t * LL;
-        Site<R> v0 = rz0;
-        if (own) {
-            if (pnew) {
-                v0 = combine(rz0, rp0);
-                if (own_write && o_valid) store_site(pnk + base + o_off, v0);
+        for (int j = 0; j < NPF; ++j) {
+            if (h2o[j] >= 0) {
+                rz[j] = load_site(xk + base + h2o[j]);
+                if (pnew) rp[j] = load_site(pok + base + h2o[j]);
             }
-            sm_store<R>(dst, N2, o_c2, v0);
-            if (ph) { ph[o_c1] = ph0[0]; ph[N1 + o_c1] = ph0[1]; ph[2 * N1 + o_c1] = ph0[2]; }
+            if (h1o[j] >= 0) {
+                const R* pp = phi + base + h1o[j];
+                rph[j][0] = __ldg(pp);
+                rph[j][1] = __ldg(pp + V);
+                rph[j][2] = __ldg(pp + 2 * V);
+            }
         }
-        if (r2_off >= 0 && !(ring1only && r2_outer)) {
-            const Site<R> v1 = pnew ? combine(rz1, rp1) : rz1;
-            sm_store<R>(dst, N2, r2_c, v1);
+    };
+    // store the prefetched slice t (p = z + beta pold, written to pnew where owned)
+    auto commit = [&](uint4* dst, R* ph, int t, bool own, bool ring1only) {
+        const int64_t base = (int64_t)t * LL;
+#pragma unroll
+        for (int j = 0; j < NPF; ++j) {
+            const int i = threadIdx.x + j * kAThreads;
+            if (h2o[j] >= 0 && !(ring1only && h2ring[j])) {
+                Site<R> v = rz[j];
+                if (pnew) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        v.c[q].x += beta * rp[j].c[q].x;
+                        v.c[q].y += beta * rp[j].c[q].y;
+                    }
+                    if (own && h2own[j]) store_site(pnk + base + h2o[j], v);
+                }
+                sm_store<R>(dst, N2, i, v);
+            }
+            if (h1o[j] >= 0 && ph) {
+                ph[i] = rph[j][0];
+                ph[N1 + i] = rph[j][1];
+                ph[2 * N1 + i] = rph[j][2];
+            }
         }
-        if (r1_off >= 0 && ph) { ph[r1_c1] = ph1[0]; ph[N1 + r1_c1] = ph1[1]; ph[2 * N1 + r1_c1] = ph1[2]; }
-        return v0;
+    };
+    // t_(t) = D^dagger x on the one-site ring from x(t) (cur) and x(t-1) (prev)
+    auto make_t = [&](uint4* dst, const uint4* cur, const uint4* prev, const R* ph, int t) {
+        const R tsign = (t == 0) ? R(-1) : R(1);   // b(t-1)
+#pragma unroll
+        for (int j = 0; j < NPF; ++j) {
+            if (h1o[j] < 0) continue;
+            const int i = threadIdx.x + j * kAThreads;
+            const int c = mtc[j];
+            Site<R> o = site_op<R>(cf, sm_load<R>(cur, N2, c), sm_load<R>(cur, N2, c - 1),
+                                   sm_load<R>(cur, N2, c + 1), sm_load<R>(cur, N2, c - HX2),
+                                   sm_load<R>(cur, N2, c + HX2), sm_load<R>(prev, N2, c), tsign,
+                                   ph[i], ph[N1 + i], ph[2 * N1 + i], mte[j]);
+            sm_store<R>(dst, N1, i, o);
+        }
     };
 
-    // ---- prologue: x(t0), x(t0 - 1), t_(t0) ------------------------------------------------
+    // prologue: x(t0) on the two-site ring, x(t0 - 1) on the one-site ring, t_(t0)
     fetch(t0);
-    Site<R> xo_cur = commit(xa, phb, t0, true, false);         // x(t0) at the own site
-    R pho_cur[3] = {ph0[0], ph0[1], ph0[2]};                  // phi(t0) at the own site
+    commit(xa, phb, t0, true, false);
     fetch(tprev(t0, Nt));
-    const Site<R> xo_prev = commit(xb, nullptr, tprev(t0, Nt), false, true);
+    commit(xb, nullptr, tprev(t0, Nt), false, true);
     __syncthreads();
-    Site<R> to_cur;                                             // t_(t0) at the own site
-    {
-        const R tsign = (t0 == 0) ? R(-1) : R(1);
-        if (own) {
-            to_cur = site_op<R>(cf, xo_cur, sm_load<R>(xa, N2, o_c2 - 1), sm_load<R>(xa, N2, o_c2 + 1),
-                                sm_load<R>(xa, N2, o_c2 - HX2), sm_load<R>(xa, N2, o_c2 + HX2), xo_prev, tsign,
-                                pho_cur[0], pho_cur[1], pho_cur[2], o_eta);
-            sm_store<R>(ta, N1, o_c1, to_cur);
-        }
-        if (r1_off >= 0) {
-            const int c = r1_c2;
-            const Site<R> o = site_op<R>(cf, sm_load<R>(xa, N2, c), sm_load<R>(xa, N2, c - 1),
-                                         sm_load<R>(xa, N2, c + 1), sm_load<R>(xa, N2, c - HX2),
-                                         sm_load<R>(xa, N2, c + HX2), sm_load<R>(xb, N2, c), tsign,
-                                         phb[r1_c1], phb[N1 + r1_c1], phb[2 * N1 + r1_c1], r1_eta);
-            sm_store<R>(ta, N1, r1_c1, o);
-        }
-    }
+    make_t(ta, xa, xb, phb, t0);
     fetch(tnext(t0, Nt));
     __syncthreads();
 
-    // ---- march -------------------------------------------------------------------------------
     uint4 *xc = xa, *xn = xb, *tc = ta, *tn = tb;
     int pc = 0;   // phi(t) is in buffer pc of the three at phb
-    R acc = 0;    // per-thread partial of ||D^dagger x||^2, in the operator's precision
+    R acc = 0;   // per-thread partial in the operator's precision
     for (int t = t0; t < t1; ++t) {
         const int tp = tnext(t, Nt);
         const int pn = pc == 2 ? 0 : pc + 1;
         R* phn = phb + pn * 3 * N1;
-        const Site<R> xo_next = commit(xn, phn, tp, t + 1 < t1, false);
-        const R pho_next[3] = {ph0[0], ph0[1], ph0[2]};
+        commit(xn, phn, tp, t + 1 < t1, false);
         if (t + 1 < t1) fetch(tnext(tp, Nt));
         __syncthreads();
-        // t_(t+1) = D^dagger x at slice t+1 on the one-site ring
-        const R tsg = (tp == 0) ? R(-1) : R(1);   // b(t)
-        Site<R> to_next;
-        if (own) {
-            to_next = site_op<R>(cf, xo_next, sm_load<R>(xn, N2, o_c2 - 1), sm_load<R>(xn, N2, o_c2 + 1),
-                                 sm_load<R>(xn, N2, o_c2 - HX2), sm_load<R>(xn, N2, o_c2 + HX2), xo_cur, tsg,
-                                 pho_next[0], pho_next[1], pho_next[2], o_eta);
-            sm_store<R>(tn, N1, o_c1, to_next);
-        }
-        if (r1_off >= 0) {
-            const int c = r1_c2;
-            const Site<R> o = site_op<R>(cf, sm_load<R>(xn, N2, c), sm_load<R>(xn, N2, c - 1),
-                                         sm_load<R>(xn, N2, c + 1), sm_load<R>(xn, N2, c - HX2),
-                                         sm_load<R>(xn, N2, c + HX2), sm_load<R>(xc, N2, c), tsg,
-                                         phn[r1_c1], phn[N1 + r1_c1], phn[2 * N1 + r1_c1], r1_eta);
-            sm_store<R>(tn, N1, r1_c1, o);
-        }
+        make_t(tn, xn, xc, phn, tp);
         __syncthreads();
         // y(t) = D t_ on the tile
-        if (own) {
+        if (yo >= 0) {
             const R tsign = (t == Nt - 1) ? R(-1) : R(1);   // b(t)
-            const int c = o_c1;
-            const Site<R> o = site_op<R>(cf, to_cur, sm_load<R>(tc, N1, c - 1), sm_load<R>(tc, N1, c + 1),
-                                         sm_load<R>(tc, N1, c - HX1), sm_load<R>(tc, N1, c + HX1), to_next, tsign,
-                                         pho_cur[0], pho_cur[1], pho_cur[2], o_eta);
-            if (o_valid) {
-                store_site(yk + (int64_t)t * LL + o_off, o);
-                if (part) {
+            const R* ph = phb + pc * 3 * N1;
+            const int c = yc;
+            const Site<R> tcen = sm_load<R>(tc, N1, c);
+            Site<R> o = site_op<R>(cf, tcen, sm_load<R>(tc, N1, c - 1), sm_load<R>(tc, N1, c + 1),
+                                   sm_load<R>(tc, N1, c - HX1), sm_load<R>(tc, N1, c + HX1),
+                                   sm_load<R>(tn, N1, c), tsign, ph[c], ph[N1 + c], ph[2 * N1 + c], ye);
+            store_site(yk + (int64_t)t * LL + yo, o);
+            if (part) {
+                R n2 = 0;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc += to_cur.c[q].x * to_cur.c[q].x + to_cur.c[q].y * to_cur.c[q].y;
-                }
+                for (int q = 0; q < 4; ++q) n2 += tcen.c[q].x * tcen.c[q].x + tcen.c[q].y * tcen.c[q].y;
+                acc += n2;
             }
-            xo_cur = xo_next;
-            to_cur = to_next;
-            pho_cur[0] = pho_next[0]; pho_cur[1] = pho_next[1]; pho_cur[2] = pho_next[2];
         }
         uint4* sw = xc; xc = xn; xn = sw;
         sw = tc; tc = tn; tn = sw;
@@ -338,10 +296,11 @@ static ATile choose_tile(const hmc_ctx* ctx, const Lat& lat, int nrhs, size_t si
     if (lat.L % 16 == 0 && site_bytes <= 32) t.TX = 16;
     int cap = (site_bytes > 32 ? 128 : 256) / t.TX;
     t.TY = largest_divisor_le(lat.L, cap < 1 ? 1 : cap);
-    // one tile site per thread (TY <= kAThreads / TX) and at most one ring site per thread
-    auto ring2 = [](const ATile& a) { return 4 * (a.TX + 4) + 4 * a.TY; };
-    while (ring2(t) > kAThreads && t.TY > 1) t.TY = largest_divisor_le(lat.L, t.TY - 1);
-    while (ring2(t) > kAThreads && t.TX > 1) t.TX = largest_divisor_le(lat.L, t.TX - 1);
+    // each thread stages at most NPF two-site-ring sites (TY <= kAThreads / TX keeps the tile
+    // within one output site per thread)
+    const int n2max = (site_bytes > 32 ? 1 : 2) * kAThreads;
+    while ((t.TX + 4) * (t.TY + 4) > n2max && t.TY > 1) t.TY = largest_divisor_le(lat.L, t.TY - 1);
+    while ((t.TX + 4) * (t.TY + 4) > n2max && t.TX > 1) t.TX = largest_divisor_le(lat.L, t.TX - 1);
     t.ntx = (lat.L + t.TX - 1) / t.TX;
     t.nty = (lat.L + t.TY - 1) / t.TY;
     const int64_t tiles = (int64_t)t.ntx * t.nty * nrhs;
@@ -382,7 +341,7 @@ static int autotune_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const Site<R>*
     for (int TX = 2; TX <= txmax && TX <= lat.L; ++TX) {
         if (lat.L % TX) continue;
         for (int TY = 2; TY <= lat.L && TX * TY <= tmax; ++TY) {
-            if (lat.L % TY || 4 * (TX + 4) + 4 * TY > kAThreads) continue;
+            if (lat.L % TY || (TX + 4) * (TY + 4) > (sizeof(R) == 8 ? 1 : 2) * kAThreads) continue;
             if (a_smem_bytes<R>(make_atile(lat, TX, TY, 1)) > 200 * 1024) continue;
             if (TX * TY < 32) continue;
             // time chunks around the one that gives ~8 blocks per SM: half, same, 2x, 4x
