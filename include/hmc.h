@@ -119,6 +119,31 @@ int apply_M(hmc_ctx* ctx, int chain, int prec, const void* phi, const void* x, v
 int apply_MdagM(hmc_ctx* ctx, int chain, int prec, const void* phi, const void* x, void* y,
                 int nrhs, double* norm2);
 
+/* Allocation-free variant of apply_MdagM, for callers that must not allocate device memory
+ * after start-up: code running under a memory pool or budget fixed in advance, an embedding
+ * runtime that owns every allocation, or a caller that cannot use hmc_init because hmc_init
+ * allocates its workspace. There is no counterpart in the paper; it computes exactly what
+ * apply_MdagM computes (y = D D^dagger x and, if norm2 is not NULL, ||D^dagger x_k||^2 per
+ * right-hand side into host memory) but takes the model parameters directly instead of a
+ * context and keeps its reduction scratch in a fixed file-scope device array of 65536
+ * doubles (512 KiB) plus 64 doubles of row sums, resident on every GPU that loads the library
+ * until the process exits. It calls no cudaMalloc, cudaFree or allocating library routine.
+ *   p: model parameters (only dtau, t_h, t_v, mu and g are read); L, Nt: lattice; prec:
+ *   HMC_FP64 or HMC_FP32 (as for apply_MdagM); phi, x, y: device, layouts as for apply_MdagM,
+ *   16-byte aligned, x and y disjoint; nrhs >= 1 (<= 64 when norm2 is requested);
+ *   cuda_stream: cudaStream_t or NULL for the default stream.
+ * Set-up: the first call on each device (with that device current) looks up the device
+ * address of the scratch array (cudaGetSymbolAddress); make that first call before any
+ * stream capture. Every call on a device shares the one array and overwrites it, and each
+ * slot it reads back is written earlier in the same call, so nothing needs clearing; calls
+ * that can overlap on the GPU (other streams, other host threads) race on the array and
+ * must be serialised by the caller. With norm2 the call synchronises cuda_stream.
+ * Errors: HMC_ERR_ARG for bad arguments, and when nrhs times the number of tile blocks of
+ * the fused kernel exceeds the 65536 scratch slots (the message gives both numbers);
+ * HMC_ERR_CUDA for runtime failures. The message is available from hmc_last_error(NULL). */
+int apply_MdagM_static(const hmc_params* p, int L, int Nt, int prec, const void* phi, const void* x, void* y,
+                       int nrhs, double* norm2, void* cuda_stream);
+
 /* y = P x with P = (K K^dagger)^{-1} = F~ P-hat F~^* (Eqs. Dsplit, twist, Kdiag, precon),
  * K the phi-independent part of D, applied with the twisted FFT. x, y: [nrhs][V][4] in prec. */
 int apply_precond(hmc_ctx* ctx, int chain, int prec, const void* x, void* y, int nrhs);

@@ -1,5 +1,7 @@
 // Fermion-matrix stencils (Eq. D_formula), the fused normal operator A = D D^dagger
 // (Eq. linsys), and the fused force kernel (Eq. hamiltonseq with S = S_B + S_PF).
+#include <mutex>
+
 #include "internal.h"
 
 namespace hmc {
@@ -290,7 +292,11 @@ static int largest_divisor_le(int L, int cap) {
     return 1;
 }
 
+static ATile choose_tile_sms(int num_sms, const Lat& lat, int nrhs, size_t site_bytes);
 static ATile choose_tile(const hmc_ctx* ctx, const Lat& lat, int nrhs, size_t site_bytes) {
+    return choose_tile_sms(ctx->num_sms, lat, nrhs, site_bytes);
+}
+static ATile choose_tile_sms(int num_sms, const Lat& lat, int nrhs, size_t site_bytes) {
     ATile t;
     t.TX = largest_divisor_le(lat.L, site_bytes > 32 ? 16 : 32);
     if (lat.L % 16 == 0 && site_bytes <= 32) t.TX = 16;
@@ -304,7 +310,7 @@ static ATile choose_tile(const hmc_ctx* ctx, const Lat& lat, int nrhs, size_t si
     t.ntx = (lat.L + t.TX - 1) / t.TX;
     t.nty = (lat.L + t.TY - 1) / t.TY;
     const int64_t tiles = (int64_t)t.ntx * t.nty * nrhs;
-    const int64_t target = (int64_t)ctx->num_sms * 8;
+    const int64_t target = (int64_t)num_sms * 8;
     int C = (int)((lat.Nt * tiles + target - 1) / target);
     if (C < 4) C = 4;
     if (C > lat.Nt) C = lat.Nt;
@@ -431,6 +437,113 @@ template int launch_apply_A<float>(hmc_ctx*, const Lat&, const float*, const flo
                                    const CgScalars*, const float2*, float2*);
 template int launch_apply_A<double>(hmc_ctx*, const Lat&, const double*, const double2*, double2*, int, double*, int*,
                                     const CgScalars*, const double2*, double2*);
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant of apply_MdagM for callers that cannot allocate device memory at
+// call time. The per-block partial sums of ||D^dagger x||^2 and their row sums live in
+// file-scope device arrays of fixed size instead of context workspace.
+constexpr int64_t kStaticPartials = 1 << 16;   // partial sums (doubles): 512 KiB per device
+constexpr int kStaticRows = 64;                // reduced sums: nrhs <= 64
+static __device__ __align__(256) double g_static_part[kStaticPartials];
+static __device__ __align__(256) double g_static_rows[kStaticRows];
+
+struct StaticScratch {
+    double* part = nullptr;   // device addresses of the arrays above on one device
+    double* rows = nullptr;
+    int num_sms = 0;
+};
+static std::mutex g_static_mu;
+static StaticScratch g_static[64];   // by device ordinal
+
+// Device addresses of the static arrays on the current device, resolved once per device.
+static int static_scratch(StaticScratch** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_check(nullptr, e, "apply_MdagM_static: cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: device ordinal >= 64");
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    StaticScratch& sc = g_static[dev];
+    if (!sc.part) {
+        void* a = nullptr;
+        void* b = nullptr;
+        if ((e = cudaGetSymbolAddress(&a, g_static_part)) != cudaSuccess)
+            return cuda_check(nullptr, e, "apply_MdagM_static: cudaGetSymbolAddress");
+        if ((e = cudaGetSymbolAddress(&b, g_static_rows)) != cudaSuccess)
+            return cuda_check(nullptr, e, "apply_MdagM_static: cudaGetSymbolAddress");
+        if ((e = cudaDeviceGetAttribute(&sc.num_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return cuda_check(nullptr, e, "apply_MdagM_static: device query");
+        sc.rows = static_cast<double*>(b);
+        sc.part = static_cast<double*>(a);
+    }
+    *out = &sc;
+    return HMC_OK;
+}
+
+__global__ void __launch_bounds__(256) k_static_rows(const double* __restrict__ part, int nblk,
+                                                     double* __restrict__ out) {
+    __shared__ double red[8];
+    const double* row = part + (int64_t)blockIdx.x * nblk;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += row[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+template <typename R>
+static int apply_A_static(const hmc_params* p, const Lat& lat, const R* phi, const Site<R>* x, Site<R>* y,
+                          int nrhs, double* norm2, cudaStream_t stream) {
+    StaticScratch* sc = nullptr;
+    int rc = static_scratch(&sc);
+    if (rc) return rc;
+    const ATile tl = choose_tile_sms(sc->num_sms, lat, nrhs, sizeof(Site<R>));
+    const dim3 grid(tl.ntx * tl.nty, tl.nchunk, nrhs);
+    const int64_t nblk = (int64_t)grid.x * grid.y;
+    if (norm2 && nblk * nrhs > kStaticPartials)
+        return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: " + std::to_string(nblk * nrhs) +
+                    " partial sums exceed the static scratch of " + std::to_string(kStaticPartials));
+    const size_t sm = a_smem_bytes<R>(tl);
+    cudaError_t e = cudaFuncSetAttribute(k_apply_A<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return cuda_check(nullptr, e, "apply_MdagM_static: cudaFuncSetAttribute");
+    k_apply_A<R><<<grid, kAThreads, sm, stream>>>(lat, make_coef<R>(*p), tl, phi, x, y, norm2 ? sc->part : nullptr,
+                                                  nullptr, nullptr, nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(nullptr, e, "apply_MdagM_static: k_apply_A");
+    if (!norm2) return HMC_OK;
+    k_static_rows<<<nrhs, 256, 0, stream>>>(sc->part, (int)nblk, sc->rows);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(nullptr, e, "apply_MdagM_static: k_static_rows");
+    if ((e = cudaMemcpyAsync(norm2, sc->rows, nrhs * sizeof(double), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+        return cuda_check(nullptr, e, "apply_MdagM_static: copy of the norms");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_check(nullptr, e, "apply_MdagM_static: sync");
+    return HMC_OK;
+}
+
+}  // namespace hmc
+
+extern "C" int apply_MdagM_static(const hmc_params* p, int L, int Nt, int prec, const void* phi, const void* x,
+                                  void* y, int nrhs, double* norm2, void* cuda_stream) {
+    using namespace hmc;
+    if (!p || !phi || !x || !y) return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: null argument");
+    if ((((uintptr_t)phi) | ((uintptr_t)x) | ((uintptr_t)y)) & 15u)
+        return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: pointer not 16-byte aligned");
+    if (x == y) return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: x and y must not overlap");
+    if (L < 2 || (L & 1) || L > 4096 || Nt < 2 || Nt > 65536)
+        return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: need even L in [2, 4096] and Nt in [2, 65536]");
+    if (nrhs < 1 || (norm2 && nrhs > kStaticRows) || nrhs > 65535)
+        return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: nrhs must be in [1, 64] when norms are requested");
+    Lat lat;
+    lat.L = L;
+    lat.Nt = Nt;
+    lat.V = (int64_t)Nt * L * L;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (prec == HMC_FP64)
+        return apply_A_static<double>(p, lat, (const double*)phi, (const Site<double>*)x, (Site<double>*)y, nrhs,
+                                      norm2, st);
+    if (prec == HMC_FP32)
+        return apply_A_static<float>(p, lat, (const float*)phi, (const Site<float>*)x, (Site<float>*)y, nrhs,
+                                     norm2, st);
+    return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: unknown precision");
+}
+
+namespace hmc {
 
 // ---------------------------------------------------------------------------------------
 // Boson pieces: -dS_B/dphi and the S_B density (forward differences, see oracle reading).

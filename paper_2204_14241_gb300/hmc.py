@@ -25,7 +25,8 @@ NOISE_EXPLICIT, NOISE_PHILOX = 0, 1
 METRIC_MOMENTUM, METRIC_VELOCITY, METRIC_KINETIC, METRIC_ACCUM, METRIC_MNORM = range(5)
 
 # every function declared in include/hmc.h
-EXPORTS = ("hmc_init", "hmc_destroy", "hmc_last_error", "hmc_counters", "apply_M", "apply_MdagM", "apply_precond",
+EXPORTS = ("hmc_init", "hmc_destroy", "hmc_last_error", "hmc_counters", "apply_M", "apply_MdagM",
+           "apply_MdagM_static", "apply_precond",
            "cg_solve", "force", "metric_apply", "trajectory", "philox_raw", "philox_normal")
 
 
@@ -91,6 +92,8 @@ def lib():
         "hmc_counters": [_P, ctypes.POINTER(ctypes.c_int64)],
         "apply_M": [_P, _I, _I, _P, _P, _P, _I, _I],
         "apply_MdagM": [_P, _I, _I, _P, _P, _P, _I, ctypes.POINTER(ctypes.c_double)],
+        "apply_MdagM_static": [ctypes.POINTER(Params), _I, _I, _I, _P, _P, _P, _I, ctypes.POINTER(ctypes.c_double),
+                               _P],
         "apply_precond": [_P, _I, _I, _P, _P, _I],
         "cg_solve": [_P, _I, _P, _P, _P, _I, ctypes.c_double, _I, _I, ctypes.POINTER(CgStats)],
         "force": [_P, _I, _P, _P, _I, _P, ctypes.POINTER(ctypes.c_double), _I, _I,
@@ -110,6 +113,27 @@ def lib():
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def apply_MdagM_static(params, L, Nt, phi, x, out, norms=False, stream=None):
+    """y = D D^dagger x without allocating device memory (libhmc's apply_MdagM_static): for
+    callers that must not allocate after start-up. `params` is a Params (or a Context's
+    .params); `out` is caller-allocated like x. Returns out, or (out, norms) when norms is set."""
+    lib_ = lib()
+    if x.dtype == torch.complex128:
+        prec = FP64
+    elif x.dtype == torch.complex64:
+        prec = FP32
+    else:
+        raise ValueError("fermion vectors must be complex128 or complex64")
+    k = x.shape[0]
+    nrm = (ctypes.c_double * k)() if norms else None
+    st = stream if stream is not None else torch.cuda.current_stream(x.device)
+    rc = lib_.apply_MdagM_static(ctypes.byref(params), L, Nt, prec, _ptr(phi), _ptr(x), _ptr(out), k, nrm,
+                                 ctypes.c_void_p(st.cuda_stream))
+    if rc:
+        raise HmcError(rc, lib_.hmc_last_error(None).decode())
+    return (out, list(nrm)) if norms else out
 
 
 class Context:
