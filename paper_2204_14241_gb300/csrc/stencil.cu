@@ -102,14 +102,13 @@ template <typename R> struct APf { static constexpr int N = sizeof(R) == 4 ? 2 :
 // With pnew != nullptr the kernel also performs the CG direction update: the operand is
 // p = x + beta_k * pold (x holding z), formed as it is loaded, and the block writes p for the
 // sites it owns (tile interior, slices [t0, t1)) to pnew; y = A p. pold and pnew must differ.
-template <typename R>
-__global__ void __launch_bounds__(kAThreads, 2) k_apply_A(Lat lat, Coef<R> cf, ATile tl,
-                                                       const R* __restrict__ phi,
-                                                       const Site<R>* __restrict__ x,
-                                                       Site<R>* __restrict__ y, double* __restrict__ part,
-                                                       const CgScalars* __restrict__ cgs,
-                                                       const Site<R>* __restrict__ pold,
-                                                       Site<R>* __restrict__ pnew) {
+// PUPD: the direction-update variant used inside PCG (pnew, pold non-null); otherwise the
+// plain operator. The plain variant carries no second prefetch register set.
+template <typename R, bool PUPD>
+__global__ void __launch_bounds__(kAThreads, 2)
+k_apply_A(Lat lat, Coef<R> cf, ATile tl, const R* __restrict__ phi, const Site<R>* __restrict__ x,
+          Site<R>* __restrict__ y, double* __restrict__ part, const CgScalars* __restrict__ cgs,
+          const Site<R>* __restrict__ pold, Site<R>* __restrict__ pnew) {
     if (cgs && !cgs[blockIdx.z].active) return;
     constexpr int NPF = APf<R>::N;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -132,9 +131,9 @@ __global__ void __launch_bounds__(kAThreads, 2) k_apply_A(Lat lat, Coef<R> cf, A
     const int k = blockIdx.z;
     const Site<R>* xk = x + k * V;
     Site<R>* yk = y + k * V;
-    const R beta = pnew ? (R)cgs[k].beta : R(0);
-    const Site<R>* pok = pnew ? pold + k * V : nullptr;
-    Site<R>* pnk = pnew ? pnew + k * V : nullptr;
+    const R beta = PUPD ? (R)cgs[k].beta : R(0);
+    const Site<R>* pok = PUPD ? pold + k * V : nullptr;
+    Site<R>* pnk = PUPD ? pnew + k * V : nullptr;
 
     auto gx = [&](int i) { int v = (x0 + i) % L; return v < 0 ? v + L : v; };
     auto gy = [&](int j) { int v = (y0 + j) % L; return v < 0 ? v + L : v; };
@@ -177,7 +176,8 @@ __global__ void __launch_bounds__(kAThreads, 2) k_apply_A(Lat lat, Coef<R> cf, A
 
     // register prefetch of one slice: x on this thread's two-site-ring sites, phi on its
     // one-site-ring sites
-    Site<R> rz[NPF], rp[NPF];
+    Site<R> rz[NPF];
+    Site<R> rp[PUPD ? NPF : 1];
     R rph[NPF][3];
     auto fetch = [&](int t) {
         const int64_t base = (int64_t)t * LL;
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kAThreads, 2) k_apply_A(Lat lat, Coef<R> cf, A
         for (int j = 0; j < NPF; ++j) {
             if (h2o[j] >= 0) {
                 rz[j] = load_site(xk + base + h2o[j]);
-                if (pnew) rp[j] = load_site(pok + base + h2o[j]);
+                if constexpr (PUPD) rp[j] = load_site(pok + base + h2o[j]);
             }
             if (h1o[j] >= 0) {
                 const R* pp = phi + base + h1o[j];
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kAThreads, 2) k_apply_A(Lat lat, Coef<R> cf, A
             const int i = threadIdx.x + j * kAThreads;
             if (h2o[j] >= 0 && !(ring1only && h2ring[j])) {
                 Site<R> v = rz[j];
-                if (pnew) {
+                if constexpr (PUPD) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         v.c[q].x += beta * rp[j].c[q].x;
@@ -373,10 +373,13 @@ static int autotune_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const Site<R>*
         const dim3 grid(tl.ntx * tl.nty, tl.nchunk, nrhs);
         if (part && (int64_t)grid.x * grid.y * nrhs > ctx->part_cap) continue;
         const size_t sm = a_smem_bytes<R>(tl);
-        k_apply_A<R><<<grid, kAThreads, sm, ctx->stream>>>(lat, cf, tl, phi, x, y, part, cgs, pold, pnew);
+        auto go = [&]() {
+            if (pnew) k_apply_A<R, true><<<grid, kAThreads, sm, ctx->stream>>>(lat, cf, tl, phi, x, y, part, cgs, pold, pnew);
+            else k_apply_A<R, false><<<grid, kAThreads, sm, ctx->stream>>>(lat, cf, tl, phi, x, y, part, cgs, pold, pnew);
+        };
+        go();
         HMC_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
-        for (int r = 0; r < 3; ++r)
-            k_apply_A<R><<<grid, kAThreads, sm, ctx->stream>>>(lat, cf, tl, phi, x, y, part, cgs, pold, pnew);
+        for (int r = 0; r < 3; ++r) go();
         HMC_CUDA(ctx, cudaEventRecord(e1, ctx->stream));
         HMC_CUDA(ctx, cudaEventSynchronize(e1));
         HMC_LAUNCH(ctx, "k_apply_A (tuning)");
@@ -396,10 +399,11 @@ int launch_apply_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x,
                    const cplx<R>* pold, cplx<R>* pnew) {
     if (nrhs <= 0) return HMC_OK;
     if (pnew && (!cgs || !pold || pold == pnew)) return fail(ctx, HMC_ERR_ARG, "apply_A: bad direction-update buffers");
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[sizeof(R) == 8]) {
-        HMC_CUDA(ctx, cudaFuncSetAttribute(k_apply_A<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr_set[sizeof(R) == 8] = true;
+    static bool attr_set = false;
+    if (!attr_set) {
+        HMC_CUDA(ctx, cudaFuncSetAttribute(k_apply_A<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        HMC_CUDA(ctx, cudaFuncSetAttribute(k_apply_A<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr_set = true;
     }
     const int prec = sizeof(R) == 8 ? HMC_FP64 : HMC_FP32;
     ATile tl;
@@ -424,11 +428,17 @@ int launch_apply_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x,
     dim3 grid(tl.ntx * tl.nty, tl.nchunk, nrhs);
     if (part && (int64_t)grid.x * grid.y * nrhs > ctx->part_cap)
         return fail(ctx, HMC_ERR_ARG, "apply_A: reduction buffer too small");
-    k_apply_A<R><<<grid, kAThreads, sm, ctx->stream>>>(lat, make_coef<R>(ctx->p), tl, phi,
-                                                 reinterpret_cast<const Site<R>*>(x),
-                                                 reinterpret_cast<Site<R>*>(y), part, cgs,
-                                                 reinterpret_cast<const Site<R>*>(pold),
-                                                 reinterpret_cast<Site<R>*>(pnew));
+    if (pnew)
+        k_apply_A<R, true><<<grid, kAThreads, sm, ctx->stream>>>(lat, make_coef<R>(ctx->p), tl, phi,
+                                                                 reinterpret_cast<const Site<R>*>(x),
+                                                                 reinterpret_cast<Site<R>*>(y), part, cgs,
+                                                                 reinterpret_cast<const Site<R>*>(pold),
+                                                                 reinterpret_cast<Site<R>*>(pnew));
+    else
+        k_apply_A<R, false><<<grid, kAThreads, sm, ctx->stream>>>(lat, make_coef<R>(ctx->p), tl, phi,
+                                                                  reinterpret_cast<const Site<R>*>(x),
+                                                                  reinterpret_cast<Site<R>*>(y), part, cgs,
+                                                                  nullptr, nullptr);
     HMC_LAUNCH(ctx, "k_apply_A");
     if (nblk_out) *nblk_out = grid.x * grid.y;
     return HMC_OK;
@@ -502,10 +512,10 @@ static int apply_A_static(const hmc_params* p, const Lat& lat, const R* phi, con
         return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: " + std::to_string(nblk * nrhs) +
                     " partial sums exceed the static scratch of " + std::to_string(kStaticPartials));
     const size_t sm = a_smem_bytes<R>(tl);
-    cudaError_t e = cudaFuncSetAttribute(k_apply_A<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_apply_A<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return cuda_check(nullptr, e, "apply_MdagM_static: cudaFuncSetAttribute");
-    k_apply_A<R><<<grid, kAThreads, sm, stream>>>(lat, make_coef<R>(*p), tl, phi, x, y, norm2 ? sc->part : nullptr,
-                                                  nullptr, nullptr, nullptr);
+    k_apply_A<R, false><<<grid, kAThreads, sm, stream>>>(lat, make_coef<R>(*p), tl, phi, x, y,
+                                                         norm2 ? sc->part : nullptr, nullptr, nullptr, nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_check(nullptr, e, "apply_MdagM_static: k_apply_A");
     if (!norm2) return HMC_OK;
     k_static_rows<<<nrhs, 256, 0, stream>>>(sc->part, (int)nblk, sc->rows);
