@@ -166,6 +166,16 @@ int cg_solve(hmc_ctx* ctx, int chain, const void* phi, const void* b, void* x, i
 int force(hmc_ctx* ctx, int chain, const void* phi, const void* phi_pf, int nrhs, void* F,
           double* S_pf, int include_boson, int precond, double* S_b, hmc_cg_stats* st);
 
+/* Randomized diagonal estimator of Section "Fermionic observables": out = (1/K) sum_k
+ * v_k . (O v_k) with O = F~^* D^{-1} F~ (the fermion Green's function in the twisted Fourier
+ * basis of Eqs. twist, Kdiag), D^{-1} = D^dagger (D D^dagger)^{-1}, for K = nrhs probe vectors
+ * with entries +-1 (E[v . O v] = diag(O)). The K solves are one multi-RHS CG (context tolerance;
+ * precond as for cg_solve). phi: [3][V] double; v: [nrhs][V][4] complex128 (real parts +-1,
+ * imaginary parts 0) in the twisted Fourier basis, site index (n_tau * L + m_y) * L + m_x;
+ * out: [V][4] complex128 in the same basis. st may be NULL. */
+int green_estimate(hmc_ctx* ctx, int chain, const void* phi, const void* v, int nrhs, void* out, int precond,
+                   hmc_cg_stats* st);
+
 /* Fourier-diagonal metric of Section "Online metric estimation" with the unitary DFT F
  * over (tau, y, x) per component and sigma-hat even in the wave vector:
  *   HMC_METRIC_MOMENTUM: out = F^{-1}(sigma^{-1/2} . F in)   (momentum draw from z = in)

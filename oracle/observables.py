@@ -14,3 +14,31 @@ def sdw_susceptibility(samples, dtau):
         term = np.sum(np.abs(ph) ** 2, axis=0)
         acc = term if acc is None else acc + term
     return acc * dtau / len(samples)
+
+
+def twisted_fourier(p, v, inverse):
+    """F~ v = T F v (inverse = True: T times the inverse unitary DFT) or F~^* v = F^* (T^* v)
+    over (tau, x, y), T = diag(e^{i pi tau / Nt}) (Eqs. twist, Kdiag)."""
+    from .solver import twist
+    T = twist(p)
+    if inverse:
+        return T * np.fft.ifftn(v, axes=(2, 3, 4), norm="ortho")
+    return np.fft.fftn(np.conj(T) * v, axes=(2, 3, 4), norm="ortho")
+
+
+def green_diagonal(p, phi, probes, method="dense", tol=1e-12):
+    """Randomized diagonal estimator (Section "Fermionic observables"): diag(O) = E[v . O v]
+    for Rademacher v, with O = F~^* D^{-1} F~ and D^{-1} = D^dagger (D D^dagger)^{-1}.
+    probes: list of real +-1 arrays of fermion shape; returns the sample mean of v . O v."""
+    from . import fermion, solver
+    acc = None
+    for v in probes:
+        w = twisted_fourier(p, v.astype(complex), inverse=True)
+        if method == "dense":
+            u = solver.dense_solve(p, phi, w)
+        else:
+            u, _, _ = solver.pcg(p, phi, w, tol=tol)
+        ov = twisted_fourier(p, fermion.apply_Ddag(p, phi, u), inverse=False)
+        term = v * ov
+        acc = term if acc is None else acc + term
+    return acc / len(probes)

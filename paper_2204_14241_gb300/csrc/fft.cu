@@ -547,6 +547,74 @@ template int launch_cg_update_precond<float>(hmc_ctx*, const Lat&, float2*, floa
 template int launch_cg_update_precond<double>(hmc_ctx*, const Lat&, double2*, double2*, const double2*,
                                               const double2*, double2*, int, const CgScalars*, double*, double*, int*);
 
+// ---- randomized diagonal estimator of the fermion Green's function ------------------------------
+// y[k][t][.] *= e^{sign i pi t / Nt}
+__global__ void k_twist(double2* __restrict__ y, const double2* __restrict__ tw, int Nt, int64_t slice, int64_t n,
+                        int sign) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int t = (int)((i / slice) % Nt);
+    const double2 w = tw[t];
+    const double2 a = y[i];
+    const double s = (double)sign;
+    y[i] = make_double2(a.x * w.x - s * a.y * w.y, a.y * w.x + s * a.x * w.y);
+}
+
+// out[i] = (1/K) sum_k v_k[i] * o_k[i]
+__global__ void k_probe_mean(const double2* __restrict__ v, const double2* __restrict__ o, double2* __restrict__ out,
+                             int64_t n, int K) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const double2 a = v[(int64_t)k * n + i], b = o[(int64_t)k * n + i];
+        re += a.x * b.x - a.y * b.y;
+        im += a.x * b.y + a.y * b.x;
+    }
+    out[i] = make_double2(re / K, im / K);
+}
+
+// F~ (inverse = 1: T times the inverse unitary DFT) or F~^* (inverse = 0: forward DFT of T^* x),
+// from src into dst, over (tau, y, x) of each of the nrhs vectors [V][4].
+static int twisted_fourier(hmc_ctx* ctx, const Lat& lat, const double2* src, double2* dst, int nrhs, int inverse) {
+    const int L = lat.L, Nt = lat.Nt;
+    const PcTables* pt = get_pc(ctx, L, Nt);
+    if (!pt) return fail(ctx, HMC_ERR_STATE, "no twist table for this lattice");
+    const int64_t n = 4 * lat.V * (int64_t)nrhs, slice = 4 * (int64_t)L * L;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    const int dir = inverse ? +1 : -1;
+    int rc;
+    if (!inverse) {
+        if (src != dst) HMC_CUDA(ctx, cudaMemcpyAsync(dst, src, n * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->stream));
+        k_twist<<<nb, 256, 0, ctx->stream>>>(dst, pt->twist, Nt, slice, n, -1);
+        HMC_LAUNCH(ctx, "k_twist");
+        src = dst;
+    }
+    if ((rc = fft_axis<double>(ctx, dst, (int64_t)nrhs * Nt * L, L, 4, dir, src))) return rc;
+    if ((rc = fft_axis<double>(ctx, dst, (int64_t)nrhs * Nt, L, 4 * (int64_t)L, dir))) return rc;
+    if ((rc = fft_axis<double>(ctx, dst, nrhs, Nt, slice, dir))) return rc;
+    if (inverse) {
+        k_twist<<<nb, 256, 0, ctx->stream>>>(dst, pt->twist, Nt, slice, n, +1);
+        HMC_LAUNCH(ctx, "k_twist");
+    }
+    return HMC_OK;
+}
+
+int green_run(hmc_ctx* ctx, int chain, const double* phi, const double2* v, int nrhs, double2* out, int precond,
+              hmc_cg_stats* st) {
+    const Lat& lat = ctx->chains[chain].lat;
+    int rc;
+    if ((rc = twisted_fourier(ctx, lat, v, ctx->d_pf, nrhs, 1))) return rc;                        // w = F~ v
+    if ((rc = cg_run(ctx, chain, phi, ctx->d_pf, ctx->d_X, nrhs, ctx->p.cg_tol, ctx->p.cg_maxit, precond, st)))
+        return rc;                                                                                   // u = A^-1 w
+    if ((rc = launch_apply_D<double>(ctx, lat, phi, ctx->d_X, ctx->d_chi, 1, nrhs))) return rc;    // D^dag u
+    if ((rc = twisted_fourier(ctx, lat, ctx->d_chi, ctx->d_chi, nrhs, 0))) return rc;              // F~^* D^-1 F~ v
+    const int64_t n = 4 * lat.V;
+    k_probe_mean<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(v, ctx->d_chi, out, n, nrhs);
+    HMC_LAUNCH(ctx, "k_probe_mean");
+    return HMC_OK;
+}
+
 // ---- metric -----------------------------------------------------------------------------
 __global__ void k_pack_real(const double* __restrict__ in, double2* __restrict__ out, int64_t n) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;

@@ -378,6 +378,13 @@ extern "C" int metric_apply(hmc_ctx* ctx, int chain, int op, const void* sig, co
     return HMC_OK;
 }
 
+extern "C" int green_estimate(hmc_ctx* ctx, int chain, const void* phi, const void* v, int nrhs, void* out,
+                              int precond, hmc_cg_stats* st) {
+    int rc;
+    if ((rc = check_chain(ctx, chain)) || (rc = check_nrhs(ctx, nrhs)) || (rc = check_ptrs(ctx, {phi, v, out}))) return rc;
+    return green_run(ctx, chain, (const double*)phi, (const double2*)v, nrhs, (double2*)out, precond ? 1 : 0, st);
+}
+
 extern "C" int philox_raw(hmc_ctx* ctx, uint64_t key, const uint32_t ctr[4], int64_t nblocks, void* out) {
     if (!ctx || !ctr || !out || nblocks < 0) return fail(ctx, HMC_ERR_ARG, "philox_raw: bad argument");
     if (nblocks == 0) return HMC_OK;

@@ -170,6 +170,10 @@ int launch_cg_update_precond(hmc_ctx* ctx, const Lat& lat, cplx<R>* x, cplx<R>* 
 int metric_op(hmc_ctx* ctx, const Lat& lat, int op, const double* sig, const double* in,
               double* out, double eps, double* scalar_dev);
 
+// randomized diagonal estimator of F~^* D^{-1} F~ over nrhs probes (fft.cu)
+int green_run(hmc_ctx* ctx, int chain, const double* phi, const double2* v, int nrhs, double2* out, int precond,
+              hmc_cg_stats* st);
+
 // reductions: sum nblk partials for each of k rows into out[k] (device)
 int reduce_rows(hmc_ctx* ctx, const double* part, int k, int nblk, double* out);
 

@@ -26,7 +26,7 @@ METRIC_MOMENTUM, METRIC_VELOCITY, METRIC_KINETIC, METRIC_ACCUM, METRIC_MNORM = r
 
 # every function declared in include/hmc.h
 EXPORTS = ("hmc_init", "hmc_destroy", "hmc_last_error", "hmc_counters", "apply_M", "apply_MdagM",
-           "apply_MdagM_static", "apply_precond",
+           "apply_MdagM_static", "apply_precond", "green_estimate",
            "cg_solve", "force", "metric_apply", "trajectory", "philox_raw", "philox_normal")
 
 
@@ -99,6 +99,7 @@ def lib():
         "force": [_P, _I, _P, _P, _I, _P, ctypes.POINTER(ctypes.c_double), _I, _I,
                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(CgStats)],
         "metric_apply": [_P, _I, _I, _P, _P, _P, ctypes.POINTER(ctypes.c_double)],
+        "green_estimate": [_P, _I, _P, _P, _I, _P, _I, ctypes.POINTER(CgStats)],
         "trajectory": [_P, ctypes.POINTER(TrajIn), ctypes.POINTER(TrajOut)],
         "philox_raw": [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int64, _P],
         "philox_normal": [_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, _I, _P],
@@ -262,6 +263,17 @@ class Context:
         self._check(self.lib.force(self.h, chain, _ptr(phi), _ptr(phi_pf), k, _ptr(F), ctypes.byref(spf),
                                    int(bool(include_boson)), int(bool(precond)), ctypes.byref(sb), ctypes.byref(st)))
         return F, spf.value, sb.value, st.as_dict()
+
+    def green_estimate(self, phi, probes, precond=True, chain=0):
+        """(1/K) sum_k v_k . (F~^* D^-1 F~ v_k) for K = probes.shape[0] +-1 probes (complex128,
+        shape (K, Nt, L, L, 2, 2), twisted Fourier basis). Returns (estimate (Nt, L, L, 2, 2), stats)."""
+        k = self._fermion(probes, chain, torch.complex128)
+        self._boson(phi, chain)
+        out = torch.empty(probes.shape[1:], dtype=torch.complex128, device=probes.device)
+        st = CgStats()
+        self._check(self.lib.green_estimate(self.h, chain, _ptr(phi), _ptr(probes), k, _ptr(out), int(bool(precond)),
+                                            ctypes.byref(st)))
+        return out, st.as_dict()
 
     def metric(self, op, sig, inp, out=None, chain=0):
         self._boson(sig, chain)

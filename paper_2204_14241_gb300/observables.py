@@ -1,13 +1,24 @@
-"""Bosonic observables on the GPU (Section "Estimation of observables").
+"""Observables on the GPU (Section "Estimation of observables").
+
+Fermionic: ``hmc.Context.green_estimate`` (libhmc's green_estimate) gives the randomized
+diagonal estimate of F~^* D^{-1} F~ from Rademacher probes; ``rademacher_probes`` draws them.
+Bosonic: ``SdwSusceptibility`` below.
 
 ``SdwSusceptibility`` accumulates Eq. (SDWsus), chi(omega, q) = < |F phi|^2 > dtau summed over the
 three components, with the library's Fourier accumulation (metric_apply, HMC_METRIC_ACCUM):
 one unitary 3-D FFT per sample, no host round trip.
 """
 
+import numpy as np
 import torch
 
 from .hmc import METRIC_ACCUM
+
+
+def rademacher_probes(seed, K, L, Nt, device="cuda"):
+    """K vectors with independent +-1 entries (complex128, imaginary part 0), fermion layout."""
+    v = np.random.default_rng(seed).choice([-1.0, 1.0], size=(K, Nt, L, L, 2, 2)).astype(np.complex128)
+    return torch.from_numpy(v).to(device)
 
 
 class SdwSusceptibility:

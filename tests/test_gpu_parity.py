@@ -439,3 +439,36 @@ def test_64_uneven_chains_trajectory():
         assert abs(out["dH"][i] - ref["dH"]) < 1e-8, (i, out["dH"][i], ref["dH"])
         assert out["accepted"][i] == ref["accept"]
         assert rel(I.to_paper_boson(phis[i].cpu().numpy()), ref["phi"]) < 1e-9
+
+
+@pytest.mark.parametrize("L,Nt,method", [(6, 7, "dense"), (12, 24, "pcg")])
+def test_green_estimator_matches_oracle(L, Nt, method):
+    # Section "Fermionic observables": diag(F~^* D^-1 F~) from K Rademacher probes, the K solves
+    # as one multi-RHS CG
+    from oracle import observables
+    K = 3
+    ctx = ctx_for(L, Nt, "mixed", nrhs=K, tol=1e-12)
+    P = oparams(L, Nt)
+    phi0 = I.gaussian_field(530, L, Nt) * 0.7
+    rng = np.random.default_rng(531)
+    v = rng.choice([-1.0, 1.0], size=(K, Nt, L, L, 2, 2)).astype(np.complex128)
+    est, st = ctx.green_estimate(dev(phi0), dev(v))
+    assert st["converged"]
+    ref = observables.green_diagonal(P, I.to_paper_boson(phi0), [I.to_paper_fermion(v[k]).real for k in range(K)],
+                                     method=method, tol=1e-13)
+    assert rel(I.to_paper_fermion(est.cpu().numpy()), ref) < 1e-8
+
+
+def test_green_estimator_free_limit():
+    # g = 0: the estimate is 1 / K-hat exactly for any probes (Eq. Kdiag)
+    from paper_2204_14241_gb300.hmc import Context
+    L, Nt = 8, 12
+    kw = dict(COUPLINGS)
+    kw["g"] = 0.0
+    ctx = Context(L, Nt, solver="mixed", nrhs_max=2, cg_tol=1e-12, **kw)
+    P = Params(L=L, Nt=Nt, **kw)
+    v = np.random.default_rng(532).choice([-1.0, 1.0], size=(2, Nt, L, L, 2, 2)).astype(np.complex128)
+    est, _ = ctx.green_estimate(dev(np.zeros((3, Nt, L, L))), dev(v))
+    kh = fermion.free_symbol(P)[:, None]
+    ref = 1.0 / np.broadcast_to(kh, (2, 2, Nt, L, L))
+    assert rel(I.to_paper_fermion(est.cpu().numpy()), ref) < 1e-9

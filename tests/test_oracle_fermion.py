@@ -189,3 +189,35 @@ def test_layout_roundtrip():
     assert np.array_equal(inputs.from_paper_fermion(inputs.to_paper_fermion(v)), v)
     f = inputs.gaussian_field(0, 4, 6)
     assert np.array_equal(inputs.from_paper_boson(inputs.to_paper_boson(f)), f)
+
+
+def test_green_estimator_exact_at_zero_coupling():
+    # g = 0: D = K is diagonal in the twisted Fourier basis (Eq. Kdiag), so O = F~^* D^-1 F~ is
+    # diagonal with entries 1 / K-hat and v . O v = O_ii for any +-1 vector v.
+    from oracle import observables
+    p = Params(L=4, Nt=6, g=0.0)
+    rng = np.random.default_rng(4)
+    probes = [rng.choice([-1.0, 1.0], size=(2, 2, p.Nt, p.L, p.L)) for _ in range(2)]
+    est = observables.green_diagonal(p, rand_phi(p), probes)
+    kh = fermion.free_symbol(p)[:, None]                    # (alpha, 1, n, m_x, m_y)
+    assert np.abs(est - 1.0 / np.broadcast_to(kh, est.shape)).max() < 1e-12
+
+
+def test_green_estimator_unbiased():
+    # E[v . O v] = diag(O): the average over many probes approaches the exact diagonal from a
+    # dense inverse (error ~ sqrt(sum_j |O_ij|^2 / S))
+    from oracle import observables
+    p = Params(L=2, Nt=4, g=0.8)
+    phi = rand_phi(p, 6)
+    D = fermion.dense_D(p, phi)
+    # exact O = F~^* D^-1 F~ as a matrix acting on C-order flattened vectors
+    n = p.n
+    E = np.eye(n, dtype=complex).reshape((n, 2, 2, p.Nt, p.L, p.L))
+    Ft = np.stack([observables.twisted_fourier(p, e, inverse=True).ravel() for e in E], axis=1)
+    O = Ft.conj().T @ np.linalg.solve(D, Ft)
+    rng = np.random.default_rng(7)
+    S = 400
+    probes = [rng.choice([-1.0, 1.0], size=(2, 2, p.Nt, p.L, p.L)) for _ in range(S)]
+    est = observables.green_diagonal(p, phi, probes).ravel()
+    off = np.sqrt((np.abs(O) ** 2).sum(axis=1) - np.abs(np.diag(O)) ** 2)
+    assert np.all(np.abs(est - np.diag(O)) < 5 * off / np.sqrt(S) + 1e-12)
