@@ -38,6 +38,10 @@ WORKLOAD = (f"L={L}x{L}, Nt={NT} (dtau=0.1), 2 bands x 2 spins, {NRHS} pseudofer
             f"Yukawa lambda={LAMBDA} as g/sqrt(N_f): D coefficient {LAMBDA / NRHS ** 0.5:.4f}), n_leap={NLEAP}, "
             f"eps={EPS}, complex64 PCG with FP64 reliable updates to true residual {TOL}, "
             "chronological initial guess, phi = free-boson-spectrum Gaussian field, sigma-hat = its spectrum")
+# DRAM bytes (read + write) of one launch of the roofline kernel, the plain fused A on 8 RHS at
+# 80x80x160, from ncu (profiles/ncu_apply_A_plain_80x80x160_8rhs.md); set to None when that
+# kernel changes until it is captured again.
+ROOFLINE_TRAFFIC_BYTES = 549_482_752
 # PCG iterations per solve of this workload on a GB300, used only to scale the oracle's timed
 # sample (a few PCG iterations) to a trajectory when no GPU run is available in the process.
 ITERS_PER_SOLVE_DEFAULT = 57
@@ -136,16 +140,21 @@ class ClockSampler:
 
 
 # ---- the oracle on the host cores (cpu_baseline / reference arm) -------------------------------------
+_ORACLE_INPUTS = {}
+
+
 def oracle_iteration_time(n_iter=2):
     """Seconds per PCG iteration of the FP64 oracle on the full lattice, one right-hand side.
     Returns (seconds per iteration, threads used)."""
     from oracle.model import Params
     from oracle import solver, fermion
     from paper_2204_14241_gb300 import inputs as I
-    phi, _ = synthetic_inputs(1)
+    if not _ORACLE_INPUTS:
+        phi, _ = synthetic_inputs(1)
+        _ORACLE_INPUTS["phi"] = I.to_paper_boson(phi)
+        _ORACLE_INPUTS["b"] = I.to_paper_fermion(I.fermion_noise(2, 1, L, NT)[0])
     P = Params(L=L, Nt=NT, **COUPLINGS)
-    phi_o = I.to_paper_boson(phi)
-    b = I.to_paper_fermion(I.fermion_noise(2, 1, L, NT)[0])
+    phi_o, b = _ORACLE_INPUTS["phi"], _ORACLE_INPUTS["b"]
     # one PCG iteration = one A apply + one preconditioner apply + vector updates
     x = b.copy()
     t0 = time.perf_counter()
@@ -223,7 +232,7 @@ def run_ours(args):
     phi = torch.from_numpy(phi_np).to(dev)
     sig = torch.from_numpy(sig_np).to(dev)
     ctx = Context(L, NT, solver="mixed", nrhs_max=NRHS, cg_tol=TOL, cg_maxit=MAXIT, device=dev, initial_guess=GUESS,
-                  autotune=1, **COUPLINGS)
+                  **COUPLINGS)
     st = ctx.stream
 
     # warm-up trajectories; they also accumulate the metric estimate of Eq. (covest)
@@ -323,7 +332,8 @@ def run_ours(args):
                            "workspace per solve; matvec timed on 537 MB in/out)", "parallelism": f"replicas x{ws}"},
                 "matvec_gbs": achieved,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": None, "kernel": "k_apply_A<float> (A = D D^dagger)",
+                             "frac": achieved / peak, "traffic": ROOFLINE_TRAFFIC_BYTES,
+                             "kernel": "k_apply_A<float, plain> (A = D D^dagger)",
                              "peak_source": peak_src, "algorithmic_bytes": mv_bytes,
                              "launch_us": t_mv * 1e6},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
@@ -364,6 +374,24 @@ def run_profile_solve(args):
     ctx.close()
 
 
+def run_profile_matvec(args):
+    """Only the dominant kernel: N launches of the fused A = D D^dagger (complex64, NRHS) on the
+    benchmark's lattice, for an ncu capture of the last one."""
+    import torch
+    from paper_2204_14241_gb300.hmc import Context
+    from paper_2204_14241_gb300 import inputs as I
+    phi_np, _ = synthetic_inputs(chain_seed(args.seed, 0))
+    phi32 = torch.from_numpy(phi_np).cuda().float()
+    x = torch.from_numpy(I.fermion_noise(3, NRHS, L, NT)).cuda().to(torch.complex64)
+    y = torch.empty_like(x)
+    ctx = Context(L, NT, solver="mixed", nrhs_max=NRHS, cg_tol=TOL, **COUPLINGS)
+    for _ in range(args.profile_matvec):
+        ctx.apply_MdagM(phi32, x, out=y)
+    torch.cuda.synchronize()
+    ctx.close()
+    print(json.dumps({"profile_matvec": args.profile_matvec}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,8 +402,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-solve", type=int, default=0,
                     help="run only a capture-sized sample: one solve cut at this many iterations")
+    ap.add_argument("--profile-matvec", type=int, default=0,
+                    help="run only this many launches of the fused A kernel (the roofline kernel)")
     args = ap.parse_args()
-    if args.profile_solve:
+    if args.profile_matvec:
+        run_profile_matvec(args)
+    elif args.profile_solve:
         run_profile_solve(args)
     elif args.impl == "reference":
         run_reference(args)

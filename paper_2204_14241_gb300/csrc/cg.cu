@@ -3,7 +3,7 @@
 //
 // Precision: HMC_SOLVER_FP64 iterates in complex128. HMC_SOLVER_MIXED iterates in complex64
 // and keeps the solution and the true residual in complex128 ("reliable updates": whenever
-// the iterated residual has dropped by a factor 100 since the last update, or meets the
+// the iterated residual has dropped by a factor 1000 since the last update, or meets the
 // tolerance, the partial solution is folded into the FP64 solution, the residual is
 // recomputed in FP64 as b - A x, and the iteration continues from it with the same search
 // direction). Both modes stop on the FP64 true residual ||b - A x|| <= tol ||b||.
@@ -222,7 +222,7 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
     const int64_t n = 4 * lat.V;                      // complex entries per RHS
     const int64_t n16 = n * sizeof(C) / 16;
     const double tol2 = tol * tol;
-    const double delta2 = 1e-4;                       // reliable update at ||r|| < 0.01 max||r||
+    const double delta2 = 1e-6;                       // reliable update at ||r|| < 1e-3 max||r||
     CgScalars* cgs = ctx->d_cg;
     double* part = ctx->d_part;
     double* part2 = ctx->d_part + ctx->part_cap / 2;
