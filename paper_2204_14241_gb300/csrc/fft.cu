@@ -354,6 +354,12 @@ static int add_pc(hmc_ctx* ctx, int L, int Nt) {
     HMC_CUDA(ctx, cudaMemcpy(t.cosk32, ck32.data(), L * sizeof(float), cudaMemcpyHostToDevice));
     HMC_CUDA(ctx, cudaMemcpy(t.eitw32, ew32.data(), Nt * sizeof(float2), cudaMemcpyHostToDevice));
     HMC_CUDA(ctx, cudaMemcpy(t.twist32, tw32.data(), Nt * sizeof(float2), cudaMemcpyHostToDevice));
+    if (fftc_xy_supported(L)) {
+        std::vector<float> ckxy(L);
+        for (int m = 0; m < L; ++m) ckxy[m] = (float)std::cos(2.0 * M_PI * fftc_xy_freq(L, m) / L);
+        HMC_CUDA(ctx, cudaMalloc(&t.cosk32_xy, L * sizeof(float)));
+        HMC_CUDA(ctx, cudaMemcpy(t.cosk32_xy, ckxy.data(), L * sizeof(float), cudaMemcpyHostToDevice));
+    }
     ctx->pcs.push_back(t);
     return HMC_OK;
 }
@@ -381,6 +387,7 @@ void free_plans(hmc_ctx* ctx) {
         cudaFree(t.cosk32);
         cudaFree(t.eitw32);
         cudaFree(t.twist32);
+        cudaFree(t.cosk32_xy);
     }
     ctx->pcs.clear();
 }
@@ -450,7 +457,7 @@ int precond_tau(hmc_ctx* ctx, const Lat& lat, cplx<R>* y, int nrhs, const CgScal
     PcTables* pt = get_pc(ctx, L, Nt);
     if (!p || !pt) return fail(ctx, HMC_ERR_STATE, "no preconditioner plan for this lattice");
     if constexpr (sizeof(R) == 4) {
-        if (fftc_can(Nt, 4 * (int64_t)L * L)) return fftc_precond_tau(ctx, lat, y, nrhs, cgs, pt);
+        if (fftc_can(Nt, 4 * (int64_t)L * L)) return fftc_precond_tau(ctx, lat, y, nrhs, cgs, pt, pt->cosk32);
     }
     PrecondCoef pc;
     pc.dtau = ctx->p.dtau;
@@ -483,6 +490,15 @@ template <typename R>
 int launch_precond(hmc_ctx* ctx, const Lat& lat, const cplx<R>* x, cplx<R>* y, int nrhs) {
     const int L = lat.L, Nt = lat.Nt;
     int rc;
+    if constexpr (sizeof(R) == 4) {
+        // the (x, y) passes and tau pass that PCG runs
+        const PcTables* pt = get_pc(ctx, L, Nt);
+        if (pt && pt->cosk32_xy && fftc_can(Nt, 4 * (int64_t)L * L)) {
+            if ((rc = fftc_xy_apply(ctx, lat, x, y, nrhs, -1))) return rc;
+            if ((rc = fftc_precond_tau(ctx, lat, y, nrhs, nullptr, pt, pt->cosk32_xy))) return rc;
+            return fftc_xy_apply(ctx, lat, y, y, nrhs, +1);
+        }
+    }
     if ((rc = fft_axis<R>(ctx, y, (int64_t)nrhs * Nt * L, L, 4, -1, x))) return rc;
     if ((rc = fft_axis<R>(ctx, y, (int64_t)nrhs * Nt, L, 4 * (int64_t)L, -1))) return rc;
     if ((rc = precond_tau<R>(ctx, lat, y, nrhs, nullptr))) return rc;
@@ -518,6 +534,16 @@ int launch_cg_update_precond(hmc_ctx* ctx, const Lat& lat, cplx<R>* x, cplx<R>* 
     }
     int rc;
     if constexpr (sizeof(R) == 4) {
+        const PcTables* pt = get_pc(ctx, L, Nt);
+        if (pt && pt->cosk32_xy && fftc_can(Nt, 4 * (int64_t)L * L)) {
+            // (x, y) in one pass each way; the spectrum between them is in digit-permuted order
+            if ((rc = fftc_xy_cg(ctx, lat, kFftcXUpd, nullptr, z, x, r, p, q, nrhs, cgs, part_r2, nblk_out))) return rc;
+            if ((rc = fftc_precond_tau(ctx, lat, z, nrhs, cgs, pt, pt->cosk32_xy))) return rc;
+            int nb2 = 0;
+            if ((rc = fftc_xy_cg(ctx, lat, kFftcXDot, z, z, nullptr, r, nullptr, nullptr, nrhs, cgs, part_rz, &nb2)))
+                return rc;
+            return HMC_OK;
+        }
         if (fftc_supported(L)) {
             if ((rc = fftc_x_cg(ctx, lat, kFftcXUpd, nullptr, z, x, r, p, q, nrhs, cgs, part_r2, nblk_out))) return rc;
             if ((rc = fft_axis<R>(ctx, z, (int64_t)nrhs * Nt, L, 4 * (int64_t)L, -1, nullptr, cgs, Nt))) return rc;

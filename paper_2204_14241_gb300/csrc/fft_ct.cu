@@ -484,7 +484,7 @@ int fftc_axis(hmc_ctx* ctx, float2* data, int64_t outer, int n, int64_t inner, i
 }
 
 int fftc_precond_tau(hmc_ctx* ctx, const Lat& lat, float2* y, int nrhs, const CgScalars* cgs,
-                     const PcTables* pt) {
+                     const PcTables* pt, const float* cosk) {
     const int n = lat.Nt;
     const FftPlan* pl = get_plan(ctx, n);
     if (!pl) return fail(ctx, HMC_ERR_STATE, "no FFT plan");
@@ -504,7 +504,7 @@ int fftc_precond_tau(hmc_ctx* ctx, const Lat& lat, float2* y, int nrhs, const Cg
         A.chy[q] = (float)(-2.0 * ctx->p.dtau * ctx->p.t_v[q]);
     }
     A.L = lat.L;
-    A.cosk = pt->cosk32;
+    A.cosk = cosk;
     A.eitw = pt->eitw32;
     A.twist = pt->twist32;
     if (A.inner < NL) return fail(ctx, HMC_ERR_STATE, "fftc: unsupported tile");
@@ -547,6 +547,247 @@ int fftc_x_cg(hmc_ctx* ctx, const Lat& lat, int mode, const float2* src, float2*
     if (n == N) return mode == kXUpd ? launch_one<N, 4, kXUpd, -1>(ctx, grid, A)       \
                                      : launch_one<N, 4, kXDot, +1>(ctx, grid, A);
     HMC_FFTC_SIZES(HMC_CASE)
+#undef HMC_CASE
+    return fail(ctx, HMC_ERR_STATE, "fftc: unsupported length");
+}
+
+
+// ---- (x, y) passes of the preconditioner inside PCG ------------------------------------------
+// One block transforms one band (the two spin components, 16 bytes per site) of one (RHS, tau)
+// plane in shared memory, both axes, so the x and y passes cost one read and one write of the
+// vector instead of two. Each axis is a two-factor Cooley-Tukey split L = N1 * N2 done in place:
+// with n = n1 + N1 n2 and k = k2 + N2 k1,
+//   step A (fixed n1): N2-point DFT over n2, times w_L^{n1 k2}, written back to n1 + N1 k2;
+//   step B (fixed k2): N1-point DFT over n1 at positions N1 k2 + n1, written back in place.
+// Position N1 k2 + k1 then holds frequency k2 + N2 k1: the forward pass leaves the spectrum
+// in this digit-permuted order (the tau pass reads its cos k table in the same order) and the
+// inverse pass (step B then step A, conjugate twiddles) takes it back to natural order.
+template <int L> struct XYSplit { static constexpr int N1 = 0, N2 = 0; };
+template <> struct XYSplit<12> { static constexpr int N1 = 4, N2 = 3; };
+template <> struct XYSplit<16> { static constexpr int N1 = 4, N2 = 4; };
+template <> struct XYSplit<20> { static constexpr int N1 = 5, N2 = 4; };
+template <> struct XYSplit<24> { static constexpr int N1 = 6, N2 = 4; };
+template <> struct XYSplit<40> { static constexpr int N1 = 8, N2 = 5; };
+template <> struct XYSplit<80> { static constexpr int N1 = 10, N2 = 8; };
+#define HMC_FFTXY_SIZES(X) X(12) X(16) X(20) X(24) X(40) X(80)
+
+constexpr int kXYThreads = 320;
+// row stride (in sites) of the shared plane: = 1 mod 8 so that eight consecutive rows at one
+// column fall in distinct bank groups
+constexpr int xy_row_stride(int L) { return L + ((9 - L % 8) % 8); }
+
+// In-place DFTs of size R over the positions base(line) + S * m, m < R, for every (line, f)
+// task; AX = 0: lines along x (line = (row y, spin c)), AX = 1: lines along y (line = (column
+// x, spin c)). STEP_A: f = n1, positions n1 + N1 m; else f = k2, positions N1 k2 + m. TW
+// multiplies output m by w_L^{DIR f m} (step A) or w_L^{DIR m f} (step B).
+template <int L, int AX, bool STEP_A, bool TW, int DIR>
+__device__ __forceinline__ void xy_step(float2* sm, const float2* __restrict__ tw) {
+    constexpr int N1 = XYSplit<L>::N1, N2 = XYSplit<L>::N2, RS = xy_row_stride(L);
+    constexpr int R = STEP_A ? N2 : N1;
+    constexpr int NF = STEP_A ? N1 : N2;
+    constexpr int total = 2 * L * NF;
+#pragma unroll 2
+    for (int task = threadIdx.x; task < total; task += kXYThreads) {
+        const int line = task % (2 * L), f = task / (2 * L);
+        const int a = line >> 1, c = line & 1;
+        auto at = [&](int pos) { return AX == 0 ? ((a * RS + pos) << 1) + c : ((pos * RS + a) << 1) + c; };
+        float2 v[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = sm[at(STEP_A ? f + N1 * m : N1 * f + m)];
+        bfly<R, DIR>(v);
+        if constexpr (TW) {
+#pragma unroll
+            for (int m = 1; m < R; ++m) {
+                float2 w = __ldg(tw + f * m);   // f * m < L
+                if (DIR > 0) w.y = -w.y;
+                v[m] = make_float2(v[m].x * w.x - v[m].y * w.y, v[m].x * w.y + v[m].y * w.x);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < R; ++m) sm[at(STEP_A ? f + N1 * m : N1 * f + m)] = v[m];
+    }
+}
+
+// MODE kXUpd (DIR -1): x += alpha p, r -= alpha q (written back), partial ||r||^2,
+// dst = F_xy r (permuted order). MODE kXDot (DIR +1): dst = F_xy^-1 src (permuted order in,
+// natural out), partial Re <r, dst>. MODE kPlain: dst = F_xy src (DIR -1) or F_xy^-1 src
+// (DIR +1), every right-hand side. Grid (2 Nt, nrhs): block (2 t + band, k). dst may alias src.
+template <int L, int MODE, int DIR>
+__global__ void __launch_bounds__(kXYThreads, 2) k_fft_xy(FftcArgs A, int Nt) {
+    static_assert(MODE == kPlain || (MODE == kXUpd) == (DIR < 0), "update pass is forward, dot pass inverse");
+    constexpr int RS = xy_row_stride(L);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[kXYThreads / 32];
+    float2* sm = reinterpret_cast<float2*>(smem_raw);   // [L][RS] sites x 2 spins
+    const int k = blockIdx.y;
+    if (A.cgs && !A.cgs[k].active) return;
+    const int t = blockIdx.x >> 1, band = blockIdx.x & 1;
+    const int64_t g0 = (((int64_t)k * Nt + t) * L * L) * 4 + 2 * band;   // float2 index of site 0
+    float alpha = 0.f;
+    if constexpr (MODE == kXUpd) alpha = (float)A.cgs[k].alpha;
+    float acc = 0.f;
+
+    // sites are taken XB at a time: all loads of a batch are issued before its stores (the
+    // vectors may alias as far as the compiler knows)
+    constexpr int XB = 4;
+    for (int e0 = threadIdx.x; e0 < L * L; e0 += XB * kXYThreads) {
+        float4 v[XB];
+        if constexpr (MODE == kXUpd) {
+            float4 xx[XB], pp[XB], qq[XB];
+#pragma unroll
+            for (int b = 0; b < XB; ++b) {
+                const int e = e0 + b * kXYThreads;
+                if (e < L * L) {
+                    const int64_t g = g0 + 4 * (int64_t)e;
+                    xx[b] = *reinterpret_cast<const float4*>(A.x + g);
+                    v[b] = *reinterpret_cast<const float4*>(A.r + g);
+                    pp[b] = *reinterpret_cast<const float4*>(A.p + g);
+                    qq[b] = *reinterpret_cast<const float4*>(A.q + g);
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < XB; ++b) {
+                const int e = e0 + b * kXYThreads;
+                if (e < L * L) {
+                    const int64_t g = g0 + 4 * (int64_t)e;
+                    float4& xb = xx[b];
+                    float4& rb = v[b];
+                    xb.x += alpha * pp[b].x; xb.y += alpha * pp[b].y; xb.z += alpha * pp[b].z; xb.w += alpha * pp[b].w;
+                    rb.x -= alpha * qq[b].x; rb.y -= alpha * qq[b].y; rb.z -= alpha * qq[b].z; rb.w -= alpha * qq[b].w;
+                    *reinterpret_cast<float4*>(A.x + g) = xb;
+                    *reinterpret_cast<float4*>(A.r + g) = rb;
+                    acc += rb.x * rb.x + rb.y * rb.y + rb.z * rb.z + rb.w * rb.w;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < XB; ++b) {
+                const int e = e0 + b * kXYThreads;
+                if (e < L * L) v[b] = *reinterpret_cast<const float4*>(A.src + g0 + 4 * (int64_t)e);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < XB; ++b) {
+            const int e = e0 + b * kXYThreads;
+            if (e < L * L) *reinterpret_cast<float4*>(sm + 2 * ((e / L) * RS + e % L)) = v[b];
+        }
+    }
+    __syncthreads();
+    if constexpr (DIR < 0) {
+        xy_step<L, 0, true, true, DIR>(sm, A.tw);
+        __syncthreads();
+        xy_step<L, 0, false, false, DIR>(sm, A.tw);
+        __syncthreads();
+        xy_step<L, 1, true, true, DIR>(sm, A.tw);
+        __syncthreads();
+        xy_step<L, 1, false, false, DIR>(sm, A.tw);
+    } else {
+        xy_step<L, 1, false, true, DIR>(sm, A.tw);
+        __syncthreads();
+        xy_step<L, 1, true, false, DIR>(sm, A.tw);
+        __syncthreads();
+        xy_step<L, 0, false, true, DIR>(sm, A.tw);
+        __syncthreads();
+        xy_step<L, 0, true, false, DIR>(sm, A.tw);
+    }
+    __syncthreads();
+    const float sc = 1.0f / (float)L;   // unitary on both axes
+    for (int e0 = threadIdx.x; e0 < L * L; e0 += XB * kXYThreads) {
+        float4 rr[XB];
+        if constexpr (MODE == kXDot) {
+#pragma unroll
+            for (int b = 0; b < XB; ++b) {
+                const int e = e0 + b * kXYThreads;
+                if (e < L * L) rr[b] = *reinterpret_cast<const float4*>(A.r + g0 + 4 * (int64_t)e);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < XB; ++b) {
+            const int e = e0 + b * kXYThreads;
+            if (e < L * L) {
+                float4 v = *reinterpret_cast<const float4*>(sm + 2 * ((e / L) * RS + e % L));
+                v.x *= sc; v.y *= sc; v.z *= sc; v.w *= sc;
+                *reinterpret_cast<float4*>(A.dst + g0 + 4 * (int64_t)e) = v;
+                if constexpr (MODE == kXDot)
+                    acc += rr[b].x * v.x + rr[b].y * v.y + rr[b].z * v.z + rr[b].w * v.w;
+            }
+        }
+    }
+    if constexpr (MODE != kPlain) {
+        const double tot = block_sum((double)acc, red);
+        if (threadIdx.x == 0) A.part[(int64_t)k * gridDim.x + blockIdx.x] = tot;
+    }
+}
+
+bool fftc_xy_supported(int L) {
+#define HMC_CASE(N) if (L == N) return true;
+    HMC_FFTXY_SIZES(HMC_CASE)
+#undef HMC_CASE
+    return false;
+}
+
+int fftc_xy_freq(int L, int pos) {
+#define HMC_CASE(N) \
+    if (L == N) return pos / XYSplit<N>::N1 + XYSplit<N>::N2 * (pos % XYSplit<N>::N1);
+    HMC_FFTXY_SIZES(HMC_CASE)
+#undef HMC_CASE
+    return -1;
+}
+
+template <int L, int MODE, int DIR>
+static int launch_xy(hmc_ctx* ctx, dim3 grid, const FftcArgs& A, int Nt) {
+    constexpr size_t sm = (size_t)L * xy_row_stride(L) * 2 * sizeof(float2);
+    static bool attr = false;
+    if (!attr) {
+        HMC_CUDA(ctx, cudaFuncSetAttribute(k_fft_xy<L, MODE, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sm));
+        attr = true;
+    }
+    k_fft_xy<L, MODE, DIR><<<grid, kXYThreads, sm, ctx->stream>>>(A, Nt);
+    HMC_LAUNCH(ctx, "k_fft_xy");
+    return HMC_OK;
+}
+
+int fftc_xy_cg(hmc_ctx* ctx, const Lat& lat, int mode, const float2* src, float2* dst, float2* x, float2* r,
+               const float2* p, const float2* q, int nrhs, const CgScalars* cgs, double* part, int* nblk_out) {
+    const int L = lat.L;
+    const FftPlan* pl = get_plan(ctx, L);
+    if (!pl) return fail(ctx, HMC_ERR_STATE, "no FFT plan");
+    FftcArgs A{};
+    A.src = src;
+    A.dst = dst;
+    A.x = x;
+    A.r = r;
+    A.p = p;
+    A.q = q;
+    A.cgs = cgs;
+    A.part = part;
+    A.tw = pl->tw32;
+    const int64_t nblk = 2 * (int64_t)lat.Nt;
+    if (nblk * nrhs > ctx->part_cap / 2) return fail(ctx, HMC_ERR_ARG, "fftc: reduction buffer too small");
+    const dim3 grid((unsigned)nblk, nrhs);
+    *nblk_out = (int)nblk;
+#define HMC_CASE(N)                                                                    \
+    if (L == N) return mode == kXUpd ? launch_xy<N, kXUpd, -1>(ctx, grid, A, lat.Nt)  \
+                                     : launch_xy<N, kXDot, +1>(ctx, grid, A, lat.Nt);
+    HMC_FFTXY_SIZES(HMC_CASE)
+#undef HMC_CASE
+    return fail(ctx, HMC_ERR_STATE, "fftc: unsupported length");
+}
+
+int fftc_xy_apply(hmc_ctx* ctx, const Lat& lat, const float2* src, float2* dst, int nrhs, int dir) {
+    const int L = lat.L;
+    const FftPlan* pl = get_plan(ctx, L);
+    if (!pl) return fail(ctx, HMC_ERR_STATE, "no FFT plan");
+    FftcArgs A{};
+    A.src = src;
+    A.dst = dst;
+    A.tw = pl->tw32;
+    const dim3 grid((unsigned)(2 * lat.Nt), nrhs);
+#define HMC_CASE(N)                                                                    \
+    if (L == N) return dir < 0 ? launch_xy<N, kPlain, -1>(ctx, grid, A, lat.Nt)       \
+                               : launch_xy<N, kPlain, +1>(ctx, grid, A, lat.Nt);
+    HMC_FFTXY_SIZES(HMC_CASE)
 #undef HMC_CASE
     return fail(ctx, HMC_ERR_STATE, "fftc: unsupported length");
 }

@@ -25,6 +25,7 @@ struct PcTables {
     float* cosk32 = nullptr;    // float copies for the FP32 path
     float2* eitw32 = nullptr;
     float2* twist32 = nullptr;
+    float* cosk32_xy = nullptr; // cos(2 pi k(m) / L), k(m) the frequency at position m after the (x, y) pass
 };
 
 // Tile shape chosen for the fused A kernel per (L, Nt, nrhs, precision).

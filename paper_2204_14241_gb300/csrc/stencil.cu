@@ -286,6 +286,206 @@ k_apply_A(Lat lat, Coef<R> cf, ATile tl, const R* __restrict__ phi, const Site<R
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Plain FP32 fused A, asynchronous staging, tile extent fixed at compile time. Same marching
+// scheme as k_apply_A, but each time slice of x and phi arrives by cp.async copies (16-byte
+// chunks for x) into a four-slice ring in shared memory, issued three slices ahead, so no
+// registers hold staged data and a slice has two steps to land. Thread i < TX*TY owns tile
+// site (i % TX, i / TX) and keeps that site's x(t), t_(t) and phi(t) in registers: its
+// t_(t+1) reads the four x neighbours and its y(t) the four t_ neighbours from shared memory.
+// The one-site-ring t_ sites are a second job of threads 0, 1, ... One barrier per step:
+// step t writes t_(t+1) into the t_ buffer that y(t-1) read before the barrier, and reads
+// t_(t), written before it; slice t+3 goes into the x buffer of slice t-1, last read before it.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int kA4Ring = 4;   // x and phi slices resident: t-1 .. t+2
+
+template <int TX, int TY> struct A4Shape {
+    static constexpr int HX2 = TX + 4, N2 = (TX + 4) * (TY + 4);   // two-site halo
+    static constexpr int HX1 = TX + 2, N1 = (TX + 2) * (TY + 2);   // one-site halo
+    static constexpr int NI = TX * TY;
+    static constexpr int NCH = (2 * N2 + kAThreads - 1) / kAThreads;   // 16-byte chunks per thread and slice
+    static constexpr int NPH = (N1 + kAThreads - 1) / kAThreads;       // phi sites per thread and slice
+    static constexpr size_t smem = (size_t)kA4Ring * N2 * 32 + (size_t)2 * N1 * 32 + (size_t)kA4Ring * 3 * N1 * 4;
+    static_assert(NI <= kAThreads && N1 - NI <= kAThreads, "one tile site and one ring site per thread");
+};
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(kAThreads, 2) k_apply_A4(Lat lat, Coef<float> cf, ATile tl,
+                                                           const float* __restrict__ phi,
+                                                           const Site<float>* __restrict__ x,
+                                                           Site<float>* __restrict__ y, double* __restrict__ part) {
+    using S = A4Shape<TX, TY>;
+    constexpr int HX2 = S::HX2, N2 = S::N2, HX1 = S::HX1, N1 = S::N1, NI = S::NI;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint4* xsb = reinterpret_cast<uint4*>(smem_raw);                 // ring x [2 planes][N2]
+    uint4* tsb = xsb + kA4Ring * 2 * N2;                             // 2 x [2 planes][N1]
+    float* phb = reinterpret_cast<float*>(tsb + 2 * 2 * N1);         // ring x [3][N1]
+    __shared__ double red[kAThreads / 32];
+
+    const int L = lat.L, Nt = lat.Nt;
+    const int64_t V = lat.V, LL = (int64_t)L * L;
+    const int x0 = (blockIdx.x % tl.ntx) * TX, y0 = (blockIdx.x / tl.ntx) * TY;
+    const int t0 = blockIdx.y * tl.C;
+    const int t1 = min(t0 + tl.C, Nt);
+    const int k = blockIdx.z;
+    const Site<float>* xk = x + k * V;
+    Site<float>* yk = y + k * V;
+    auto gx = [&](int i) { int v = (x0 + i) % L; return v < 0 ? v + L : v; };
+    auto gy = [&](int j) { int v = (y0 + j) % L; return v < 0 ? v + L : v; };
+    auto wrap_t = [&](int t) { return t < 0 ? t + Nt : (t >= Nt ? t - Nt : t); };
+    const int tid = threadIdx.x;
+
+    // staging: chunk c = tid + j * threads is plane (c & 1) of two-site-halo site (c >> 1);
+    // g_off in 16-byte units within a slice, -1 for none
+    int g_off[S::NCH];
+#pragma unroll
+    for (int j = 0; j < S::NCH; ++j) {
+        const int c = tid + j * kAThreads, i = c >> 1;
+        g_off[j] = c < 2 * N2 ? 2 * (gy(i / HX2 - 2) * L + gx(i % HX2 - 2)) + (c & 1) : -1;
+    }
+    int p_off[S::NPH];
+#pragma unroll
+    for (int j = 0; j < S::NPH; ++j) {
+        const int i = tid + j * kAThreads;
+        p_off[j] = i < N1 ? gy(i / HX1 - 1) * L + gx(i % HX1 - 1) : -1;
+    }
+    // own tile site
+    const bool own = tid < NI;
+    const int ix = tid % TX, iy = tid / TX;
+    const int o_c2 = (iy + 2) * HX2 + ix + 2, o_c1 = (iy + 1) * HX1 + ix + 1;
+    const bool o_valid = own && x0 + ix < L && y0 + iy < L;
+    const int o_off = gy(iy) * L + gx(ix);
+    const float o_eta = ((gx(ix) + gy(iy)) & 1) ? -1.f : 1.f;
+    // one-site-ring site of this thread: top row, the two side columns, bottom row
+    int r1_c1 = -1, r1_c2 = 0;
+    float r1_eta = 1.f;
+    if (tid < N1 - NI) {
+        int hx, hy;
+        if (tid < HX1) { hy = 0; hx = tid; }
+        else if (tid < HX1 + 2 * TY) { const int r = tid - HX1; hy = 1 + r / 2; hx = (r & 1) ? TX + 1 : 0; }
+        else { hy = TY + 1; hx = tid - HX1 - 2 * TY; }
+        r1_c1 = hy * HX1 + hx;
+        r1_c2 = (hy + 1) * HX2 + hx + 1;
+        r1_eta = ((gx(hx - 1) + gy(hy - 1)) & 1) ? -1.f : 1.f;
+    }
+
+    auto xbuf = [&](int b) { return xsb + b * (2 * N2); };
+    auto tbuf = [&](int b) { return tsb + b * (2 * N1); };
+    auto pbuf = [&](int b) { return phb + b * (3 * N1); };
+    auto issue = [&](int b, int t) {
+        const int64_t base = (int64_t)t * LL;
+        const uint4* src = reinterpret_cast<const uint4*>(xk + base);
+        uint4* dst = xbuf(b);
+#pragma unroll
+        for (int j = 0; j < S::NCH; ++j) {
+            const int c = tid + j * kAThreads;
+            if (g_off[j] >= 0) cp_async16(dst + (c & 1) * N2 + (c >> 1), src + g_off[j]);
+        }
+        float* pd = pbuf(b);
+#pragma unroll
+        for (int j = 0; j < S::NPH; ++j)
+            if (p_off[j] >= 0) {
+                const int i = tid + j * kAThreads;
+                const float* ps = phi + base + p_off[j];
+                cp_async4(pd + i, ps);
+                cp_async4(pd + N1 + i, ps + V);
+                cp_async4(pd + 2 * N1 + i, ps + 2 * V);
+            }
+    };
+    // t_ at slice t on this thread's ring site from x(t) (buffer bc) and x(t-1) (buffer bp)
+    auto ring_t = [&](int bc, int bp, int bt, int t) {
+        if (r1_c1 < 0) return;
+        const uint4* xc = xbuf(bc);
+        const float* ph = pbuf(bc);
+        const int c = r1_c2;
+        const Site<float> o = site_op<float>(cf, sm_load<float>(xc, N2, c), sm_load<float>(xc, N2, c - 1),
+                                             sm_load<float>(xc, N2, c + 1), sm_load<float>(xc, N2, c - HX2),
+                                             sm_load<float>(xc, N2, c + HX2), sm_load<float>(xbuf(bp), N2, c),
+                                             t == 0 ? -1.f : 1.f, ph[r1_c1], ph[N1 + r1_c1], ph[2 * N1 + r1_c1],
+                                             r1_eta);
+        sm_store<float>(tbuf(bt), N1, r1_c1, o);
+    };
+    // t_ at slice t on the own site from x(t) (buffer bc, also returned in xo) and x(t-1)
+    auto own_t = [&](int bc, const Site<float>& xprev, int bt, int t, Site<float>& xo, float* ph3) {
+        const uint4* xc = xbuf(bc);
+        const float* ph = pbuf(bc);
+        xo = sm_load<float>(xc, N2, o_c2);
+        ph3[0] = ph[o_c1]; ph3[1] = ph[N1 + o_c1]; ph3[2] = ph[2 * N1 + o_c1];
+        const Site<float> o = site_op<float>(cf, xo, sm_load<float>(xc, N2, o_c2 - 1), sm_load<float>(xc, N2, o_c2 + 1),
+                                             sm_load<float>(xc, N2, o_c2 - HX2), sm_load<float>(xc, N2, o_c2 + HX2),
+                                             xprev, t == 0 ? -1.f : 1.f, ph3[0], ph3[1], ph3[2], o_eta);
+        sm_store<float>(tbuf(bt), N1, o_c1, o);
+        return o;
+    };
+
+    // prologue: slices t0-1 .. t0+2 in buffers 0 .. 3 (slice t0+2 only if step t0+1 exists)
+    issue(0, wrap_t(t0 - 1));
+    cp_async_commit();
+    issue(1, t0);
+    cp_async_commit();
+    issue(2, wrap_t(t0 + 1));   // y(t0) needs t_(t0+1) even when the chunk is one slice long
+    cp_async_commit();
+    if (t0 + 1 < t1) issue(3, wrap_t(t0 + 2));
+    cp_async_commit();
+    cp_async_wait<2>();
+    __syncthreads();
+    Site<float> xo, to;
+    float pho[3] = {0.f, 0.f, 0.f};
+    if (own) to = own_t(1, sm_load<float>(xbuf(0), N2, o_c2), 0, t0, xo, pho);
+    ring_t(1, 0, 0, t0);
+
+    float acc = 0.f;
+    for (int t = t0; t < t1; ++t) {
+        const int u = t - t0 + 1;              // ring buffer of slice t is u & 3
+        cp_async_wait<1>();                    // slice t+1 has landed (slice t+2 may be in flight)
+        __syncthreads();
+        if (t + 2 < t1) issue((u + 3) & 3, wrap_t(t + 3));
+        cp_async_commit();
+        const int tp = wrap_t(t + 1);
+        const int bn = (u + 1) & 3, bt = (t + 1 - t0) & 1;
+        Site<float> xn, tn;
+        float phn[3] = {0.f, 0.f, 0.f};
+        if (own) tn = own_t(bn, xo, bt, tp, xn, phn);
+        ring_t(bn, u & 3, bt, tp);
+        // y(t) = D t_ on the own site: t_(t) neighbours from the buffer written before the barrier
+        if (own) {
+            const uint4* tc = tbuf(bt ^ 1);
+            const Site<float> o = site_op<float>(cf, to, sm_load<float>(tc, N1, o_c1 - 1),
+                                                 sm_load<float>(tc, N1, o_c1 + 1), sm_load<float>(tc, N1, o_c1 - HX1),
+                                                 sm_load<float>(tc, N1, o_c1 + HX1), tn, t == Nt - 1 ? -1.f : 1.f,
+                                                 pho[0], pho[1], pho[2], o_eta);
+            if (o_valid) {
+                store_site(yk + (int64_t)t * LL + o_off, o);
+                if (part) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc += to.c[q].x * to.c[q].x + to.c[q].y * to.c[q].y;
+                }
+            }
+            xo = xn;
+            to = tn;
+            pho[0] = phn[0]; pho[1] = phn[1]; pho[2] = phn[2];
+        }
+    }
+    cp_async_wait<0>();
+    if (part) {
+        const double tot = block_sum((double)acc, red);
+        if (threadIdx.x == 0)
+            part[(int64_t)k * (gridDim.x * gridDim.y) + blockIdx.y * gridDim.x + blockIdx.x] = tot;
+    }
+}
+
 static int largest_divisor_le(int L, int cap) {
     for (int d = cap < L ? cap : L; d >= 1; --d)
         if (L % d == 0) return d;
@@ -336,6 +536,28 @@ static ATile make_atile(const Lat& lat, int TX, int TY, int C) {
     return t;
 }
 
+// One launch of the fused A on tile tl: the plain FP32 operator takes the asynchronous-staging
+// kernel where the tile fits it, everything else the register-prefetch kernel.
+template <typename R>
+static void go_apply_A(hmc_ctx* ctx, const Lat& lat, const ATile& tl, int nrhs, const R* phi, const Site<R>* x,
+                       Site<R>* y, double* part, const CgScalars* cgs, const Site<R>* pold, Site<R>* pnew) {
+    const dim3 grid(tl.ntx * tl.nty, tl.nchunk, nrhs);
+    const Coef<R> cf = make_coef<R>(ctx->p);
+    if (pnew) {
+        k_apply_A<R, true><<<grid, kAThreads, a_smem_bytes<R>(tl), ctx->stream>>>(lat, cf, tl, phi, x, y, part, cgs,
+                                                                                  pold, pnew);
+        return;
+    }
+    if constexpr (sizeof(R) == 4) {
+        if (!cgs && tl.TX == 16 && tl.TY == 16) {
+            k_apply_A4<16, 16><<<grid, kAThreads, A4Shape<16, 16>::smem, ctx->stream>>>(lat, cf, tl, phi, x, y, part);
+            return;
+        }
+    }
+    k_apply_A<R, false><<<grid, kAThreads, a_smem_bytes<R>(tl), ctx->stream>>>(lat, cf, tl, phi, x, y, part, cgs,
+                                                                               nullptr, nullptr);
+}
+
 // Times every valid (TX, TY, C) on the call's own buffers (the launch is idempotent: y, pnew
 // and the partial sums depend only on the inputs) and returns the fastest.
 template <typename R>
@@ -368,15 +590,10 @@ static int autotune_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const Site<R>*
     HMC_CUDA(ctx, cudaEventCreate(&e0));
     HMC_CUDA(ctx, cudaEventCreate(&e1));
     float best_ms = 1e30f;
-    const Coef<R> cf = make_coef<R>(ctx->p);
     for (const ATile& tl : cand) {
         const dim3 grid(tl.ntx * tl.nty, tl.nchunk, nrhs);
         if (part && (int64_t)grid.x * grid.y * nrhs > ctx->part_cap) continue;
-        const size_t sm = a_smem_bytes<R>(tl);
-        auto go = [&]() {
-            if (pnew) k_apply_A<R, true><<<grid, kAThreads, sm, ctx->stream>>>(lat, cf, tl, phi, x, y, part, cgs, pold, pnew);
-            else k_apply_A<R, false><<<grid, kAThreads, sm, ctx->stream>>>(lat, cf, tl, phi, x, y, part, cgs, pold, pnew);
-        };
+        auto go = [&]() { go_apply_A<R>(ctx, lat, tl, nrhs, phi, x, y, part, cgs, pold, pnew); };
         go();
         HMC_CUDA(ctx, cudaEventRecord(e0, ctx->stream));
         for (int r = 0; r < 3; ++r) go();
@@ -403,6 +620,11 @@ int launch_apply_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x,
     if (!attr_set) {
         HMC_CUDA(ctx, cudaFuncSetAttribute(k_apply_A<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         HMC_CUDA(ctx, cudaFuncSetAttribute(k_apply_A<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        if constexpr (sizeof(R) == 4)
+        {
+            HMC_CUDA(ctx, cudaFuncSetAttribute(k_apply_A4<16, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)A4Shape<16, 16>::smem));
+        }
         attr_set = true;
     }
     const int prec = sizeof(R) == 8 ? HMC_FP64 : HMC_FP32;
@@ -424,21 +646,11 @@ int launch_apply_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x,
         }
         ctx->atuned.push_back(ATuned{lat.L, lat.Nt, nrhs, prec, tl.TX, tl.TY, tl.C});
     }
-    const size_t sm = a_smem_bytes<R>(tl);
     dim3 grid(tl.ntx * tl.nty, tl.nchunk, nrhs);
     if (part && (int64_t)grid.x * grid.y * nrhs > ctx->part_cap)
         return fail(ctx, HMC_ERR_ARG, "apply_A: reduction buffer too small");
-    if (pnew)
-        k_apply_A<R, true><<<grid, kAThreads, sm, ctx->stream>>>(lat, make_coef<R>(ctx->p), tl, phi,
-                                                                 reinterpret_cast<const Site<R>*>(x),
-                                                                 reinterpret_cast<Site<R>*>(y), part, cgs,
-                                                                 reinterpret_cast<const Site<R>*>(pold),
-                                                                 reinterpret_cast<Site<R>*>(pnew));
-    else
-        k_apply_A<R, false><<<grid, kAThreads, sm, ctx->stream>>>(lat, make_coef<R>(ctx->p), tl, phi,
-                                                                  reinterpret_cast<const Site<R>*>(x),
-                                                                  reinterpret_cast<Site<R>*>(y), part, cgs,
-                                                                  nullptr, nullptr);
+    go_apply_A<R>(ctx, lat, tl, nrhs, phi, reinterpret_cast<const Site<R>*>(x), reinterpret_cast<Site<R>*>(y), part,
+                  cgs, reinterpret_cast<const Site<R>*>(pold), reinterpret_cast<Site<R>*>(pnew));
     HMC_LAUNCH(ctx, "k_apply_A");
     if (nblk_out) *nblk_out = grid.x * grid.y;
     return HMC_OK;

@@ -91,6 +91,25 @@ def test_apply_A_fused(L, Nt, prec):
         assert abs(norms[k] - n2) < tol * n2
 
 
+@pytest.mark.parametrize("L,Nt", [(16, 9), (32, 6), (48, 5)])
+def test_apply_A_fp32_16x16_tiles(L, Nt):
+    # L a multiple of 16: the plain FP32 operator runs on 16 x 16 tiles with asynchronous
+    # staging; one tile wrapping onto itself (L = 16), several tiles, time chunks of 4 slices
+    # with a ragged last chunk (Nt = 9: 4 + 4 + 1, Nt = 6: 4 + 2, Nt = 5: 4 + 1)
+    ctx = ctx_for(L, Nt, nrhs=3)
+    P = oparams(L, Nt)
+    phi = dev(I.gaussian_field(30 + L, L, Nt), torch.float32)
+    x = dev(I.fermion_noise(31 + L, 3, L, Nt), torch.complex64)
+    phi_o = I.to_paper_boson(phi.double().cpu().numpy())
+    y, norms = ctx.apply_MdagM(phi, x, norms=True)
+    y2 = ctx.apply_MdagM(phi, x)   # without the norm reduction
+    for k, xk in enumerate(to_paper_vecs(x)):
+        ref = fermion.apply_A(P, phi_o, xk)
+        assert rel(to_paper_vecs(y)[k], ref) < 1e-5 and rel(to_paper_vecs(y2)[k], ref) < 1e-5
+        t = fermion.apply_Ddag(P, phi_o, xk)
+        assert abs(norms[k] - np.vdot(t, t).real) < 1e-5 * norms[k]
+
+
 @pytest.mark.parametrize("L,Nt", CASES)
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_preconditioner(L, Nt, prec):
@@ -105,9 +124,21 @@ def test_preconditioner(L, Nt, prec):
         assert rel(ys[k], solver.apply_precond(P, xs[k])) < tol
 
 
+@pytest.mark.parametrize("L,Nt", [(16, 8), (24, 6), (40, 4), (80, 4)])
+def test_preconditioner_fp32_xy_pass(L, Nt):
+    # complex64, L with a compiled (x, y) split: one kernel per band and plane does both axes,
+    # leaving the spectrum in digit-permuted order for the tau pass (the same kernels as PCG)
+    ctx = ctx_for(L, Nt)
+    P = oparams(L, Nt)
+    x = dev(I.fermion_noise(50 + L, 2, L, Nt), torch.complex64)
+    y = ctx.apply_precond(x)
+    for yk, xk in zip(to_paper_vecs(y), to_paper_vecs(x)):
+        assert rel(yk, solver.apply_precond(P, xk)) < 1e-5
+
+
 @pytest.mark.parametrize("mode", ["fp64", "mixed"])
 @pytest.mark.parametrize("precond", [False, True])
-@pytest.mark.parametrize("L,Nt", [(6, 7), (12, 24)])
+@pytest.mark.parametrize("L,Nt", [(6, 7), (12, 24), (20, 12)])
 def test_cg_solve(mode, precond, L, Nt):
     tol = 1e-10
     ctx = ctx_for(L, Nt, mode, tol=tol)
