@@ -92,13 +92,13 @@ __global__ void k_cg_alpha(CgScalars* cgs, const double* __restrict__ part, int 
 
 // r2 = ||r||^2, rz_new = <r, z> (= r2 without preconditioner), beta, convergence flags
 __global__ void k_cg_beta(CgScalars* cgs, const double* __restrict__ part_r2,
-                          const double* __restrict__ part_rz, int nblk, double tol2, double delta2,
+                          const double* __restrict__ part_rz, int nblk, int nblk_rz, double tol2, double delta2,
                           int mixed) {
     __shared__ double red[8];
     const int k = blockIdx.x;
     if (!cgs[k].active) return;
     const double r2 = row_sum(part_r2 + (int64_t)k * nblk, nblk, red);
-    const double rz = part_rz ? row_sum(part_rz + (int64_t)k * nblk, nblk, red) : r2;
+    const double rz = part_rz ? row_sum(part_rz + (int64_t)k * nblk_rz, nblk_rz, red) : r2;
     if (threadIdx.x == 0) {
         CgScalars& c = cgs[k];
         c.beta = c.rr > 0.0 ? rz / c.rr : 0.0;
@@ -309,17 +309,18 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
         { C* t = pv; pv = pw; pw = t; }
         k_cg_alpha<<<nrhs, 256, 0, sm>>>(cgs, part, nb);
         HMC_LAUNCH(ctx, "k_cg_alpha");
-        int nbr = kRedBlocks;
+        int nbr = kRedBlocks, nbz = kRedBlocks;
         if (precond) {
             // x += alpha p, r -= alpha q, z = P r, with ||r||^2 and <r, z>
-            if ((rc = launch_cg_update_precond<R>(ctx, lat, xv, rv, pv, qv, zv, nrhs, cgs, part, part2, &nbr))) return rc;
+            if ((rc = launch_cg_update_precond<R>(ctx, lat, xv, rv, pv, qv, zv, nrhs, cgs, part, part2, &nbr, &nbz)))
+                return rc;
         } else {
             k_cg_xr<R><<<vgrid, 256, 0, sm>>>(reinterpret_cast<V16<R>*>(xv), reinterpret_cast<V16<R>*>(rv),
                                               reinterpret_cast<const V16<R>*>(pv), reinterpret_cast<const V16<R>*>(qv),
                                               n16, part, cgs);
             HMC_LAUNCH(ctx, "k_cg_xr");
         }
-        k_cg_beta<<<nrhs, 256, 0, sm>>>(cgs, part, precond ? part2 : nullptr, nbr, tol2, delta2, kMixed);
+        k_cg_beta<<<nrhs, 256, 0, sm>>>(cgs, part, precond ? part2 : nullptr, nbr, nbz, tol2, delta2, kMixed);
         HMC_LAUNCH(ctx, "k_cg_beta");
         ++it;
         if (it % check_every == 0 || it >= maxit) {

@@ -457,7 +457,8 @@ int precond_tau(hmc_ctx* ctx, const Lat& lat, cplx<R>* y, int nrhs, const CgScal
     PcTables* pt = get_pc(ctx, L, Nt);
     if (!p || !pt) return fail(ctx, HMC_ERR_STATE, "no preconditioner plan for this lattice");
     if constexpr (sizeof(R) == 4) {
-        if (fftc_can(Nt, 4 * (int64_t)L * L)) return fftc_precond_tau(ctx, lat, y, nrhs, cgs, pt, pt->cosk32);
+        if (fftc_can(Nt, 4 * (int64_t)L * L))
+            return fftc_precond_tau(ctx, lat, y, nrhs, cgs, pt, pt->cosk32, nullptr, nullptr);
     }
     PrecondCoef pc;
     pc.dtau = ctx->p.dtau;
@@ -494,9 +495,9 @@ int launch_precond(hmc_ctx* ctx, const Lat& lat, const cplx<R>* x, cplx<R>* y, i
         // the (x, y) passes and tau pass that PCG runs
         const PcTables* pt = get_pc(ctx, L, Nt);
         if (pt && pt->cosk32_xy && fftc_can(Nt, 4 * (int64_t)L * L)) {
-            if ((rc = fftc_xy_apply(ctx, lat, x, y, nrhs, -1))) return rc;
-            if ((rc = fftc_precond_tau(ctx, lat, y, nrhs, nullptr, pt, pt->cosk32_xy))) return rc;
-            return fftc_xy_apply(ctx, lat, y, y, nrhs, +1);
+            if ((rc = fftc_xy_apply(ctx, lat, x, y, nrhs, -1, nullptr))) return rc;
+            if ((rc = fftc_precond_tau(ctx, lat, y, nrhs, nullptr, pt, pt->cosk32_xy, nullptr, nullptr))) return rc;
+            return fftc_xy_apply(ctx, lat, y, y, nrhs, +1, nullptr);
         }
     }
     if ((rc = fft_axis<R>(ctx, y, (int64_t)nrhs * Nt * L, L, 4, -1, x))) return rc;
@@ -515,7 +516,7 @@ template int launch_precond<double>(hmc_ctx*, const Lat&, const double2*, double
 template <typename R>
 int launch_cg_update_precond(hmc_ctx* ctx, const Lat& lat, cplx<R>* x, cplx<R>* r, const cplx<R>* p,
                              const cplx<R>* q, cplx<R>* z, int nrhs, const CgScalars* cgs, double* part_r2,
-                             double* part_rz, int* nblk_out) {
+                             double* part_rz, int* nblk_out, int* nblk_rz_out) {
     const int L = lat.L, Nt = lat.Nt;
     const FftPlan* pl = get_plan(ctx, L);
     if (!pl) return fail(ctx, HMC_ERR_STATE, "no FFT plan for length " + std::to_string(L));
@@ -536,21 +537,21 @@ int launch_cg_update_precond(hmc_ctx* ctx, const Lat& lat, cplx<R>* x, cplx<R>* 
     if constexpr (sizeof(R) == 4) {
         const PcTables* pt = get_pc(ctx, L, Nt);
         if (pt && pt->cosk32_xy && fftc_can(Nt, 4 * (int64_t)L * L)) {
-            // (x, y) in one pass each way; the spectrum between them is in digit-permuted order
-            if ((rc = fftc_xy_cg(ctx, lat, kFftcXUpd, nullptr, z, x, r, p, q, nrhs, cgs, part_r2, nblk_out))) return rc;
-            if ((rc = fftc_precond_tau(ctx, lat, z, nrhs, cgs, pt, pt->cosk32_xy))) return rc;
-            int nb2 = 0;
-            if ((rc = fftc_xy_cg(ctx, lat, kFftcXDot, z, z, nullptr, r, nullptr, nullptr, nrhs, cgs, part_rz, &nb2)))
-                return rc;
-            return HMC_OK;
+            // the vector update streams on its own; (x, y) take one pass each way with the
+            // spectrum in digit-permuted order between them, and the tau pass forms
+            // <r, z> = sum P-hat |F~^* r|^2 (F~ unitary) where it applies P-hat
+            if ((rc = fftc_xy_update(ctx, lat, x, r, p, q, nrhs, cgs, part_r2, nblk_out))) return rc;
+            if ((rc = fftc_xy_apply(ctx, lat, r, z, nrhs, -1, cgs))) return rc;
+            if ((rc = fftc_precond_tau(ctx, lat, z, nrhs, cgs, pt, pt->cosk32_xy, part_rz, nblk_rz_out))) return rc;
+            return fftc_xy_apply(ctx, lat, z, z, nrhs, +1, cgs);
         }
         if (fftc_supported(L)) {
             if ((rc = fftc_x_cg(ctx, lat, kFftcXUpd, nullptr, z, x, r, p, q, nrhs, cgs, part_r2, nblk_out))) return rc;
             if ((rc = fft_axis<R>(ctx, z, (int64_t)nrhs * Nt, L, 4 * (int64_t)L, -1, nullptr, cgs, Nt))) return rc;
             if ((rc = precond_tau<R>(ctx, lat, z, nrhs, cgs))) return rc;
             if ((rc = fft_axis<R>(ctx, z, (int64_t)nrhs * Nt, L, 4 * (int64_t)L, +1, nullptr, cgs, Nt))) return rc;
-            int nb2 = 0;
-            if ((rc = fftc_x_cg(ctx, lat, kFftcXDot, z, z, nullptr, r, nullptr, nullptr, nrhs, cgs, part_rz, &nb2)))
+            if ((rc = fftc_x_cg(ctx, lat, kFftcXDot, z, z, nullptr, r, nullptr, nullptr, nrhs, cgs, part_rz,
+                                nblk_rz_out)))
                 return rc;
             return HMC_OK;
         }
@@ -566,12 +567,14 @@ int launch_cg_update_precond(hmc_ctx* ctx, const Lat& lat, cplx<R>* x, cplx<R>* 
                                                       part_rz);
     HMC_LAUNCH(ctx, "k_fft_x_cg<2>");
     *nblk_out = (int)nblk;
+    *nblk_rz_out = (int)nblk;
     return HMC_OK;
 }
 template int launch_cg_update_precond<float>(hmc_ctx*, const Lat&, float2*, float2*, const float2*, const float2*,
-                                             float2*, int, const CgScalars*, double*, double*, int*);
+                                             float2*, int, const CgScalars*, double*, double*, int*, int*);
 template int launch_cg_update_precond<double>(hmc_ctx*, const Lat&, double2*, double2*, const double2*,
-                                              const double2*, double2*, int, const CgScalars*, double*, double*, int*);
+                                              const double2*, double2*, int, const CgScalars*, double*, double*, int*,
+                                              int*);
 
 // ---- randomized diagonal estimator of the fermion Green's function ------------------------------
 // y[k][t][.] *= e^{sign i pi t / Nt}

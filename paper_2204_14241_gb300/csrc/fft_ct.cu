@@ -370,6 +370,7 @@ __global__ void __launch_bounds__(kThreads) k_fftc(FftcArgs A) {
             const float re = ew.x + base;
             const float ph = 1.0f / (re * re + ew.y * ew.y);
             float4 v = *reinterpret_cast<float4*>(res + j * NL + icp);
+            acc += ph * (v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w);   // sum P-hat |v|^2
             v.x *= ph; v.y *= ph; v.z *= ph; v.w *= ph;
             *reinterpret_cast<float4*>(res + j * NL + icp) = v;
         }
@@ -413,6 +414,13 @@ __global__ void __launch_bounds__(kThreads) k_fftc(FftcArgs A) {
     if constexpr (MODE == kXUpd || MODE == kXDot) {
         const double tot = block_sum((double)acc, red);
         if (threadIdx.x == 0) A.part[(int64_t)k * gridDim.x + blockIdx.x] = tot;
+    }
+    if constexpr (MODE == kTau) {
+        // the forward FFT above is unnormalised: |v|^2 = N |unitary coefficient|^2
+        if (A.part) {
+            const double tot = block_sum((double)acc, red);
+            if (threadIdx.x == 0) A.part[blockIdx.x] = tot / N;   // block = k * nib + inner block
+        }
     }
 }
 
@@ -484,7 +492,7 @@ int fftc_axis(hmc_ctx* ctx, float2* data, int64_t outer, int n, int64_t inner, i
 }
 
 int fftc_precond_tau(hmc_ctx* ctx, const Lat& lat, float2* y, int nrhs, const CgScalars* cgs,
-                     const PcTables* pt, const float* cosk) {
+                     const PcTables* pt, const float* cosk, double* part, int* nblk_out) {
     const int n = lat.Nt;
     const FftPlan* pl = get_plan(ctx, n);
     if (!pl) return fail(ctx, HMC_ERR_STATE, "no FFT plan");
@@ -509,6 +517,11 @@ int fftc_precond_tau(hmc_ctx* ctx, const Lat& lat, float2* y, int nrhs, const Cg
     A.twist = pt->twist32;
     if (A.inner < NL) return fail(ctx, HMC_ERR_STATE, "fftc: unsupported tile");
     A.nib = (A.inner + NL - 1) / NL;
+    A.part = part;
+    if (part) {
+        if (A.nib * nrhs > ctx->part_cap / 2) return fail(ctx, HMC_ERR_ARG, "fftc: reduction buffer too small");
+        *nblk_out = (int)A.nib;
+    }
     const dim3 grid((unsigned)(nrhs * A.nib));
 #define HMC_CASE(N) \
     if (n == N) return launch_one<N, 0, kTau, -1>(ctx, grid, A);
@@ -554,14 +567,15 @@ int fftc_x_cg(hmc_ctx* ctx, const Lat& lat, int mode, const float2* src, float2*
 
 // ---- (x, y) passes of the preconditioner inside PCG ------------------------------------------
 // One block transforms one band (the two spin components, 16 bytes per site) of one (RHS, tau)
-// plane in shared memory, both axes, so the x and y passes cost one read and one write of the
-// vector instead of two. Each axis is a two-factor Cooley-Tukey split L = N1 * N2 done in place:
-// with n = n1 + N1 n2 and k = k2 + N2 k1,
+// plane in shared memory along both axes, so the x and y passes cost one read and one write of
+// the vector instead of two. Each axis is a two-factor Cooley-Tukey split L = N1 * N2 done in
+// place: with n = n1 + N1 n2 and k = k2 + N2 k1,
 //   step A (fixed n1): N2-point DFT over n2, times w_L^{n1 k2}, written back to n1 + N1 k2;
 //   step B (fixed k2): N1-point DFT over n1 at positions N1 k2 + n1, written back in place.
 // Position N1 k2 + k1 then holds frequency k2 + N2 k1: the forward pass leaves the spectrum
 // in this digit-permuted order (the tau pass reads its cos k table in the same order) and the
-// inverse pass (step B then step A, conjugate twiddles) takes it back to natural order.
+// inverse pass (step B then step A, conjugate twiddles) takes it back to natural order. A task
+// transforms one line for both spins (16-byte shared-memory accesses).
 template <int L> struct XYSplit { static constexpr int N1 = 0, N2 = 0; };
 template <> struct XYSplit<12> { static constexpr int N1 = 4, N2 = 3; };
 template <> struct XYSplit<16> { static constexpr int N1 = 4, N2 = 4; };
@@ -575,148 +589,128 @@ constexpr int kXYThreads = 320;
 // row stride (in sites) of the shared plane: = 1 mod 8 so that eight consecutive rows at one
 // column fall in distinct bank groups
 constexpr int xy_row_stride(int L) { return L + ((9 - L % 8) % 8); }
+template <int L> constexpr size_t xy_smem_bytes() { return (size_t)L * xy_row_stride(L) * sizeof(float4); }
 
 // In-place DFTs of size R over the positions base(line) + S * m, m < R, for every (line, f)
-// task; AX = 0: lines along x (line = (row y, spin c)), AX = 1: lines along y (line = (column
-// x, spin c)). STEP_A: f = n1, positions n1 + N1 m; else f = k2, positions N1 k2 + m. TW
-// multiplies output m by w_L^{DIR f m} (step A) or w_L^{DIR m f} (step B).
+// task, both spins at once; AX = 0: lines along x (line = row y), AX = 1: lines along y
+// (line = column x). STEP_A: f = n1, positions n1 + N1 m; else f = k2, positions N1 k2 + m.
+// TW multiplies output m by w_L^{DIR f m} (twiddle table tw in shared memory, forward sign).
 template <int L, int AX, bool STEP_A, bool TW, int DIR>
-__device__ __forceinline__ void xy_step(float2* sm, const float2* __restrict__ tw) {
+__device__ __forceinline__ void xy_step(float4* sm, const float2* tw) {
     constexpr int N1 = XYSplit<L>::N1, N2 = XYSplit<L>::N2, RS = xy_row_stride(L);
     constexpr int R = STEP_A ? N2 : N1;
     constexpr int NF = STEP_A ? N1 : N2;
-    constexpr int total = 2 * L * NF;
-#pragma unroll 2
+    constexpr int total = L * NF;
+#pragma unroll 1
     for (int task = threadIdx.x; task < total; task += kXYThreads) {
-        const int line = task % (2 * L), f = task / (2 * L);
-        const int a = line >> 1, c = line & 1;
-        auto at = [&](int pos) { return AX == 0 ? ((a * RS + pos) << 1) + c : ((pos * RS + a) << 1) + c; };
-        float2 v[R];
+        const int a = task % L, f = task / L;
+        float4* base = AX == 0 ? sm + a * RS + (STEP_A ? f : N1 * f) : sm + a + (STEP_A ? f : N1 * f) * RS;
+        constexpr int S = (STEP_A ? N1 : 1) * (AX == 0 ? 1 : RS);   // stride between the R points
+        float2 u[R], v[R];
 #pragma unroll
-        for (int m = 0; m < R; ++m) v[m] = sm[at(STEP_A ? f + N1 * m : N1 * f + m)];
+        for (int m = 0; m < R; ++m) {
+            const float4 e = base[m * S];
+            u[m] = make_float2(e.x, e.y);
+            v[m] = make_float2(e.z, e.w);
+        }
+        bfly<R, DIR>(u);
         bfly<R, DIR>(v);
         if constexpr (TW) {
 #pragma unroll
             for (int m = 1; m < R; ++m) {
-                float2 w = __ldg(tw + f * m);   // f * m < L
+                float2 w = tw[f * m];   // f * m < L
                 if (DIR > 0) w.y = -w.y;
+                u[m] = make_float2(u[m].x * w.x - u[m].y * w.y, u[m].x * w.y + u[m].y * w.x);
                 v[m] = make_float2(v[m].x * w.x - v[m].y * w.y, v[m].x * w.y + v[m].y * w.x);
             }
         }
 #pragma unroll
-        for (int m = 0; m < R; ++m) sm[at(STEP_A ? f + N1 * m : N1 * f + m)] = v[m];
+        for (int m = 0; m < R; ++m) base[m * S] = make_float4(u[m].x, u[m].y, v[m].x, v[m].y);
     }
 }
 
-// MODE kXUpd (DIR -1): x += alpha p, r -= alpha q (written back), partial ||r||^2,
-// dst = F_xy r (permuted order). MODE kXDot (DIR +1): dst = F_xy^-1 src (permuted order in,
-// natural out), partial Re <r, dst>. MODE kPlain: dst = F_xy src (DIR -1) or F_xy^-1 src
-// (DIR +1), every right-hand side. Grid (2 Nt, nrhs): block (2 t + band, k). dst may alias src.
-template <int L, int MODE, int DIR>
+// dst = F_xy src (DIR -1, permuted order out) or F_xy^-1 src (DIR +1, permuted order in).
+// Grid (2 Nt, nrhs): block (2 t + band, k); right-hand sides with cgs[k].active == 0 are
+// skipped when cgs is given. dst may alias src.
+template <int L, int DIR>
 __global__ void __launch_bounds__(kXYThreads, 2) k_fft_xy(FftcArgs A, int Nt) {
-    static_assert(MODE == kPlain || (MODE == kXUpd) == (DIR < 0), "update pass is forward, dot pass inverse");
     constexpr int RS = xy_row_stride(L);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[kXYThreads / 32];
-    float2* sm = reinterpret_cast<float2*>(smem_raw);   // [L][RS] sites x 2 spins
+    __shared__ float2 tws[L];
+    float4* sm = reinterpret_cast<float4*>(smem_raw);   // [L][RS] sites, both spins
     const int k = blockIdx.y;
     if (A.cgs && !A.cgs[k].active) return;
     const int t = blockIdx.x >> 1, band = blockIdx.x & 1;
     const int64_t g0 = (((int64_t)k * Nt + t) * L * L) * 4 + 2 * band;   // float2 index of site 0
-    float alpha = 0.f;
-    if constexpr (MODE == kXUpd) alpha = (float)A.cgs[k].alpha;
-    float acc = 0.f;
+    for (int i = threadIdx.x; i < L; i += kXYThreads) tws[i] = __ldg(A.tw + i);
 
-    // sites are taken XB at a time: all loads of a batch are issued before its stores (the
-    // vectors may alias as far as the compiler knows)
-    constexpr int XB = 4;
-    for (int e0 = threadIdx.x; e0 < L * L; e0 += XB * kXYThreads) {
-        float4 v[XB];
-        if constexpr (MODE == kXUpd) {
-            float4 xx[XB], pp[XB], qq[XB];
-#pragma unroll
-            for (int b = 0; b < XB; ++b) {
-                const int e = e0 + b * kXYThreads;
-                if (e < L * L) {
-                    const int64_t g = g0 + 4 * (int64_t)e;
-                    xx[b] = *reinterpret_cast<const float4*>(A.x + g);
-                    v[b] = *reinterpret_cast<const float4*>(A.r + g);
-                    pp[b] = *reinterpret_cast<const float4*>(A.p + g);
-                    qq[b] = *reinterpret_cast<const float4*>(A.q + g);
-                }
-            }
-#pragma unroll
-            for (int b = 0; b < XB; ++b) {
-                const int e = e0 + b * kXYThreads;
-                if (e < L * L) {
-                    const int64_t g = g0 + 4 * (int64_t)e;
-                    float4& xb = xx[b];
-                    float4& rb = v[b];
-                    xb.x += alpha * pp[b].x; xb.y += alpha * pp[b].y; xb.z += alpha * pp[b].z; xb.w += alpha * pp[b].w;
-                    rb.x -= alpha * qq[b].x; rb.y -= alpha * qq[b].y; rb.z -= alpha * qq[b].z; rb.w -= alpha * qq[b].w;
-                    *reinterpret_cast<float4*>(A.x + g) = xb;
-                    *reinterpret_cast<float4*>(A.r + g) = rb;
-                    acc += rb.x * rb.x + rb.y * rb.y + rb.z * rb.z + rb.w * rb.w;
-                }
-            }
-        } else {
-#pragma unroll
-            for (int b = 0; b < XB; ++b) {
-                const int e = e0 + b * kXYThreads;
-                if (e < L * L) v[b] = *reinterpret_cast<const float4*>(A.src + g0 + 4 * (int64_t)e);
-            }
-        }
-#pragma unroll
-        for (int b = 0; b < XB; ++b) {
-            const int e = e0 + b * kXYThreads;
-            if (e < L * L) *reinterpret_cast<float4*>(sm + 2 * ((e / L) * RS + e % L)) = v[b];
-        }
-    }
+    // the whole band-plane is requested at once (cp.async, 16 bytes per site)
+    for (int e = threadIdx.x; e < L * L; e += kXYThreads)
+        cp_async16(sm + (e / L) * RS + e % L, A.src + g0 + 4 * (int64_t)e);
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     if constexpr (DIR < 0) {
-        xy_step<L, 0, true, true, DIR>(sm, A.tw);
+        xy_step<L, 0, true, true, DIR>(sm, tws);
         __syncthreads();
-        xy_step<L, 0, false, false, DIR>(sm, A.tw);
+        xy_step<L, 0, false, false, DIR>(sm, tws);
         __syncthreads();
-        xy_step<L, 1, true, true, DIR>(sm, A.tw);
+        xy_step<L, 1, true, true, DIR>(sm, tws);
         __syncthreads();
-        xy_step<L, 1, false, false, DIR>(sm, A.tw);
+        xy_step<L, 1, false, false, DIR>(sm, tws);
     } else {
-        xy_step<L, 1, false, true, DIR>(sm, A.tw);
+        xy_step<L, 1, false, true, DIR>(sm, tws);
         __syncthreads();
-        xy_step<L, 1, true, false, DIR>(sm, A.tw);
+        xy_step<L, 1, true, false, DIR>(sm, tws);
         __syncthreads();
-        xy_step<L, 0, false, true, DIR>(sm, A.tw);
+        xy_step<L, 0, false, true, DIR>(sm, tws);
         __syncthreads();
-        xy_step<L, 0, true, false, DIR>(sm, A.tw);
+        xy_step<L, 0, true, false, DIR>(sm, tws);
     }
     __syncthreads();
     const float sc = 1.0f / (float)L;   // unitary on both axes
-    for (int e0 = threadIdx.x; e0 < L * L; e0 += XB * kXYThreads) {
-        float4 rr[XB];
-        if constexpr (MODE == kXDot) {
+    for (int e = threadIdx.x; e < L * L; e += kXYThreads) {
+        float4 v = sm[(e / L) * RS + e % L];
+        v.x *= sc; v.y *= sc; v.z *= sc; v.w *= sc;
+        *reinterpret_cast<float4*>(A.dst + g0 + 4 * (int64_t)e) = v;
+    }
+}
+
+// x += alpha p, r -= alpha q and one partial ||r||^2 per band-plane-sized chunk: grid (2 Nt,
+// nrhs), so that the partials line up with those of the inverse (x, y) pass.
+__global__ void __launch_bounds__(256) k_xy_cg_update(FftcArgs A, int64_t chunk4) {
+    __shared__ double red[8];
+    const int k = blockIdx.y;
+    if (!A.cgs[k].active) return;
+    const float alpha = (float)A.cgs[k].alpha;
+    const int64_t o = ((int64_t)k * gridDim.x + blockIdx.x) * chunk4;   // float4 index
+    float4* x = reinterpret_cast<float4*>(A.x) + o;
+    float4* r = reinterpret_cast<float4*>(A.r) + o;
+    const float4* p = reinterpret_cast<const float4*>(A.p) + o;
+    const float4* q = reinterpret_cast<const float4*>(A.q) + o;
+    float acc = 0.f;
+    constexpr int XB = 4;
+    for (int64_t e0 = threadIdx.x; e0 < chunk4; e0 += XB * 256) {
+        float4 xx[XB], rr[XB], pp[XB], qq[XB];
 #pragma unroll
-            for (int b = 0; b < XB; ++b) {
-                const int e = e0 + b * kXYThreads;
-                if (e < L * L) rr[b] = *reinterpret_cast<const float4*>(A.r + g0 + 4 * (int64_t)e);
-            }
+        for (int b = 0; b < XB; ++b) {
+            const int64_t e = e0 + b * 256;
+            if (e < chunk4) { xx[b] = x[e]; rr[b] = r[e]; pp[b] = p[e]; qq[b] = q[e]; }
         }
 #pragma unroll
         for (int b = 0; b < XB; ++b) {
-            const int e = e0 + b * kXYThreads;
-            if (e < L * L) {
-                float4 v = *reinterpret_cast<const float4*>(sm + 2 * ((e / L) * RS + e % L));
-                v.x *= sc; v.y *= sc; v.z *= sc; v.w *= sc;
-                *reinterpret_cast<float4*>(A.dst + g0 + 4 * (int64_t)e) = v;
-                if constexpr (MODE == kXDot)
-                    acc += rr[b].x * v.x + rr[b].y * v.y + rr[b].z * v.z + rr[b].w * v.w;
+            const int64_t e = e0 + b * 256;
+            if (e < chunk4) {
+                xx[b].x += alpha * pp[b].x; xx[b].y += alpha * pp[b].y; xx[b].z += alpha * pp[b].z; xx[b].w += alpha * pp[b].w;
+                rr[b].x -= alpha * qq[b].x; rr[b].y -= alpha * qq[b].y; rr[b].z -= alpha * qq[b].z; rr[b].w -= alpha * qq[b].w;
+                x[e] = xx[b];
+                r[e] = rr[b];
+                acc += rr[b].x * rr[b].x + rr[b].y * rr[b].y + rr[b].z * rr[b].z + rr[b].w * rr[b].w;
             }
         }
     }
-    if constexpr (MODE != kPlain) {
-        const double tot = block_sum((double)acc, red);
-        if (threadIdx.x == 0) A.part[(int64_t)k * gridDim.x + blockIdx.x] = tot;
-    }
+    const double tot = block_sum((double)acc, red);
+    if (threadIdx.x == 0) A.part[(int64_t)k * gridDim.x + blockIdx.x] = tot;
 }
 
 bool fftc_xy_supported(int L) {
@@ -734,59 +728,48 @@ int fftc_xy_freq(int L, int pos) {
     return -1;
 }
 
-template <int L, int MODE, int DIR>
-static int launch_xy(hmc_ctx* ctx, dim3 grid, const FftcArgs& A, int Nt) {
-    constexpr size_t sm = (size_t)L * xy_row_stride(L) * 2 * sizeof(float2);
+template <int L, int DIR>
+static int launch_xy(hmc_ctx* ctx, const FftcArgs& A, int Nt, int nrhs) {
+    constexpr size_t sm = xy_smem_bytes<L>();
     static bool attr = false;
     if (!attr) {
-        HMC_CUDA(ctx, cudaFuncSetAttribute(k_fft_xy<L, MODE, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)sm));
+        HMC_CUDA(ctx, cudaFuncSetAttribute(k_fft_xy<L, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         attr = true;
     }
-    k_fft_xy<L, MODE, DIR><<<grid, kXYThreads, sm, ctx->stream>>>(A, Nt);
+    k_fft_xy<L, DIR><<<dim3((unsigned)(2 * Nt), nrhs), kXYThreads, sm, ctx->stream>>>(A, Nt);
     HMC_LAUNCH(ctx, "k_fft_xy");
     return HMC_OK;
 }
 
-int fftc_xy_cg(hmc_ctx* ctx, const Lat& lat, int mode, const float2* src, float2* dst, float2* x, float2* r,
-               const float2* p, const float2* q, int nrhs, const CgScalars* cgs, double* part, int* nblk_out) {
-    const int L = lat.L;
-    const FftPlan* pl = get_plan(ctx, L);
-    if (!pl) return fail(ctx, HMC_ERR_STATE, "no FFT plan");
+int fftc_xy_update(hmc_ctx* ctx, const Lat& lat, float2* x, float2* r, const float2* p, const float2* q, int nrhs,
+                   const CgScalars* cgs, double* part, int* nblk_out) {
     FftcArgs A{};
-    A.src = src;
-    A.dst = dst;
     A.x = x;
     A.r = r;
     A.p = p;
     A.q = q;
     A.cgs = cgs;
     A.part = part;
-    A.tw = pl->tw32;
     const int64_t nblk = 2 * (int64_t)lat.Nt;
     if (nblk * nrhs > ctx->part_cap / 2) return fail(ctx, HMC_ERR_ARG, "fftc: reduction buffer too small");
-    const dim3 grid((unsigned)nblk, nrhs);
     *nblk_out = (int)nblk;
-#define HMC_CASE(N)                                                                    \
-    if (L == N) return mode == kXUpd ? launch_xy<N, kXUpd, -1>(ctx, grid, A, lat.Nt)  \
-                                     : launch_xy<N, kXDot, +1>(ctx, grid, A, lat.Nt);
-    HMC_FFTXY_SIZES(HMC_CASE)
-#undef HMC_CASE
-    return fail(ctx, HMC_ERR_STATE, "fftc: unsupported length");
+    k_xy_cg_update<<<dim3((unsigned)nblk, nrhs), 256, 0, ctx->stream>>>(A, (int64_t)lat.L * lat.L);
+    HMC_LAUNCH(ctx, "k_xy_cg_update");
+    return HMC_OK;
 }
 
-int fftc_xy_apply(hmc_ctx* ctx, const Lat& lat, const float2* src, float2* dst, int nrhs, int dir) {
+int fftc_xy_apply(hmc_ctx* ctx, const Lat& lat, const float2* src, float2* dst, int nrhs, int dir,
+                  const CgScalars* cgs) {
     const int L = lat.L;
     const FftPlan* pl = get_plan(ctx, L);
     if (!pl) return fail(ctx, HMC_ERR_STATE, "no FFT plan");
     FftcArgs A{};
     A.src = src;
     A.dst = dst;
+    A.cgs = cgs;
     A.tw = pl->tw32;
-    const dim3 grid((unsigned)(2 * lat.Nt), nrhs);
-#define HMC_CASE(N)                                                                    \
-    if (L == N) return dir < 0 ? launch_xy<N, kPlain, -1>(ctx, grid, A, lat.Nt)       \
-                               : launch_xy<N, kPlain, +1>(ctx, grid, A, lat.Nt);
+#define HMC_CASE(N)                                                                \
+    if (L == N) return dir < 0 ? launch_xy<N, -1>(ctx, A, lat.Nt, nrhs) : launch_xy<N, +1>(ctx, A, lat.Nt, nrhs);
     HMC_FFTXY_SIZES(HMC_CASE)
 #undef HMC_CASE
     return fail(ctx, HMC_ERR_STATE, "fftc: unsupported length");

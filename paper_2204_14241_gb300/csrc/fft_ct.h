@@ -15,20 +15,23 @@ int fftc_axis(hmc_ctx* ctx, float2* data, int64_t outer, int n, int64_t inner, i
               const CgScalars* cgs, int64_t opr);
 // cosk: the cos k table indexed by the position of k along x and y (pt->cosk32 for natural
 // order, pt->cosk32_xy after the (x, y) pass of fftc_xy_cg)
+// part (optional): partial sums of sum P-hat |y-hat|^2 = <y_in, P y_in> when the transform
+// ahead of this pass is unitary; *nblk_out of them per right-hand side
 int fftc_precond_tau(hmc_ctx* ctx, const Lat& lat, float2* y, int nrhs, const CgScalars* cgs, const PcTables* pt,
-                     const float* cosk);
+                     const float* cosk, double* part, int* nblk_out);
 int fftc_x_cg(hmc_ctx* ctx, const Lat& lat, int mode, const float2* src, float2* dst, float2* x, float2* r,
               const float2* p, const float2* q, int nrhs, const CgScalars* cgs, double* part, int* nblk_out);
 
-// (x, y) passes fused in one kernel per band and plane (lattice extents with a compiled split):
-// kFftcXUpd: CG update and forward transform into digit-permuted order; kFftcXDot: inverse
-// transform back to natural order and <r, z>. Partial sums: 2 Nt per right-hand side.
+// (x, y) passes in one kernel per band and plane, for lattice extents with a compiled split
 bool fftc_xy_supported(int L);
 // frequency index held at position pos of an axis after the forward (x, y) pass
 int fftc_xy_freq(int L, int pos);
-// dst = F_xy src (dir < 0, permuted order out) or F_xy^-1 src (dir > 0, permuted order in)
-int fftc_xy_apply(hmc_ctx* ctx, const Lat& lat, const float2* src, float2* dst, int nrhs, int dir);
-int fftc_xy_cg(hmc_ctx* ctx, const Lat& lat, int mode, const float2* src, float2* dst, float2* x, float2* r,
-               const float2* p, const float2* q, int nrhs, const CgScalars* cgs, double* part, int* nblk_out);
+// dst = F_xy src (dir < 0, permuted order out) or F_xy^-1 src (dir > 0, permuted order in);
+// right-hand sides with cgs[k].active == 0 are skipped when cgs is given
+int fftc_xy_apply(hmc_ctx* ctx, const Lat& lat, const float2* src, float2* dst, int nrhs, int dir,
+                  const CgScalars* cgs);
+// x += alpha p, r -= alpha q with partial ||r||^2 (*nblk_out = 2 Nt per right-hand side)
+int fftc_xy_update(hmc_ctx* ctx, const Lat& lat, float2* x, float2* r, const float2* p, const float2* q, int nrhs,
+                   const CgScalars* cgs, double* part, int* nblk_out);
 
 }  // namespace hmc

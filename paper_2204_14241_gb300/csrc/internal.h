@@ -163,11 +163,11 @@ int fft_axis(hmc_ctx* ctx, cplx<R>* data, int64_t outer, int n, int64_t inner, i
 template <typename R>
 int launch_precond(hmc_ctx* ctx, const Lat& lat, const cplx<R>* x, cplx<R>* y, int nrhs);
 // x += alpha p, r -= alpha q, z = P r for every active RHS with partial sums of ||r||^2 and
-// <r, z> (rows of *nblk_out entries per RHS in part_r2 / part_rz).
+// <r, z> (rows of *nblk_out entries per RHS in part_r2, of *nblk_rz_out in part_rz).
 template <typename R>
 int launch_cg_update_precond(hmc_ctx* ctx, const Lat& lat, cplx<R>* x, cplx<R>* r, const cplx<R>* p,
                              const cplx<R>* q, cplx<R>* z, int nrhs, const CgScalars* cgs, double* part_r2,
-                             double* part_rz, int* nblk_out);
+                             double* part_rz, int* nblk_out, int* nblk_rz_out);
 int metric_op(hmc_ctx* ctx, const Lat& lat, int op, const double* sig, const double* in,
               double* out, double eps, double* scalar_dev);
 

@@ -296,18 +296,6 @@ k_apply_A(Lat lat, Coef<R> cf, ATile tl, const R* __restrict__ phi, const Site<R
 // The one-site-ring t_ sites are a second job of threads 0, 1, ... One barrier per step:
 // step t writes t_(t+1) into the t_ buffer that y(t-1) read before the barrier, and reads
 // t_(t), written before it; slice t+3 goes into the x buffer of slice t-1, last read before it.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
 
 constexpr int kA4Ring = 4;   // x and phi slices resident: t-1 .. t+2
 
