@@ -207,6 +207,20 @@ __global__ void k_to32(const double2* __restrict__ a, float2* __restrict__ b, in
     }
 }
 
+// pnew = z + beta pold for every active right-hand side: the direction after a (re)start of
+// the complex64 PCG with the fused (x, y) passes, whose iterations form it in that pass
+__global__ void k_pupd(float4* __restrict__ pnew, const float4* __restrict__ z, const float4* __restrict__ pold,
+                       int64_t n4, const CgScalars* __restrict__ cgs) {
+    const int k = blockIdx.y;
+    if (!cgs[k].active) return;
+    const float beta = (float)cgs[k].beta;
+    const int64_t off = k * n4;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = z[off + i], b = pold[off + i];
+        pnew[off + i] = make_float4(a.x + beta * b.x, a.y + beta * b.y, a.z + beta * b.z, a.w + beta * b.w);
+    }
+}
+
 __global__ void k_phi_to32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) b[i] = (float)a[i];
@@ -262,8 +276,14 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
     }
     HMC_LAUNCH(ctx, "k_cg_start");
 
-    // directions start at zero: the first fused update forms p = z + 0 * p
+    // complex64 PCG with the fused (x, y) passes: the direction update p = z + beta p moves from
+    // the operator launch into the inverse (x, y) pass (beta is known by then: <r, z> comes from
+    // the tau pass)
+    bool xy = false;
+    if constexpr (kMixed) xy = precond && pcg_xy_path(ctx, lat);
+    // directions start at zero: the first update forms p = z + 0 * p
     HMC_CUDA(ctx, cudaMemsetAsync(pv, 0, nrhs * n * sizeof(C), sm));
+    if (xy) HMC_CUDA(ctx, cudaMemsetAsync(pw, 0, nrhs * n * sizeof(C), sm));
     // z = P r, rz = <r, z>
     auto restart_dir = [&]() -> int {
         if (precond) {
@@ -277,6 +297,14 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
         HMC_LAUNCH(ctx, "k_dot");
         k_cg_set_rz<<<nrhs, 256, 0, sm>>>(cgs, part, kRedBlocks);
         HMC_LAUNCH(ctx, "k_cg_set_rz");
+        if constexpr (kMixed) {
+            if (xy) {
+                // pv = z + beta pw: pw holds the direction of the last operator application
+                k_pupd<<<vgrid, 256, 0, sm>>>(reinterpret_cast<float4*>(pv), reinterpret_cast<const float4*>(zv),
+                                              reinterpret_cast<const float4*>(pw), n / 2, cgs);
+                HMC_LAUNCH(ctx, "k_pupd");
+            }
+        }
         return HMC_OK;
     };
     if ((rc = restart_dir())) return rc;
@@ -303,8 +331,24 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
     int it = 0;
     while (!done) {
         if (it >= maxit) break;
-        // p = z + beta p (fused into the operator), q = A p, partial <p, A p>
         int nb = 0;
+        if constexpr (kMixed) {
+            if (xy) {
+                // q = A p, partial <p, A p>; x, r update and zhat = P-hat F~^* r; beta; next p
+                if ((rc = launch_apply_A<R>(ctx, lat, phiR, pv, qv, nrhs, part, &nb, cgs))) return rc;
+                k_cg_alpha<<<nrhs, 256, 0, sm>>>(cgs, part, nb);
+                HMC_LAUNCH(ctx, "k_cg_alpha");
+                int nbr = 0, nbz = 0;
+                if ((rc = launch_pcg_xy_forward(ctx, lat, xv, rv, pv, qv, zv, nrhs, cgs, part, part2, &nbr, &nbz)))
+                    return rc;
+                k_cg_beta<<<nrhs, 256, 0, sm>>>(cgs, part, part2, nbr, nbz, tol2, delta2, kMixed);
+                HMC_LAUNCH(ctx, "k_cg_beta");
+                if ((rc = launch_pcg_xy_inverse(ctx, lat, zv, pv, pw, nrhs, cgs))) return rc;
+                { C* t = pv; pv = pw; pw = t; }
+            }
+        }
+        if (!xy) {
+        // p = z + beta p (fused into the operator), q = A p, partial <p, A p>
         if ((rc = launch_apply_A<R>(ctx, lat, phiR, zv, qv, nrhs, part, &nb, cgs, pv, pw))) return rc;
         { C* t = pv; pv = pw; pw = t; }
         k_cg_alpha<<<nrhs, 256, 0, sm>>>(cgs, part, nb);
@@ -322,6 +366,7 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
         }
         k_cg_beta<<<nrhs, 256, 0, sm>>>(cgs, part, precond ? part2 : nullptr, nbr, nbz, tol2, delta2, kMixed);
         HMC_LAUNCH(ctx, "k_cg_beta");
+        }
         ++it;
         if (it % check_every == 0 || it >= maxit) {
             HMC_CUDA(ctx, cudaMemcpyAsync(ctx->h_cg, cgs, nrhs * sizeof(CgScalars), cudaMemcpyDeviceToHost, sm));

@@ -535,16 +535,6 @@ int launch_cg_update_precond(hmc_ctx* ctx, const Lat& lat, cplx<R>* x, cplx<R>* 
     }
     int rc;
     if constexpr (sizeof(R) == 4) {
-        const PcTables* pt = get_pc(ctx, L, Nt);
-        if (pt && pt->cosk32_xy && fftc_can(Nt, 4 * (int64_t)L * L)) {
-            // the vector update streams on its own; (x, y) take one pass each way with the
-            // spectrum in digit-permuted order between them, and the tau pass forms
-            // <r, z> = sum P-hat |F~^* r|^2 (F~ unitary) where it applies P-hat
-            if ((rc = fftc_xy_update(ctx, lat, x, r, p, q, nrhs, cgs, part_r2, nblk_out))) return rc;
-            if ((rc = fftc_xy_apply(ctx, lat, r, z, nrhs, -1, cgs))) return rc;
-            if ((rc = fftc_precond_tau(ctx, lat, z, nrhs, cgs, pt, pt->cosk32_xy, part_rz, nblk_rz_out))) return rc;
-            return fftc_xy_apply(ctx, lat, z, z, nrhs, +1, cgs);
-        }
         if (fftc_supported(L)) {
             if ((rc = fftc_x_cg(ctx, lat, kFftcXUpd, nullptr, z, x, r, p, q, nrhs, cgs, part_r2, nblk_out))) return rc;
             if ((rc = fft_axis<R>(ctx, z, (int64_t)nrhs * Nt, L, 4 * (int64_t)L, -1, nullptr, cgs, Nt))) return rc;
@@ -570,6 +560,29 @@ int launch_cg_update_precond(hmc_ctx* ctx, const Lat& lat, cplx<R>* x, cplx<R>* 
     *nblk_rz_out = (int)nblk;
     return HMC_OK;
 }
+bool pcg_xy_path(hmc_ctx* ctx, const Lat& lat) {
+    const PcTables* pt = get_pc(ctx, lat.L, lat.Nt);
+    return pt && pt->cosk32_xy && fftc_can(lat.Nt, 4 * (int64_t)lat.L * lat.L);
+}
+
+int launch_pcg_xy_forward(hmc_ctx* ctx, const Lat& lat, float2* x, float2* r, const float2* p, const float2* q,
+                          float2* zhat, int nrhs, const CgScalars* cgs, double* part_r2, double* part_rz,
+                          int* nblk_r2, int* nblk_rz) {
+    const PcTables* pt = get_pc(ctx, lat.L, lat.Nt);
+    if (!pt || !pt->cosk32_xy) return fail(ctx, HMC_ERR_STATE, "no (x, y) pass for this lattice");
+    int rc;
+    // the vector update streams on its own; the (x, y) pass leaves the spectrum in digit-permuted
+    // order, and the tau pass forms <r, z> = sum P-hat |F~^* r|^2 (F~ unitary) as it applies P-hat
+    if ((rc = fftc_xy_update(ctx, lat, x, r, p, q, nrhs, cgs, part_r2, nblk_r2))) return rc;
+    if ((rc = fftc_xy_apply(ctx, lat, r, zhat, nrhs, -1, cgs))) return rc;
+    return fftc_precond_tau(ctx, lat, zhat, nrhs, cgs, pt, pt->cosk32_xy, part_rz, nblk_rz);
+}
+
+int launch_pcg_xy_inverse(hmc_ctx* ctx, const Lat& lat, const float2* zhat, const float2* pold, float2* pnew,
+                          int nrhs, const CgScalars* cgs) {
+    return fftc_xy_inverse_pupd(ctx, lat, zhat, pold, pnew, nrhs, cgs);
+}
+
 template int launch_cg_update_precond<float>(hmc_ctx*, const Lat&, float2*, float2*, const float2*, const float2*,
                                              float2*, int, const CgScalars*, double*, double*, int*, int*);
 template int launch_cg_update_precond<double>(hmc_ctx*, const Lat&, double2*, double2*, const double2*,

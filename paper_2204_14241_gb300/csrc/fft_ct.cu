@@ -630,10 +630,13 @@ __device__ __forceinline__ void xy_step(float4* sm, const float2* tw) {
 }
 
 // dst = F_xy src (DIR -1, permuted order out) or F_xy^-1 src (DIR +1, permuted order in).
-// Grid (2 Nt, nrhs): block (2 t + band, k); right-hand sides with cgs[k].active == 0 are
-// skipped when cgs is given. dst may alias src.
-template <int L, int DIR>
+// PUPD (DIR +1): dst = F_xy^-1 src + beta_k pold instead, the CG direction update
+// p_{k+1} = z + beta_k p_k (A.p = pold, which must not alias dst). Grid (2 Nt, nrhs): block
+// (2 t + band, k); right-hand sides with cgs[k].active == 0 are skipped when cgs is given.
+// dst may alias src.
+template <int L, int DIR, bool PUPD>
 __global__ void __launch_bounds__(kXYThreads, 2) k_fft_xy(FftcArgs A, int Nt) {
+    static_assert(!PUPD || DIR > 0, "the direction update follows the inverse pass");
     constexpr int RS = xy_row_stride(L);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ float2 tws[L];
@@ -648,6 +651,12 @@ __global__ void __launch_bounds__(kXYThreads, 2) k_fft_xy(FftcArgs A, int Nt) {
     for (int e = threadIdx.x; e < L * L; e += kXYThreads)
         cp_async16(sm + (e / L) * RS + e % L, A.src + g0 + 4 * (int64_t)e);
     cp_async_commit();
+    if constexpr (PUPD) {
+        // pold is read only when the transform is done: bring it into L2 meanwhile (one
+        // prefetch per 128-byte line: four sites)
+        for (int e = 4 * threadIdx.x; e < L * L; e += 4 * kXYThreads)
+            asm volatile("prefetch.global.L2 [%0];\n" ::"l"(A.p + g0 + 4 * (int64_t)e));
+    }
     cp_async_wait<0>();
     __syncthreads();
     if constexpr (DIR < 0) {
@@ -669,10 +678,33 @@ __global__ void __launch_bounds__(kXYThreads, 2) k_fft_xy(FftcArgs A, int Nt) {
     }
     __syncthreads();
     const float sc = 1.0f / (float)L;   // unitary on both axes
-    for (int e = threadIdx.x; e < L * L; e += kXYThreads) {
-        float4 v = sm[(e / L) * RS + e % L];
-        v.x *= sc; v.y *= sc; v.z *= sc; v.w *= sc;
-        *reinterpret_cast<float4*>(A.dst + g0 + 4 * (int64_t)e) = v;
+    if constexpr (PUPD) {
+        const float beta = (float)A.cgs[k].beta;
+        constexpr int XB = 4;   // sites per batch: the batch's loads of pold come before its stores
+        for (int e0 = threadIdx.x; e0 < L * L; e0 += XB * kXYThreads) {
+            float4 po[XB];
+#pragma unroll
+            for (int b = 0; b < XB; ++b) {
+                const int e = e0 + b * kXYThreads;
+                if (e < L * L) po[b] = *reinterpret_cast<const float4*>(A.p + g0 + 4 * (int64_t)e);
+            }
+#pragma unroll
+            for (int b = 0; b < XB; ++b) {
+                const int e = e0 + b * kXYThreads;
+                if (e < L * L) {
+                    const float4 v = sm[(e / L) * RS + e % L];
+                    *reinterpret_cast<float4*>(A.dst + g0 + 4 * (int64_t)e) =
+                        make_float4(v.x * sc + beta * po[b].x, v.y * sc + beta * po[b].y, v.z * sc + beta * po[b].z,
+                                    v.w * sc + beta * po[b].w);
+                }
+            }
+        }
+    } else {
+        for (int e = threadIdx.x; e < L * L; e += kXYThreads) {
+            float4 v = sm[(e / L) * RS + e % L];
+            v.x *= sc; v.y *= sc; v.z *= sc; v.w *= sc;
+            *reinterpret_cast<float4*>(A.dst + g0 + 4 * (int64_t)e) = v;
+        }
     }
 }
 
@@ -728,15 +760,16 @@ int fftc_xy_freq(int L, int pos) {
     return -1;
 }
 
-template <int L, int DIR>
+template <int L, int DIR, bool PUPD>
 static int launch_xy(hmc_ctx* ctx, const FftcArgs& A, int Nt, int nrhs) {
     constexpr size_t sm = xy_smem_bytes<L>();
     static bool attr = false;
     if (!attr) {
-        HMC_CUDA(ctx, cudaFuncSetAttribute(k_fft_xy<L, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        HMC_CUDA(ctx, cudaFuncSetAttribute(k_fft_xy<L, DIR, PUPD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sm));
         attr = true;
     }
-    k_fft_xy<L, DIR><<<dim3((unsigned)(2 * Nt), nrhs), kXYThreads, sm, ctx->stream>>>(A, Nt);
+    k_fft_xy<L, DIR, PUPD><<<dim3((unsigned)(2 * Nt), nrhs), kXYThreads, sm, ctx->stream>>>(A, Nt);
     HMC_LAUNCH(ctx, "k_fft_xy");
     return HMC_OK;
 }
@@ -768,8 +801,28 @@ int fftc_xy_apply(hmc_ctx* ctx, const Lat& lat, const float2* src, float2* dst, 
     A.dst = dst;
     A.cgs = cgs;
     A.tw = pl->tw32;
-#define HMC_CASE(N)                                                                \
-    if (L == N) return dir < 0 ? launch_xy<N, -1>(ctx, A, lat.Nt, nrhs) : launch_xy<N, +1>(ctx, A, lat.Nt, nrhs);
+#define HMC_CASE(N)                                                                            \
+    if (L == N) return dir < 0 ? launch_xy<N, -1, false>(ctx, A, lat.Nt, nrhs)                  \
+                               : launch_xy<N, +1, false>(ctx, A, lat.Nt, nrhs);
+    HMC_FFTXY_SIZES(HMC_CASE)
+#undef HMC_CASE
+    return fail(ctx, HMC_ERR_STATE, "fftc: unsupported length");
+}
+
+int fftc_xy_inverse_pupd(hmc_ctx* ctx, const Lat& lat, const float2* zhat, const float2* pold, float2* pnew, int nrhs,
+                         const CgScalars* cgs) {
+    const int L = lat.L;
+    const FftPlan* pl = get_plan(ctx, L);
+    if (!pl) return fail(ctx, HMC_ERR_STATE, "no FFT plan");
+    if (pold == pnew || !cgs) return fail(ctx, HMC_ERR_ARG, "fftc: bad direction-update buffers");
+    FftcArgs A{};
+    A.src = zhat;
+    A.dst = pnew;
+    A.p = pold;
+    A.cgs = cgs;
+    A.tw = pl->tw32;
+#define HMC_CASE(N) \
+    if (L == N) return launch_xy<N, +1, true>(ctx, A, lat.Nt, nrhs);
     HMC_FFTXY_SIZES(HMC_CASE)
 #undef HMC_CASE
     return fail(ctx, HMC_ERR_STATE, "fftc: unsupported length");

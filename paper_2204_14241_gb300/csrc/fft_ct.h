@@ -30,6 +30,9 @@ int fftc_xy_freq(int L, int pos);
 // right-hand sides with cgs[k].active == 0 are skipped when cgs is given
 int fftc_xy_apply(hmc_ctx* ctx, const Lat& lat, const float2* src, float2* dst, int nrhs, int dir,
                   const CgScalars* cgs);
+// pnew = F_xy^-1 zhat + beta_k pold for every active right-hand side (beta from cgs)
+int fftc_xy_inverse_pupd(hmc_ctx* ctx, const Lat& lat, const float2* zhat, const float2* pold, float2* pnew, int nrhs,
+                         const CgScalars* cgs);
 // x += alpha p, r -= alpha q with partial ||r||^2 (*nblk_out = 2 Nt per right-hand side)
 int fftc_xy_update(hmc_ctx* ctx, const Lat& lat, float2* x, float2* r, const float2* p, const float2* q, int nrhs,
                    const CgScalars* cgs, double* part, int* nblk_out);

@@ -168,6 +168,16 @@ template <typename R>
 int launch_cg_update_precond(hmc_ctx* ctx, const Lat& lat, cplx<R>* x, cplx<R>* r, const cplx<R>* p,
                              const cplx<R>* q, cplx<R>* z, int nrhs, const CgScalars* cgs, double* part_r2,
                              double* part_rz, int* nblk_out, int* nblk_rz_out);
+// complex64 PCG with the fused (x, y) passes (lattices where pcg_xy_path holds). One iteration
+// after q = A p: launch_pcg_xy_forward does x += alpha p, r -= alpha q (partial ||r||^2), zhat
+// = P-hat F~^* r in digit-permuted order (partial <r, z>); after beta, launch_pcg_xy_inverse
+// forms the next direction pnew = F~ zhat + beta pold = z + beta pold.
+bool pcg_xy_path(hmc_ctx* ctx, const Lat& lat);
+int launch_pcg_xy_forward(hmc_ctx* ctx, const Lat& lat, float2* x, float2* r, const float2* p, const float2* q,
+                          float2* zhat, int nrhs, const CgScalars* cgs, double* part_r2, double* part_rz,
+                          int* nblk_r2, int* nblk_rz);
+int launch_pcg_xy_inverse(hmc_ctx* ctx, const Lat& lat, const float2* zhat, const float2* pold, float2* pnew,
+                          int nrhs, const CgScalars* cgs);
 int metric_op(hmc_ctx* ctx, const Lat& lat, int op, const double* sig, const double* in,
               double* out, double eps, double* scalar_dev);
 

@@ -313,7 +313,9 @@ template <int TX, int TY>
 __global__ void __launch_bounds__(kAThreads, 2) k_apply_A4(Lat lat, Coef<float> cf, ATile tl,
                                                            const float* __restrict__ phi,
                                                            const Site<float>* __restrict__ x,
-                                                           Site<float>* __restrict__ y, double* __restrict__ part) {
+                                                           Site<float>* __restrict__ y, double* __restrict__ part,
+                                                           const CgScalars* __restrict__ cgs) {
+    if (cgs && !cgs[blockIdx.z].active) return;
     using S = A4Shape<TX, TY>;
     constexpr int HX2 = S::HX2, N2 = S::N2, HX1 = S::HX1, N1 = S::N1, NI = S::NI;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -537,8 +539,9 @@ static void go_apply_A(hmc_ctx* ctx, const Lat& lat, const ATile& tl, int nrhs, 
         return;
     }
     if constexpr (sizeof(R) == 4) {
-        if (!cgs && tl.TX == 16 && tl.TY == 16) {
-            k_apply_A4<16, 16><<<grid, kAThreads, A4Shape<16, 16>::smem, ctx->stream>>>(lat, cf, tl, phi, x, y, part);
+        if (tl.TX == 16 && tl.TY == 16) {
+            k_apply_A4<16, 16><<<grid, kAThreads, A4Shape<16, 16>::smem, ctx->stream>>>(lat, cf, tl, phi, x, y, part,
+                                                                                        cgs);
             return;
         }
     }
