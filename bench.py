@@ -41,7 +41,7 @@ WORKLOAD = (f"L={L}x{L}, Nt={NT} (dtau=0.1), 2 bands x 2 spins, {NRHS} pseudofer
 # DRAM bytes (read + write) of one launch of the roofline kernel, the plain fused A on 8 RHS at
 # 80x80x160, from ncu (profiles/ncu_apply_A_plain_80x80x160_8rhs.md); set to None when that
 # kernel changes until it is captured again.
-ROOFLINE_TRAFFIC_BYTES = 550_735_872
+ROOFLINE_TRAFFIC_BYTES = 550_630_144
 # PCG iterations per solve of this workload on a GB300, used only to scale the oracle's timed
 # sample (a few PCG iterations) to a trajectory when no GPU run is available in the process.
 ITERS_PER_SOLVE_DEFAULT = 57
