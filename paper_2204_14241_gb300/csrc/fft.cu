@@ -354,6 +354,12 @@ static int add_pc(hmc_ctx* ctx, int L, int Nt) {
     HMC_CUDA(ctx, cudaMemcpy(t.cosk32, ck32.data(), L * sizeof(float), cudaMemcpyHostToDevice));
     HMC_CUDA(ctx, cudaMemcpy(t.eitw32, ew32.data(), Nt * sizeof(float2), cudaMemcpyHostToDevice));
     HMC_CUDA(ctx, cudaMemcpy(t.twist32, tw32.data(), Nt * sizeof(float2), cudaMemcpyHostToDevice));
+    if (fftc_tau_supported(Nt)) {
+        std::vector<float2> ewp(Nt);
+        for (int m = 0; m < Nt; ++m) ewp[m] = ew32[fftc_tau_freq(Nt, m)];
+        HMC_CUDA(ctx, cudaMalloc(&t.eitw32_tau, Nt * sizeof(float2)));
+        HMC_CUDA(ctx, cudaMemcpy(t.eitw32_tau, ewp.data(), Nt * sizeof(float2), cudaMemcpyHostToDevice));
+    }
     if (fftc_xy_supported(L)) {
         std::vector<float> ckxy(L);
         for (int m = 0; m < L; ++m) ckxy[m] = (float)std::cos(2.0 * M_PI * fftc_xy_freq(L, m) / L);
@@ -388,6 +394,7 @@ void free_plans(hmc_ctx* ctx) {
         cudaFree(t.eitw32);
         cudaFree(t.twist32);
         cudaFree(t.cosk32_xy);
+        cudaFree(t.eitw32_tau);
     }
     ctx->pcs.clear();
 }

@@ -491,6 +491,151 @@ int fftc_axis(hmc_ctx* ctx, float2* data, int64_t outer, int n, int64_t inner, i
     return fail(ctx, HMC_ERR_STATE, "fftc: unsupported length");
 }
 
+// ---- tau pass in place ------------------------------------------------------------------------
+// The preconditioner's tau pass (twist, FFT along tau, P-hat, inverse FFT, twist) for 16
+// consecutive inner indices (4 sites x 4 components) of one right-hand side, all N slices in
+// one shared buffer [N][16]. The FFT is the same in-place two-factor split as the (x, y) pass,
+// N = N1 * N2: the spectrum between the forward and inverse steps is in digit-permuted order
+// (position N1 k2 + k1 holds frequency k2 + N2 k1) and P-hat reads e^{i w_n} in that order. The
+// forward twist is applied as step A reads its points, the inverse twist as the result is stored.
+template <int N> struct TauSplit { static constexpr int N1 = 0, N2 = 0; };
+template <> struct TauSplit<4> { static constexpr int N1 = 2, N2 = 2; };
+template <> struct TauSplit<6> { static constexpr int N1 = 3, N2 = 2; };
+template <> struct TauSplit<8> { static constexpr int N1 = 4, N2 = 2; };
+template <> struct TauSplit<12> { static constexpr int N1 = 4, N2 = 3; };
+template <> struct TauSplit<16> { static constexpr int N1 = 4, N2 = 4; };
+template <> struct TauSplit<20> { static constexpr int N1 = 5, N2 = 4; };
+template <> struct TauSplit<24> { static constexpr int N1 = 6, N2 = 4; };
+template <> struct TauSplit<32> { static constexpr int N1 = 8, N2 = 4; };
+template <> struct TauSplit<40> { static constexpr int N1 = 8, N2 = 5; };
+template <> struct TauSplit<48> { static constexpr int N1 = 8, N2 = 6; };
+template <> struct TauSplit<64> { static constexpr int N1 = 8, N2 = 8; };
+template <> struct TauSplit<80> { static constexpr int N1 = 10, N2 = 8; };
+template <> struct TauSplit<160> { static constexpr int N1 = 16, N2 = 10; };
+#define HMC_TAU2_SIZES(X) X(4) X(6) X(8) X(12) X(16) X(20) X(24) X(32) X(40) X(48) X(64) X(80) X(160)
+
+constexpr int kTauLines = 16, kTauThreads = 256;
+
+// In-place DFTs of size R for every (line, f) task over the positions f + N1 m (STEP_A) or
+// N1 f + m; TW multiplies output m by w_N^{DIR f m}; TWIST multiplies input point pos by
+// conj(e^{i pi pos / N}) before the transform.
+template <int N, bool STEP_A, bool TW, bool TWIST, int DIR>
+__device__ __forceinline__ void tau_step(float2* sm, const float2* tw, const float2* twist) {
+    constexpr int N1 = TauSplit<N>::N1, N2 = TauSplit<N>::N2;
+    constexpr int R = STEP_A ? N2 : N1;
+    constexpr int NF = STEP_A ? N1 : N2;
+    constexpr int total = kTauLines * NF;
+#pragma unroll 1
+    for (int task = threadIdx.x; task < total; task += kTauThreads) {
+        const int line = task % kTauLines, f = task / kTauLines;
+        float2* base = sm + (STEP_A ? f : N1 * f) * kTauLines + line;
+        constexpr int S = (STEP_A ? N1 : 1) * kTauLines;
+        float2 v[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) {
+            v[m] = base[m * S];
+            if constexpr (TWIST) {
+                const float2 w = twist[STEP_A ? f + N1 * m : N1 * f + m];
+                v[m] = make_float2(v[m].x * w.x + v[m].y * w.y, v[m].y * w.x - v[m].x * w.y);
+            }
+        }
+        bfly<R, DIR>(v);
+        if constexpr (TW) {
+#pragma unroll
+            for (int m = 1; m < R; ++m) {
+                float2 w = tw[f * m];   // f * m < N
+                if (DIR > 0) w.y = -w.y;
+                v[m] = make_float2(v[m].x * w.x - v[m].y * w.y, v[m].x * w.y + v[m].y * w.x);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < R; ++m) base[m * S] = v[m];
+    }
+}
+
+// y [nrhs][N][inner] in place; grid nrhs * (inner / 16). A.eitw holds e^{i w_n} in the
+// digit-permuted order of the split; A.cosk the cos k table in the order of the x and y
+// positions. A.part (optional): per block sum P-hat |y-hat|^2 / N (= <y_in, P y_in> when y_in is
+// the unitary (x, y) transform of a vector).
+// Six blocks per SM (40 registers): the pass waits on its cp.async loads and barriers, and more
+// resident blocks measured faster than fewer blocks without spills.
+template <int N>
+__global__ void __launch_bounds__(kTauThreads, 6) k_tau(FftcArgs A) {
+    __shared__ __align__(16) float2 sm[N * kTauLines];
+    __shared__ float2 s_tw[N], s_twist[N], s_ew[N];
+    __shared__ double red[kTauThreads / 32];
+    const int nib = (int)A.nib;
+    const int k = blockIdx.x / nib;
+    const int64_t i0 = (int64_t)(blockIdx.x % nib) * kTauLines;
+    if (A.cgs && !A.cgs[k].active) return;
+    float2* y = A.dst + (int64_t)k * N * A.inner + i0;
+    // 16-byte chunks: row t = c / 8, column pair c % 8
+    for (int c = threadIdx.x; c < N * kTauLines / 2; c += kTauThreads)
+        cp_async16(sm + 2 * c, y + (int64_t)(c >> 3) * A.inner + 2 * (c & 7));
+    cp_async_commit();
+    for (int i = threadIdx.x; i < N; i += kTauThreads) {
+        s_tw[i] = __ldg(A.tw + i);
+        s_twist[i] = __ldg(A.twist + i);
+        s_ew[i] = __ldg(A.eitw + i);
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    tau_step<N, true, true, true, -1>(sm, s_tw, s_twist);
+    __syncthreads();
+    tau_step<N, false, false, false, -1>(sm, s_tw, s_twist);
+    __syncthreads();
+    // P-hat = 1 / |K-hat|^2; the momentum part depends only on the line
+    float acc = 0.f;
+    {
+        const int line = threadIdx.x % kTauLines;
+        const int64_t i = i0 + line;
+        const int ab = (int)((i & 3) >> 1);
+        const int kk = (int)(i >> 2);
+        const float base = A.c0[ab] + A.chx[ab] * __ldg(A.cosk + kk % A.L) + A.chy[ab] * __ldg(A.cosk + kk / A.L);
+        for (int p = threadIdx.x / kTauLines; p < N; p += kTauThreads / kTauLines) {
+            const float re = s_ew[p].x + base;
+            const float ph = 1.0f / (re * re + s_ew[p].y * s_ew[p].y);
+            float2 v = sm[p * kTauLines + line];
+            acc += ph * (v.x * v.x + v.y * v.y);
+            sm[p * kTauLines + line] = make_float2(v.x * ph, v.y * ph);
+        }
+    }
+    __syncthreads();
+    tau_step<N, false, true, false, +1>(sm, s_tw, s_twist);
+    __syncthreads();
+    tau_step<N, true, false, false, +1>(sm, s_tw, s_twist);
+    __syncthreads();
+    const float sc = A.scale;
+    const float4* s4 = reinterpret_cast<const float4*>(sm);
+    for (int c = threadIdx.x; c < N * kTauLines / 2; c += kTauThreads) {
+        const int t = c >> 3;
+        const float2 w = s_twist[t];
+        const float4 v = s4[c];
+        *reinterpret_cast<float4*>(y + (int64_t)t * A.inner + 2 * (c & 7)) =
+            make_float4(sc * (v.x * w.x - v.y * w.y), sc * (v.x * w.y + v.y * w.x), sc * (v.z * w.x - v.w * w.y),
+                        sc * (v.z * w.y + v.w * w.x));
+    }
+    if (A.part) {
+        const double tot = block_sum((double)acc, red);
+        if (threadIdx.x == 0) A.part[blockIdx.x] = tot / N;   // block = k * nib + inner block
+    }
+}
+
+bool fftc_tau_supported(int n) {
+#define HMC_CASE(N) if (n == N) return true;
+    HMC_TAU2_SIZES(HMC_CASE)
+#undef HMC_CASE
+    return false;
+}
+
+int fftc_tau_freq(int n, int pos) {
+#define HMC_CASE(N) \
+    if (n == N) return pos / TauSplit<N>::N1 + TauSplit<N>::N2 * (pos % TauSplit<N>::N1);
+    HMC_TAU2_SIZES(HMC_CASE)
+#undef HMC_CASE
+    return -1;
+}
+
 int fftc_precond_tau(hmc_ctx* ctx, const Lat& lat, float2* y, int nrhs, const CgScalars* cgs,
                      const PcTables* pt, const float* cosk, double* part, int* nblk_out) {
     const int n = lat.Nt;
@@ -515,6 +660,25 @@ int fftc_precond_tau(hmc_ctx* ctx, const Lat& lat, float2* y, int nrhs, const Cg
     A.cosk = cosk;
     A.eitw = pt->eitw32;
     A.twist = pt->twist32;
+    if (pt->eitw32_tau && A.inner % kTauLines == 0) {
+        A.eitw = pt->eitw32_tau;
+        A.dst = y;
+        A.nib = A.inner / kTauLines;
+        A.part = part;
+        if (part) {
+            if (A.nib * nrhs > ctx->part_cap / 2) return fail(ctx, HMC_ERR_ARG, "fftc: reduction buffer too small");
+            *nblk_out = (int)A.nib;
+        }
+        const dim3 grid((unsigned)(nrhs * A.nib));
+#define HMC_CASE(N)                                                 \
+        if (n == N) {                                               \
+            k_tau<N><<<grid, kTauThreads, 0, ctx->stream>>>(A);     \
+            HMC_LAUNCH(ctx, "k_tau");                               \
+            return HMC_OK;                                          \
+        }
+        HMC_TAU2_SIZES(HMC_CASE)
+#undef HMC_CASE
+    }
     if (A.inner < NL) return fail(ctx, HMC_ERR_STATE, "fftc: unsupported tile");
     A.nib = (A.inner + NL - 1) / NL;
     A.part = part;

@@ -22,6 +22,10 @@ int fftc_precond_tau(hmc_ctx* ctx, const Lat& lat, float2* y, int nrhs, const Cg
 int fftc_x_cg(hmc_ctx* ctx, const Lat& lat, int mode, const float2* src, float2* dst, float2* x, float2* r,
               const float2* p, const float2* q, int nrhs, const CgScalars* cgs, double* part, int* nblk_out);
 
+// in-place tau pass for these lengths (spectrum in digit-permuted order inside the kernel)
+bool fftc_tau_supported(int n);
+// frequency index held at position pos after the forward steps of that pass
+int fftc_tau_freq(int n, int pos);
 // (x, y) passes in one kernel per band and plane, for lattice extents with a compiled split
 bool fftc_xy_supported(int L);
 // frequency index held at position pos of an axis after the forward (x, y) pass

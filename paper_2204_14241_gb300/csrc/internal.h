@@ -26,6 +26,7 @@ struct PcTables {
     float2* eitw32 = nullptr;
     float2* twist32 = nullptr;
     float* cosk32_xy = nullptr; // cos(2 pi k(m) / L), k(m) the frequency at position m after the (x, y) pass
+    float2* eitw32_tau = nullptr;   // e^{i w_n(p)}, n(p) the frequency at position p inside the in-place tau pass
 };
 
 // Tile shape chosen for the fused A kernel per (L, Nt, nrhs, precision).
