@@ -227,6 +227,18 @@ __global__ void k_phi_to32(const double* __restrict__ a, float* __restrict__ b, 
 }
 
 // ---- host driver ---------------------------------------------------------------------------
+// FP64 y = A x for the start residual and the reliable updates, as two passes through
+// ctx->d_z64 (t_ = D^dagger x, then y = D t_). GB300's FP64 pipe bounds this operator; the fused
+// kernel recomputes t_ on a one-site ring around each tile (about 2.4 site operations per output
+// site against 2.0 here), and the extra 128 B per RHS-site of traffic hides under the FP64 work:
+// 2.55 ms against 3.33 ms at 80x80x160 with 8 RHS. d_z64 is dead whenever this runs: the next
+// direction restart recomputes z.
+static int apply_A64(hmc_ctx* ctx, const Lat& lat, const double* phi, const double2* x, double2* y, int nrhs) {
+    int rc;
+    if ((rc = launch_apply_D<double>(ctx, lat, phi, x, ctx->d_z64, 1, nrhs))) return rc;
+    return launch_apply_D<double>(ctx, lat, phi, ctx->d_z64, y, 0, nrhs);
+}
+
 template <typename R>
 static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2* b, double2* x,
                int nrhs, double tol, int maxit, int precond, hmc_cg_stats* st, bool use_x0) {
@@ -262,8 +274,7 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
         k_dot<double><<<vgrid, 256, 0, sm>>>(reinterpret_cast<const double2*>(b), reinterpret_cast<const double2*>(b),
                                              n, part2, nullptr);
         HMC_LAUNCH(ctx, "k_dot");
-        int nb0 = 0;
-        if ((rc = launch_apply_A<double>(ctx, lat, phi64, x, ctx->d_q64, nrhs, nullptr, &nb0))) return rc;
+        if ((rc = apply_A64(ctx, lat, phi64, x, ctx->d_q64, nrhs))) return rc;
         k_residual<<<vgrid, 256, 0, sm>>>(b, ctx->d_q64, ctx->d_r64, kMixed ? ctx->d_r32 : nullptr, n, part, nullptr);
         HMC_LAUNCH(ctx, "k_residual");
         k_cg_start<<<nrhs, 256, 0, sm>>>(cgs, part2, part, kRedBlocks, tol2);
@@ -317,8 +328,7 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
             k_accum_x<<<vgrid, 256, 0, sm>>>(x, ctx->d_x32, n, cgs);
             HMC_LAUNCH(ctx, "k_accum_x");
         }
-        int nb = 0;
-        if ((rc = launch_apply_A<double>(ctx, lat, phi64, x, ctx->d_q64, nrhs, nullptr, &nb, cgs))) return rc;
+        if ((rc = apply_A64(ctx, lat, phi64, x, ctx->d_q64, nrhs))) return rc;
         k_residual<<<vgrid, 256, 0, sm>>>(b, ctx->d_q64, ctx->d_r64, kMixed ? ctx->d_r32 : nullptr, n, part, cgs);
         HMC_LAUNCH(ctx, "k_residual");
         k_ru_finish<<<nrhs, 256, 0, sm>>>(cgs, part, kRedBlocks, tol2);

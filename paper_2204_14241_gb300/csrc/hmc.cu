@@ -233,7 +233,7 @@ int hmc_init(const hmc_params* p, int n_chains, const hmc_chain* chains, void* c
     const bool mixed = p->solver_mode == HMC_SOLVER_MIXED;
     if ((rc = dalloc(ctx, &ctx->d_r64, nf)) || (rc = dalloc(ctx, &ctx->d_p64, mixed ? 1 : nf)) ||
         (rc = dalloc(ctx, &ctx->d_p64b, mixed ? 1 : nf)) || (rc = dalloc(ctx, &ctx->d_p32b, mixed ? nf : 1)) ||
-        (rc = dalloc(ctx, &ctx->d_q64, nf)) || (rc = dalloc(ctx, &ctx->d_z64, mixed ? 1 : nf)) ||
+        (rc = dalloc(ctx, &ctx->d_q64, nf)) || (rc = dalloc(ctx, &ctx->d_z64, nf)) ||
         (rc = dalloc(ctx, &ctx->d_X, nf)) || (rc = dalloc(ctx, &ctx->d_Xprev, p->initial_guess ? nf : 1)) || (rc = dalloc(ctx, &ctx->d_pf, nf)) ||
         (rc = dalloc(ctx, &ctx->d_chi, nf)) || (rc = dalloc(ctx, &ctx->d_x32, mixed ? nf : 1)) ||
         (rc = dalloc(ctx, &ctx->d_r32, mixed ? nf : 1)) || (rc = dalloc(ctx, &ctx->d_p32, mixed ? nf : 1)) ||

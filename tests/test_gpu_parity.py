@@ -124,10 +124,11 @@ def test_preconditioner(L, Nt, prec):
         assert rel(ys[k], solver.apply_precond(P, xs[k])) < tol
 
 
-@pytest.mark.parametrize("L,Nt", [(16, 8), (24, 6), (40, 4), (80, 4)])
+@pytest.mark.parametrize("L,Nt", [(16, 8), (24, 6), (40, 4), (80, 4), (20, 160), (12, 80), (16, 48)])
 def test_preconditioner_fp32_xy_pass(L, Nt):
     # complex64, L with a compiled (x, y) split: one kernel per band and plane does both axes,
-    # leaving the spectrum in digit-permuted order for the tau pass (the same kernels as PCG)
+    # leaving the spectrum in digit-permuted order for the in-place tau pass (the same kernels
+    # as PCG; N_tau = 160, 80, 48 exercise the tau splits 16 x 10, 10 x 8, 8 x 6)
     ctx = ctx_for(L, Nt)
     P = oparams(L, Nt)
     x = dev(I.fermion_noise(50 + L, 2, L, Nt), torch.complex64)
