@@ -28,7 +28,7 @@ if ROOT not in sys.path:
 
 METRIC = "HMC traj/s and M†M matvec GB/s at 80×80; mixed vs FP64 at equal CG residual"
 L, NT, NRHS, NLEAP, EPS, TOL, MAXIT = 80, 160, 8, 40, 0.01, 1e-10, 20000
-GUESS = 1   # force solves start from the extrapolated previous solutions (same stopping test)
+GUESS = 4   # force solves start from the degree-4 extrapolation of the previous solutions (same stopping test)
 # Yukawa coupling lambda = 1 in the paper's convention g / sqrt(N_f): with k pseudofermion fields
 # (N_f = 2k) the on-site coefficient of D is lambda * sqrt(2 / N_f) = lambda / sqrt(k)
 LAMBDA = 1.0
@@ -37,14 +37,15 @@ COUPLINGS = dict(dtau=0.1, t_h=(1.0, 0.5), t_v=(0.5, 1.0), mu=(-0.5, -0.5), g=LA
 WORKLOAD = (f"L={L}x{L}, Nt={NT} (dtau=0.1), 2 bands x 2 spins, {NRHS} pseudofermion RHS (N_f={2 * NRHS}, "
             f"Yukawa lambda={LAMBDA} as g/sqrt(N_f): D coefficient {LAMBDA / NRHS ** 0.5:.4f}), n_leap={NLEAP}, "
             f"eps={EPS}, complex64 PCG with FP64 reliable updates to true residual {TOL}, "
-            "chronological initial guess, phi = free-boson-spectrum Gaussian field, sigma-hat = its spectrum")
+            "degree-4 chronological initial guess, phi = free-boson-spectrum Gaussian field, sigma-hat = its spectrum")
 # DRAM bytes (read + write) of one launch of the roofline kernel, the plain fused A on 8 RHS at
 # 80x80x160, from ncu (profiles/ncu_apply_A_plain_80x80x160_8rhs.md); set to None when that
 # kernel changes until it is captured again.
 ROOFLINE_TRAFFIC_BYTES = 550_630_144
-# PCG iterations per solve of this workload on a GB300, used only to scale the oracle's timed
-# sample (a few PCG iterations) to a trajectory when no GPU run is available in the process.
-ITERS_PER_SOLVE_DEFAULT = 57
+# PCG iterations per solve of this workload with the degree-4 chronological start (20.3 measured
+# on a GB300), used only to scale the oracle's timed sample (a few PCG iterations) to a
+# trajectory when no GPU run is available in the process.
+ITERS_PER_SOLVE_DEFAULT = 21
 
 
 def kt():

@@ -73,9 +73,13 @@ typedef struct {
     int nrhs_max;       /* most pseudofermion right-hand sides per call, >= 1 */
     double cg_tol;      /* default relative true-residual tolerance ||b - A x|| / ||b|| */
     int cg_maxit;       /* default iteration cap */
-    int initial_guess;  /* trajectory() force solves: 0 = zero start (default); 1 = chronological
-                           start from the linear extrapolation 2 X_n - X_{n-1} of the trajectory's
-                           previous two solutions (the same stopping test applies either way) */
+    int initial_guess;  /* trajectory() force solves: 0 = zero start (default); m = 1 .. 5 =
+                           chronological start from the polynomial extrapolation of degree m
+                           through the trajectory's previous m + 1 solutions (m = 1:
+                           2 X_n - X_{n-1}; 2: 3 X_n - 3 X_{n-1} + X_{n-2}; 3: 4 X_n - 6 X_{n-1}
+                           + 4 X_{n-2} - X_{n-3}; ...; lower degree while fewer solutions exist),
+                           m FP64 vectors of workspace. The same stopping test applies in every
+                           case. */
     int autotune;       /* 0: tile shapes of the fused A kernel from a fixed rule (default; the
                            reduction order, hence every bit of the results, is reproducible);
                            1: on first use per (L, Nt, nrhs, precision) time the valid tile and

@@ -1,3 +1,4 @@
+#include <algorithm>
 // Context management, the C ABI of include/hmc.h, the HMC trajectory (Section "HMC":
 // heatbath, momentum draw, leapfrog, Metropolis) and the Philox4x32-10 generator.
 #include <cmath>
@@ -104,13 +105,28 @@ __global__ void k_axpy(double a, const double* __restrict__ x, double* __restric
     if (i < n) y[i] += a * x[i];
 }
 
-// b = 2 a - b (linear extrapolation of two solutions)
-__global__ void k_extrap(const double2* __restrict__ a, double2* __restrict__ b, int64_t n) {
+// The previous solutions of a trajectory's force solves, newest first.
+constexpr int kMaxGuess = 5;   // highest extrapolation degree
+struct SolHist {
+    const double2* h[kMaxGuess + 1];
+};
+
+// out = sum_j c_j h_j, the polynomial extrapolation through np equally spaced solutions h_0
+// (newest) .. h_{np-1}: c_j = (-1)^j binomial(np, j + 1) (1; 2, -1; 3, -3, 1; 4, -6, 4, -1; ...).
+// out may be one of the h_j.
+__global__ void k_extrap(SolHist hs, double2* out, int np, int64_t n) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) {
-        const double2 u = a[i], v = b[i];
-        b[i] = make_double2(2.0 * u.x - v.x, 2.0 * u.y - v.y);
+    if (i >= n) return;
+    double2 s = make_double2(0.0, 0.0);
+    double c = (double)np, sign = 1.0;   // binomial(np, j + 1), starting at j = 0
+    for (int j = 0; j < np; ++j) {
+        const double2 v = hs.h[j][i];
+        s.x += sign * c * v.x;
+        s.y += sign * c * v.y;
+        c = c * (double)(np - j - 1) / (double)(j + 2);
+        sign = -sign;
     }
+    out[i] = s;
 }
 
 __global__ void __launch_bounds__(256) k_norm2(const double* __restrict__ a, int64_t n, double* __restrict__ part) {
@@ -153,8 +169,21 @@ template <typename T> static int dalloc(hmc_ctx* ctx, T** p, int64_t count) {
     return HMC_OK;
 }
 
+// m FP64 solution buffers for a degree-m chronological start
+static int alloc_hist(hmc_ctx* ctx, int m, int64_t nf) {
+    for (int j = 0; j < m; ++j) {
+        int rc;
+        if ((rc = dalloc(ctx, &ctx->d_Xhist[j], nf))) return rc;
+    }
+    return HMC_OK;
+}
+
 static void free_all(hmc_ctx* ctx) {
-    void* ps[] = {ctx->d_r64, ctx->d_p64, ctx->d_p64b, ctx->d_p32b, ctx->d_q64, ctx->d_z64, ctx->d_X, ctx->d_Xprev, ctx->d_pf, ctx->d_chi,
+    for (double2*& b : ctx->d_Xhist) {
+        cudaFree(b);
+        b = nullptr;
+    }
+    void* ps[] = {ctx->d_r64, ctx->d_p64, ctx->d_p64b, ctx->d_p32b, ctx->d_q64, ctx->d_z64, ctx->d_X, ctx->d_pf, ctx->d_chi,
                   ctx->d_x32, ctx->d_r32, ctx->d_p32, ctx->d_q32, ctx->d_z32, ctx->d_phi32,
                   ctx->d_phi_save, ctx->d_pi, ctx->d_F, ctx->d_vel, ctx->d_z, ctx->d_fft,
                   ctx->d_part, ctx->d_red, ctx->d_cg, ctx->d_u32};
@@ -191,6 +220,8 @@ int hmc_init(const hmc_params* p, int n_chains, const hmc_chain* chains, void* c
     if (p->solver_mode != HMC_SOLVER_FP64 && p->solver_mode != HMC_SOLVER_MIXED)
         return fail(nullptr, HMC_ERR_ARG, "hmc_init: unknown solver_mode");
     if (!(p->dtau > 0.0) || !(p->c > 0.0)) return fail(nullptr, HMC_ERR_ARG, "hmc_init: dtau and c must be positive");
+    if (p->initial_guess < 0 || p->initial_guess > kMaxGuess)
+        return fail(nullptr, HMC_ERR_ARG, "hmc_init: initial_guess must be in [0, 5]");
     hmc_ctx* ctx = new (std::nothrow) hmc_ctx();
     if (!ctx) return fail(nullptr, HMC_ERR_ARG, "hmc_init: out of host memory");
     ctx->p = *p;
@@ -234,7 +265,7 @@ int hmc_init(const hmc_params* p, int n_chains, const hmc_chain* chains, void* c
     if ((rc = dalloc(ctx, &ctx->d_r64, nf)) || (rc = dalloc(ctx, &ctx->d_p64, mixed ? 1 : nf)) ||
         (rc = dalloc(ctx, &ctx->d_p64b, mixed ? 1 : nf)) || (rc = dalloc(ctx, &ctx->d_p32b, mixed ? nf : 1)) ||
         (rc = dalloc(ctx, &ctx->d_q64, nf)) || (rc = dalloc(ctx, &ctx->d_z64, nf)) ||
-        (rc = dalloc(ctx, &ctx->d_X, nf)) || (rc = dalloc(ctx, &ctx->d_Xprev, p->initial_guess ? nf : 1)) || (rc = dalloc(ctx, &ctx->d_pf, nf)) ||
+        (rc = dalloc(ctx, &ctx->d_X, nf)) || (rc = alloc_hist(ctx, p->initial_guess, nf)) || (rc = dalloc(ctx, &ctx->d_pf, nf)) ||
         (rc = dalloc(ctx, &ctx->d_chi, nf)) || (rc = dalloc(ctx, &ctx->d_x32, mixed ? nf : 1)) ||
         (rc = dalloc(ctx, &ctx->d_r32, mixed ? nf : 1)) || (rc = dalloc(ctx, &ctx->d_p32, mixed ? nf : 1)) ||
         (rc = dalloc(ctx, &ctx->d_q32, mixed ? nf : 1)) || (rc = dalloc(ctx, &ctx->d_z32, mixed ? nf : 1)) ||
@@ -473,24 +504,32 @@ static int run_chain(hmc_ctx* ctx, int c, const hmc_traj_in* in, double out_e[6]
     int tot_it = 0;
     double wr = 0.0, s_pf = 0.0, s_b = 0.0;
     hmc_cg_stats st;
-    // solution buffers: xa holds the latest solution, xb the one before (initial guesses)
-    double2 *xa = ctx->d_X, *xb = ctx->initial_guess_buf();
+    // solution history (initial guesses): hist[0] the latest solution, hist[1] the one before, ...; the
+    // start of the next solve is the extrapolation through the last min(nsol, mode + 1) of them,
+    // built in a free buffer or in place of the oldest
+    const int mode = ctx->p.initial_guess;
+    double2* hist[kMaxGuess + 1] = {ctx->d_X};
+    for (int j = 1; j <= mode; ++j) hist[j] = ctx->d_Xhist[j - 1];
     int nsol = 0;
     const int64_t nfv = (int64_t)K * 4 * lat.V;
+    const unsigned gx = (unsigned)((nfv + 255) / 256);
     auto do_force = [&](bool want) -> int {
-        const bool guess = ctx->p.initial_guess && nsol >= 1;
-        double2* xo = guess ? xb : xa;
+        const bool guess = mode && nsol >= 1;
+        const int np = guess ? std::min(nsol, mode + 1) : 0;
+        const int io = np < mode + 1 ? np : mode;   // free slot, or the oldest solution
+        double2* xo = !guess ? hist[0] : hist[io];
         if (guess) {
-            if (nsol >= 2) {
-                k_extrap<<<(unsigned)((nfv + 255) / 256), 256, 0, sm>>>(xa, xb, nfv);
-                HMC_LAUNCH(ctx, "k_extrap");
-            } else {
-                HMC_CUDA(ctx, cudaMemcpyAsync(xb, xa, nfv * sizeof(double2), cudaMemcpyDeviceToDevice, sm));
-            }
+            SolHist hs{};
+            for (int j = 0; j < np; ++j) hs.h[j] = hist[j];
+            k_extrap<<<gx, 256, 0, sm>>>(hs, xo, np, nfv);
+            HMC_LAUNCH(ctx, "k_extrap");
         }
         int r2 = force_impl(ctx, c, phi, ctx->d_pf, K, ctx->d_F, 1, in->precond, want ? &s_pf : nullptr,
                             want ? &s_b : nullptr, &st, xo, guess);
-        if (guess) { xb = xa; xa = xo; }
+        if (guess) {
+            for (int j = io; j > 0; --j) hist[j] = hist[j - 1];   // buffers past io keep their place
+            hist[0] = xo;
+        }
         ++nsol;
         tot_it += st.iterations;
         if (st.true_rel_resid > wr) wr = st.true_rel_resid;

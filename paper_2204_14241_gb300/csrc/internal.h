@@ -81,7 +81,7 @@ struct hmc_ctx {
     double2* d_q64 = nullptr;
     double2* d_z64 = nullptr;
     double2* d_X = nullptr;       // solve output used by force
-    double2* d_Xprev = nullptr;   // previous solution (chronological initial guess)
+    double2* d_Xhist[5] = {};     // earlier solutions of a trajectory (chronological initial guess)
     double2* d_pf = nullptr;      // pseudofermion fields of a trajectory
     double2* d_chi = nullptr;     // heatbath noise (Philox mode)
     float2* d_x32 = nullptr;
@@ -109,7 +109,6 @@ struct hmc_ctx {
     double* h_red = nullptr;          // pinned, 64 doubles
     uint32_t* d_u32 = nullptr;        // 4 words scratch for uniforms
 
-    double2* initial_guess_buf() { return p.initial_guess ? d_Xprev : d_X; }
 };
 
 namespace hmc {

@@ -221,11 +221,11 @@ def test_boson_action_and_force_parity():
     assert rel(I.to_paper_boson(F.cpu().numpy()), -boson.grad(P, phi_o)) < 1e-12
 
 
-@pytest.mark.parametrize("mode,guess", [("fp64", 0), ("mixed", 0), ("mixed", 1)])
+@pytest.mark.parametrize("mode,guess", [("fp64", 0), ("mixed", 0), ("mixed", 1), ("mixed", 2), ("mixed", 3), ("mixed", 5)])
 @pytest.mark.parametrize("nrhs", [1, 2])
 def test_trajectory_matches_oracle(mode, guess, nrhs):
-    # the small configuration: L = 4, Nt = 8, dtau = 0.1, eps = 0.05, n_leap = 10; guess = 1 starts
-    # each force solve from the extrapolated previous solutions (same stopping test)
+    # the small configuration: L = 4, Nt = 8, dtau = 0.1, eps = 0.05, n_leap = 10; guess = m starts
+    # each force solve from the degree-m extrapolation of the previous solutions (same stopping test)
     L, Nt, eps, n_leap = 4, 8, 0.05, 10
     ctx = ctx_for(L, Nt, mode, nrhs=nrhs, tol=1e-12, guess=guess)
     P = oparams(L, Nt)
