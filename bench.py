@@ -375,6 +375,32 @@ def run_profile_solve(args):
     ctx.close()
 
 
+def run_profile_trajectory(args):
+    """One benchmark trajectory for an ncu launch list: the workload of the default mode (inputs,
+    coupling, eps, n_leap, chronological start), one warm-up trajectory, then one inside the NVTX
+    range "trajectory" (capture it with ncu --nvtx --nvtx-include "trajectory/")."""
+    import torch
+    from paper_2204_14241_gb300.hmc import Context
+    phi_np, sig_np = synthetic_inputs(chain_seed(args.seed, 0))
+    phi = torch.from_numpy(phi_np).cuda()
+    sig = torch.from_numpy(sig_np).cuda()
+    ctx = Context(L, NT, solver="mixed", nrhs_max=NRHS, cg_tol=TOL, cg_maxit=MAXIT, initial_guess=GUESS, **COUPLINGS)
+    for rep in range(2):
+        if rep == 1:
+            torch.cuda.nvtx.range_push("trajectory")
+        n0 = ctx.launches()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        o = ctx.trajectory([phi], [sig], EPS, NLEAP, nrhs=NRHS, precond=True, seed=args.seed, counter=rep, check=False)
+        torch.cuda.synchronize()
+        if rep == 1:
+            torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile_trajectory": rep, "seconds": time.perf_counter() - t0,
+                          "launches": ctx.launches() - n0, "cg_iterations": o["cg_iterations"][0],
+                          "dH": o["dH"][0]}))
+    ctx.close()
+
+
 def run_profile_matvec(args):
     """Only the dominant kernel: N launches of the fused A = D D^dagger (complex64, NRHS) on the
     benchmark's lattice, for an ncu capture of the last one."""
@@ -403,10 +429,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-solve", type=int, default=0,
                     help="run only a capture-sized sample: one solve cut at this many iterations")
+    ap.add_argument("--profile-trajectory", action="store_true",
+                    help="run only two trajectories of the workload, the second inside an NVTX range")
     ap.add_argument("--profile-matvec", type=int, default=0,
                     help="run only this many launches of the fused A kernel (the roofline kernel)")
     args = ap.parse_args()
-    if args.profile_matvec:
+    if args.profile_trajectory:
+        run_profile_trajectory(args)
+    elif args.profile_matvec:
         run_profile_matvec(args)
     elif args.profile_solve:
         run_profile_solve(args)

@@ -105,28 +105,30 @@ __global__ void k_axpy(double a, const double* __restrict__ x, double* __restric
     if (i < n) y[i] += a * x[i];
 }
 
-// The previous solutions of a trajectory's force solves, newest first.
+// The previous solutions of a trajectory's force solves, newest first, with their weights.
 constexpr int kMaxGuess = 5;   // highest extrapolation degree
 struct SolHist {
     const double2* h[kMaxGuess + 1];
+    double c[kMaxGuess + 1];
 };
 
-// out = sum_j c_j h_j, the polynomial extrapolation through np equally spaced solutions h_0
-// (newest) .. h_{np-1}: c_j = (-1)^j binomial(np, j + 1) (1; 2, -1; 3, -3, 1; 4, -6, 4, -1; ...).
-// out may be one of the h_j.
-__global__ void k_extrap(SolHist hs, double2* out, int np, int64_t n) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double2 s = make_double2(0.0, 0.0);
-    double c = (double)np, sign = 1.0;   // binomial(np, j + 1), starting at j = 0
-    for (int j = 0; j < np; ++j) {
-        const double2 v = hs.h[j][i];
-        s.x += sign * c * v.x;
-        s.y += sign * c * v.y;
-        c = c * (double)(np - j - 1) / (double)(j + 2);
-        sign = -sign;
+// out = sum_j c_j h_j over NP solutions (the weights come from the host); out may be one of the
+// h_j. FP64 throughout: the start's error only costs iterations, but an FP32 one would sit near
+// the size of the residual that a good extrapolation leaves.
+template <int NP>
+__global__ void __launch_bounds__(256) k_extrap(SolHist hs, double2* out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 v[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) v[j] = hs.h[j][i];
+        double2 s = make_double2(hs.c[0] * v[0].x, hs.c[0] * v[0].y);
+#pragma unroll
+        for (int j = 1; j < NP; ++j) {
+            s.x = fma(hs.c[j], v[j].x, s.x);
+            s.y = fma(hs.c[j], v[j].y, s.y);
+        }
+        out[i] = s;
     }
-    out[i] = s;
 }
 
 __global__ void __launch_bounds__(256) k_norm2(const double* __restrict__ a, int64_t n, double* __restrict__ part) {
@@ -512,16 +514,30 @@ static int run_chain(hmc_ctx* ctx, int c, const hmc_traj_in* in, double out_e[6]
     for (int j = 1; j <= mode; ++j) hist[j] = ctx->d_Xhist[j - 1];
     int nsol = 0;
     const int64_t nfv = (int64_t)K * 4 * lat.V;
-    const unsigned gx = (unsigned)((nfv + 255) / 256);
     auto do_force = [&](bool want) -> int {
         const bool guess = mode && nsol >= 1;
         const int np = guess ? std::min(nsol, mode + 1) : 0;
         const int io = np < mode + 1 ? np : mode;   // free slot, or the oldest solution
         double2* xo = !guess ? hist[0] : hist[io];
         if (guess) {
+            // polynomial extrapolation through np equally spaced solutions, newest first:
+            // c_j = (-1)^j binomial(np, j + 1) (1; 2, -1; 3, -3, 1; 4, -6, 4, -1; ...)
             SolHist hs{};
-            for (int j = 0; j < np; ++j) hs.h[j] = hist[j];
-            k_extrap<<<gx, 256, 0, sm>>>(hs, xo, np, nfv);
+            double cb = np;
+            for (int j = 0; j < np; ++j) {
+                hs.h[j] = hist[j];
+                hs.c[j] = (j % 2 ? -cb : cb);
+                cb = cb * (np - j - 1) / (j + 2);
+            }
+            const unsigned ge = (unsigned)std::min<int64_t>((nfv + 255) / 256, (int64_t)ctx->num_sms * 16);
+            switch (np) {
+                case 1: k_extrap<1><<<ge, 256, 0, sm>>>(hs, xo, nfv); break;
+                case 2: k_extrap<2><<<ge, 256, 0, sm>>>(hs, xo, nfv); break;
+                case 3: k_extrap<3><<<ge, 256, 0, sm>>>(hs, xo, nfv); break;
+                case 4: k_extrap<4><<<ge, 256, 0, sm>>>(hs, xo, nfv); break;
+                case 5: k_extrap<5><<<ge, 256, 0, sm>>>(hs, xo, nfv); break;
+                default: k_extrap<6><<<ge, 256, 0, sm>>>(hs, xo, nfv); break;
+            }
             HMC_LAUNCH(ctx, "k_extrap");
         }
         int r2 = force_impl(ctx, c, phi, ctx->d_pf, K, ctx->d_F, 1, in->precond, want ? &s_pf : nullptr,
