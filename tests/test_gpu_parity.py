@@ -156,6 +156,35 @@ def test_cg_solve(mode, precond, L, Nt):
         assert st["reliable_updates"] >= 1
 
 
+def test_preconditioner_speedup_point():
+    # Supplementary Note 5's claim in miniature: at the study's parameters (nesting v_2, r = 1.26,
+    # g = 0.7 sqrt(2), u = 0) the preconditioner cuts the CG iterations several-fold
+    from paper_2204_14241_gb300.experiments import precond_point
+    pt = precond_point(8, 20, 0.1, n_cfg=1)
+    assert pt["pcg_iterations"] > 0 and pt["speedup_iterations"] > 2.0, pt
+
+
+def test_sdw_zero_mode_series_binder_and_tau():
+    # SdwSusceptibility's per-sample chi(0, 0) and |Phi|^2 against the oracle on the same fields,
+    # then the Binder cumulant and tau_int of the GPU series against the oracle's
+    from oracle import observables as oobs
+    from paper_2204_14241_gb300 import observables as gobs
+    L, Nt = 6, 8
+    ctx = ctx_for(L, Nt)
+    est = gobs.SdwSusceptibility(ctx)
+    samples = [I.gaussian_field(900 + i, L, Nt) + 0.2 * (i % 3) for i in range(12)]
+    for phi in samples:
+        est.add(dev(phi))
+    V = Nt * L * L
+    for phi, m2, chi in zip(samples, est.phi2, est.chi00):
+        big = float(np.sum(np.sum(phi, axis=(1, 2, 3)) ** 2))
+        assert abs(m2 - big) < 1e-10 * big
+        assert abs(chi - COUPLINGS["dtau"] * big / V) < 1e-10 * chi
+    b_ref = oobs.binder_cumulant([I.to_paper_boson(p) for p in samples])
+    assert abs(gobs.binder_cumulant(est.phi2) - b_ref) < 1e-10
+    assert abs(gobs.tau_int(est.chi00) - oobs.tau_int(est.chi00)) < 1e-9
+
+
 def test_cg_matches_dense_solution():
     L, Nt = 4, 8
     ctx = ctx_for(L, Nt, "mixed", tol=1e-12)

@@ -202,6 +202,42 @@ def test_sdw_susceptibility_free_field():
     assert abs(rel.mean() - 1) < 0.02 and np.abs(rel - 1).max() < 0.2
 
 
+def test_binder_cumulant_limits():
+    # B_c = 1 - 3<|Phi|^4>/(5<|Phi|^2>^2): exactly 0.4 for an order parameter of fixed length, 0 on
+    # average for a Gaussian one (<|Phi|^4> = 15 s^2 and <|Phi|^2> = 3 s for three N(0, s) components)
+    from oracle import observables
+    rng = np.random.default_rng(7)
+    L, Nt = 4, 6
+    fixed = []
+    for _ in range(50):
+        u = rng.standard_normal(3)
+        u /= np.linalg.norm(u)
+        fixed.append(np.broadcast_to((0.3 * u)[:, None, None, None], (3, Nt, L, L)).copy())
+    assert abs(observables.binder_cumulant(fixed) - 0.4) < 1e-12
+    gauss = [rng.standard_normal((3, Nt, L, L)) for _ in range(4000)]
+    assert abs(observables.binder_cumulant(gauss)) < 0.05
+
+
+@pytest.mark.parametrize("a", [0.0, 0.5, 0.8])
+def test_tau_int_ar1(a):
+    # an AR(1) series x_{n+1} = a x_n + sqrt(1 - a^2) e_n has rho(t) = a^t, so
+    # tau_int = 1 + 2 sum_t a^t = (1 + a) / (1 - a); the package's FFT estimator agrees with the
+    # oracle's lag-by-lag sum on the same series
+    from oracle import observables
+    from paper_2204_14241_gb300 import observables as gobs
+    rng = np.random.default_rng(11)
+    n = 100000
+    e = rng.standard_normal(n)
+    x = np.empty(n)
+    x[0] = e[0]
+    for i in range(1, n):
+        x[i] = a * x[i - 1] + np.sqrt(1 - a * a) * e[i]
+    ref = (1 + a) / (1 - a)
+    t = observables.tau_int(x)
+    assert abs(t - ref) < 0.08 * ref, (t, ref)
+    assert abs(gobs.tau_int(x) - t) < 1e-9 * t
+
+
 def test_presets_follow_the_paper_table():
     from paper_2204_14241_gb300 import presets
     p1, p5 = presets.paper_nesting(1), presets.paper_nesting(5)
