@@ -33,6 +33,37 @@ __device__ __forceinline__ void dft_small(C* v, const C* __restrict__ tw, int n,
         C s3r; s3r.x = -dir * s3.y; s3r.y = dir * s3.x;
         v[0] = cadd(s0, s2); v[2] = csub(s0, s2);
         v[1] = cadd(s1, s3r); v[3] = csub(s1, s3r);
+    } else if constexpr (R == 3) {
+        // X_{1,2} = v0 - (v1 + v2)/2 +- dir i (sqrt(3)/2) (v1 - v2)
+        using T = decltype(v[0].x);
+        constexpr T h = (T)0.86602540378443864676;   // sin(2 pi / 3) = sqrt(3) / 2
+        const C a = v[0], b = v[1], c = v[2];
+        const T tx = b.x + c.x, ty = b.y + c.y;
+        const T dx = dir * h * (b.x - c.x), dy = dir * h * (b.y - c.y);
+        const T mx = a.x - (T)0.5 * tx, my = a.y - (T)0.5 * ty;
+        v[0].x = a.x + tx; v[0].y = a.y + ty;
+        v[1].x = mx - dy;  v[1].y = my + dx;
+        v[2].x = mx + dy;  v[2].y = my - dx;
+    } else if constexpr (R == 5) {
+        // pairs (1, 4) and (2, 3): X_{1,4} = m1 +- i n1, X_{2,3} = m2 +- i n2 with
+        // m = v0 + c (v_q + v_{5-q}) terms and n = dir s (v_q - v_{5-q}) terms
+        using T = decltype(v[0].x);
+        constexpr T c1 = (T)0.30901699437494742410;    // cos(2 pi / 5) = (sqrt 5 - 1) / 4
+        constexpr T c2 = (T)-0.80901699437494742410;   // cos(4 pi / 5) = -(sqrt 5 + 1) / 4
+        constexpr T s1 = (T)0.95105651629515357212;    // sin(2 pi / 5) = sqrt(10 + 2 sqrt 5) / 4
+        constexpr T s2 = (T)0.58778525229247312917;    // sin(4 pi / 5) = sqrt(10 - 2 sqrt 5) / 4
+        const C v0 = v[0];
+        const T a1x = v[1].x + v[4].x, a1y = v[1].y + v[4].y, a2x = v[2].x + v[3].x, a2y = v[2].y + v[3].y;
+        const T b1x = v[1].x - v[4].x, b1y = v[1].y - v[4].y, b2x = v[2].x - v[3].x, b2y = v[2].y - v[3].y;
+        const T m1x = v0.x + c1 * a1x + c2 * a2x, m1y = v0.y + c1 * a1y + c2 * a2y;
+        const T m2x = v0.x + c2 * a1x + c1 * a2x, m2y = v0.y + c2 * a1y + c1 * a2y;
+        const T n1x = dir * (s1 * b1x + s2 * b2x), n1y = dir * (s1 * b1y + s2 * b2y);
+        const T n2x = dir * (s2 * b1x - s1 * b2x), n2y = dir * (s2 * b1y - s1 * b2y);
+        v[0].x = v0.x + a1x + a2x; v[0].y = v0.y + a1y + a2y;
+        v[1].x = m1x - n1y; v[1].y = m1y + n1x;
+        v[4].x = m1x + n1y; v[4].y = m1y - n1x;
+        v[2].x = m2x - n2y; v[2].y = m2y + n2x;
+        v[3].x = m2x + n2y; v[3].y = m2y - n2x;
     } else {
         C out[R];
         const int step = n / R;
