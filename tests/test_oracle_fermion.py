@@ -184,6 +184,22 @@ def test_precond_is_inverse_of_KKdag():
     assert np.abs((K @ K.conj().T) @ Pv.ravel() - v.ravel()).max() < 1e-11 * np.abs(v).max()
 
 
+def test_precond_quadratic_form_in_frequency_space():
+    # <r, P r> = sum P-hat |F~^* r|^2 because F~ = T F is unitary (|T| = 1, F the unitary DFT): the
+    # complex64 PCG sums <r, z> this way inside its tau pass instead of re-reading r and z.
+    # Also: <r, P r> > 0 (P is positive definite) and the identity fails for a non-unitary F.
+    for L, Nt in ((4, 6), (6, 8)):
+        p = Params(L=L, Nt=Nt)
+        r = rand_vec(p, 30 + L)
+        lhs = np.vdot(r, solver.apply_precond(p, r)).real
+        T = solver.twist(p)
+        rh = np.fft.fftn(np.conj(T) * r, axes=(2, 3, 4), norm="ortho")
+        rhs = float(np.sum(solver.precond_symbol(p) * np.abs(rh) ** 2))
+        assert lhs > 0 and abs(lhs - rhs) < 1e-12 * lhs
+        rh_raw = np.fft.fftn(np.conj(T) * r, axes=(2, 3, 4))   # unnormalised: off by V
+        assert abs(float(np.sum(solver.precond_symbol(p) * np.abs(rh_raw) ** 2)) - lhs) > 0.5 * lhs
+
+
 def test_layout_roundtrip():
     v = inputs.fermion_noise(0, 1, 4, 6)[0]
     assert np.array_equal(inputs.from_paper_fermion(inputs.to_paper_fermion(v)), v)
