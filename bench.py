@@ -39,8 +39,8 @@ WORKLOAD = (f"L={L}x{L}, Nt={NT} (dtau=0.1), 2 bands x 2 spins, {NRHS} pseudofer
             f"eps={EPS}, complex64 PCG with FP64 reliable updates to true residual {TOL}, "
             "degree-4 chronological initial guess, phi = free-boson-spectrum Gaussian field, sigma-hat = its spectrum")
 # DRAM bytes (read + write) of one launch of the roofline kernel, the plain fused A on 8 RHS at
-# 80x80x160, from ncu (profiles/ncu_apply_A_plain_80x80x160_8rhs.md); set to None when that
-# kernel changes until it is captured again.
+# 80x80x160, from one ncu capture of `bench.py --profile-matvec 3`; set to None when that kernel
+# changes until it is captured again.
 ROOFLINE_TRAFFIC_BYTES = 550_630_144
 # PCG iterations per solve of this workload with the degree-4 chronological start (20.3 measured
 # on a GB300), used only to scale the oracle's timed sample (a few PCG iterations) to a
@@ -91,6 +91,15 @@ def chain_seed(base, rank):
 
 
 # ---- clocks ------------------------------------------------------------------------------------------
+CLOCK_LOG_DIR = None   # --clock-log DIR keeps the raw nvidia-smi samples there (default: a temp file)
+
+
+def clock_log_path(gpu_index):
+    import tempfile
+    d = CLOCK_LOG_DIR or tempfile.gettempdir()
+    return os.path.join(d, f"hmc_bench_clocks_gpu{gpu_index}_{os.getpid()}.csv")
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -99,7 +108,7 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.path = clock_log_path(gpu_index)
 
     def start(self):
         try:
@@ -427,6 +436,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clock-log", default=None, help="directory for the raw nvidia-smi clock samples")
     ap.add_argument("--profile-solve", type=int, default=0,
                     help="run only a capture-sized sample: one solve cut at this many iterations")
     ap.add_argument("--profile-trajectory", action="store_true",
@@ -434,6 +444,8 @@ def main():
     ap.add_argument("--profile-matvec", type=int, default=0,
                     help="run only this many launches of the fused A kernel (the roofline kernel)")
     args = ap.parse_args()
+    global CLOCK_LOG_DIR
+    CLOCK_LOG_DIR = args.clock_log
     if args.profile_trajectory:
         run_profile_trajectory(args)
     elif args.profile_matvec:

@@ -105,7 +105,9 @@ typedef struct hmc_ctx hmc_ctx;
 
 /* Create a context for n_chains lattices. chains may be NULL, in which case every chain
  * uses p->L, p->Nt, p->r. cuda_stream is a cudaStream_t (or NULL for the default
- * stream). Allocates all device workspace. Errors: HMC_ERR_ARG, HMC_ERR_CUDA. */
+ * stream). Allocates all device workspace on the device current at the call; every later
+ * call on the context makes that device current for its duration and restores the caller's.
+ * Errors: HMC_ERR_ARG, HMC_ERR_CUDA. */
 int hmc_init(const hmc_params* p, int n_chains, const hmc_chain* chains, void* cuda_stream,
              hmc_ctx** out);
 int hmc_destroy(hmc_ctx* ctx);
@@ -134,16 +136,20 @@ int apply_MdagM(hmc_ctx* ctx, int chain, int prec, const void* phi, const void* 
  * until the process exits. It calls no cudaMalloc, cudaFree or allocating library routine.
  *   p: model parameters (only dtau, t_h, t_v, mu and g are read); L, Nt: lattice; prec:
  *   HMC_FP64 or HMC_FP32 (as for apply_MdagM); phi, x, y: device, layouts as for apply_MdagM,
- *   16-byte aligned, x and y disjoint; nrhs >= 1 (<= 64 when norm2 is requested);
- *   cuda_stream: cudaStream_t or NULL for the default stream.
+ *   16-byte aligned, the byte range of y disjoint from those of x and phi; 1 <= nrhs <= 65535
+ *   (<= 64 when norm2 is requested); cuda_stream: cudaStream_t or NULL for the default stream.
+ * It always runs the generic fused kernel (the one apply_MdagM uses for FP64 and for lattices
+ * without 16 x 16 tiles), never the complex64 16 x 16-tile kernel, so for complex64 with L a
+ * multiple of 16 it is slower than apply_MdagM; the results agree to rounding.
  * Set-up: the first call on each device (with that device current) looks up the device
  * address of the scratch array (cudaGetSymbolAddress); make that first call before any
  * stream capture. Every call on a device shares the one array and overwrites it, and each
  * slot it reads back is written earlier in the same call, so nothing needs clearing; calls
  * that can overlap on the GPU (other streams, other host threads) race on the array and
  * must be serialised by the caller. With norm2 the call synchronises cuda_stream.
- * Errors: HMC_ERR_ARG for bad arguments, and when nrhs times the number of tile blocks of
- * the fused kernel exceeds the 65536 scratch slots (the message gives both numbers);
+ * Errors: HMC_ERR_ARG for bad arguments (including overlapping ranges), and when norm2 is
+ * requested and nrhs times the number of tile blocks of the fused kernel exceeds the 65536
+ * scratch slots (the message gives the count needed, its two factors and the limit);
  * HMC_ERR_CUDA for runtime failures. The message is available from hmc_last_error(NULL). */
 int apply_MdagM_static(const hmc_params* p, int L, int Nt, int prec, const void* phi, const void* x, void* y,
                        int nrhs, double* norm2, void* cuda_stream);

@@ -7,6 +7,7 @@ backward: the force kernel. dS/dphi = -F_PF, where F_PF is the fermion part of t
 (include_boson = 0); the solution X = A^{-1} varphi and Y = D^dagger X are recomputed in
 backward, not stored, so memory does not grow with the lattice.
 The boson field phi is float64 (3, Nt, L, L); varphi is complex128 (k, Nt, L, L, 2, 2).
+Only phi is differentiable: a varphi that requires grad is refused in forward.
 """
 
 import torch
@@ -15,6 +16,8 @@ import torch
 class PseudofermionAction(torch.autograd.Function):
     @staticmethod
     def forward(fctx, phi, phi_pf, hmc_ctx, chain=0, precond=True):
+        if fctx.needs_input_grad[1]:
+            raise ValueError("PseudofermionAction: only phi is differentiable; pass varphi without requires_grad")
         phi_c = phi.detach().contiguous()
         _, s_pf, _, _ = hmc_ctx.force(phi_c, phi_pf.contiguous(), include_boson=False, precond=precond,
                                       chain=chain)

@@ -472,10 +472,11 @@ int fft_axis(hmc_ctx* ctx, cplx<R>* data, int64_t outer, int n, int64_t inner, i
     if (!p) return fail(ctx, HMC_ERR_STATE, "no FFT plan for length " + std::to_string(n));
     FftTile ft = make_tile<R>(outer, n, inner);
     const size_t sm = 2 * (size_t)n * ft.OB * ft.IC * sizeof(cplx<R>);
-    static bool attr[2] = {false, false};
-    if (!attr[sizeof(R) == 8]) {
+    static PerDevice attr;
+    uint64_t bit;
+    if (attr.pending(&bit)) {
         HMC_CUDA(ctx, cudaFuncSetAttribute(k_fft<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-        attr[sizeof(R) == 8] = true;
+        attr.mark(bit);
     }
     const int64_t nblk = ((outer + ft.OB - 1) / ft.OB) * ft.nib;
     k_fft<R><<<(unsigned)nblk, 256, sm, ctx->stream>>>(src ? src : data, data, ft, stage_plan(p), tw_of<R>(p), dir,
@@ -512,10 +513,11 @@ int precond_tau(hmc_ctx* ctx, const Lat& lat, cplx<R>* y, int nrhs, const CgScal
     pc.twist = pt->twist;
     FftTile ft = make_tile<R>(nrhs, Nt, 4 * (int64_t)L * L);
     const size_t sm = 2 * (size_t)Nt * ft.OB * ft.IC * sizeof(cplx<R>);
-    static bool attr = false;
-    if (!attr) {
+    static PerDevice attr;
+    uint64_t bit;
+    if (attr.pending(&bit)) {
         HMC_CUDA(ctx, cudaFuncSetAttribute(k_precond_tau<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-        attr = true;
+        attr.mark(bit);
     }
     const int64_t nblk = ((ft.outer + ft.OB - 1) / ft.OB) * ft.nib;
     k_precond_tau<R><<<(unsigned)nblk, 256, sm, ctx->stream>>>(y, ft, stage_plan(p), tw_of<R>(p), pc,
@@ -565,11 +567,12 @@ int launch_cg_update_precond(hmc_ctx* ctx, const Lat& lat, cplx<R>* x, cplx<R>* 
     const int64_t nblk = (rows + OB - 1) / OB;
     if (nblk * nrhs > ctx->part_cap / 2) return fail(ctx, HMC_ERR_ARG, "cg update: reduction buffer too small");
     const size_t sm = 2 * (size_t)L * OB * 4 * sizeof(cplx<R>);
-    static bool attr = false;
-    if (!attr) {
+    static PerDevice attr;
+    uint64_t bit;
+    if (attr.pending(&bit)) {
         HMC_CUDA(ctx, cudaFuncSetAttribute(k_fft_x_cg<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
         HMC_CUDA(ctx, cudaFuncSetAttribute(k_fft_x_cg<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-        attr = true;
+        attr.mark(bit);
     }
     int rc;
     if constexpr (sizeof(R) == 4) {

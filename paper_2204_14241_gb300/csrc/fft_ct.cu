@@ -432,11 +432,12 @@ static int launch_one(hmc_ctx* ctx, dim3 grid, const FftcArgs& A) {
     constexpr int NL = lines_for<N>();
     constexpr int ICr = (IC == 4) ? 4 : NL;
     const size_t sm = 2 * (size_t)N * NL * sizeof(float2);
-    static bool attr = false;
-    if (!attr) {
+    static PerDevice attr;
+    uint64_t bit;
+    if (attr.pending(&bit)) {
         HMC_CUDA(ctx, cudaFuncSetAttribute(k_fftc<N, NL, ICr, MODE, DIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)sm));
-        attr = true;
+        attr.mark(bit);
     }
     k_fftc<N, NL, ICr, MODE, DIR><<<grid, kThreads, sm, ctx->stream>>>(A);
     HMC_LAUNCH(ctx, "k_fftc");
@@ -927,11 +928,12 @@ int fftc_xy_freq(int L, int pos) {
 template <int L, int DIR, bool PUPD>
 static int launch_xy(hmc_ctx* ctx, const FftcArgs& A, int Nt, int nrhs) {
     constexpr size_t sm = xy_smem_bytes<L>();
-    static bool attr = false;
-    if (!attr) {
+    static PerDevice attr;
+    uint64_t bit;
+    if (attr.pending(&bit)) {
         HMC_CUDA(ctx, cudaFuncSetAttribute(k_fft_xy<L, DIR, PUPD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)sm));
-        attr = true;
+        attr.mark(bit);
     }
     k_fft_xy<L, DIR, PUPD><<<dim3((unsigned)(2 * Nt), nrhs), kXYThreads, sm, ctx->stream>>>(A, Nt);
     HMC_LAUNCH(ctx, "k_fft_xy");

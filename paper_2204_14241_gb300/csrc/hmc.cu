@@ -251,6 +251,7 @@ int hmc_init(const hmc_params* p, int n_chains, const hmc_chain* chains, void* c
     int rc = HMC_OK;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    ctx->device = dev;
     if (e != cudaSuccess) {
         rc = cuda_check(nullptr, e, "hmc_init: device query");
         delete ctx;
@@ -301,6 +302,7 @@ int hmc_init(const hmc_params* p, int n_chains, const hmc_chain* chains, void* c
 
 int hmc_destroy(hmc_ctx* ctx) {
     if (!ctx) return HMC_OK;
+    DevGuard g(ctx);
     cudaStreamSynchronize(ctx->stream);
     free_all(ctx);
     delete ctx;
@@ -311,6 +313,7 @@ int apply_M(hmc_ctx* ctx, int chain, int prec, const void* phi, const void* x, v
     int rc;
     if ((rc = check_chain(ctx, chain)) || (rc = check_nrhs(ctx, nrhs)) || (rc = check_ptrs(ctx, {phi, x, y}))) return rc;
     if (x == y) return fail(ctx, HMC_ERR_ARG, "apply_M: x and y must not overlap");
+    DevGuard g(ctx);
     const Lat& lat = ctx->chains[chain].lat;
     if (prec == HMC_FP64)
         return launch_apply_D<double>(ctx, lat, (const double*)phi, (const double2*)x, (double2*)y, dagger, nrhs);
@@ -323,6 +326,7 @@ int apply_MdagM(hmc_ctx* ctx, int chain, int prec, const void* phi, const void* 
     int rc;
     if ((rc = check_chain(ctx, chain)) || (rc = check_nrhs(ctx, nrhs)) || (rc = check_ptrs(ctx, {phi, x, y}))) return rc;
     if (x == y) return fail(ctx, HMC_ERR_ARG, "apply_MdagM: x and y must not overlap");
+    DevGuard g(ctx);
     const Lat& lat = ctx->chains[chain].lat;
     double* part = norm2 ? ctx->d_part : nullptr;
     int nb = 0;
@@ -337,6 +341,7 @@ int apply_MdagM(hmc_ctx* ctx, int chain, int prec, const void* phi, const void* 
 int apply_precond(hmc_ctx* ctx, int chain, int prec, const void* x, void* y, int nrhs) {
     int rc;
     if ((rc = check_chain(ctx, chain)) || (rc = check_nrhs(ctx, nrhs)) || (rc = check_ptrs(ctx, {x, y}))) return rc;
+    DevGuard g(ctx);
     const Lat& lat = ctx->chains[chain].lat;
     if (prec == HMC_FP64) return launch_precond<double>(ctx, lat, (const double2*)x, (double2*)y, nrhs);
     if (prec == HMC_FP32) return launch_precond<float>(ctx, lat, (const float2*)x, (float2*)y, nrhs);
@@ -348,6 +353,7 @@ int cg_solve(hmc_ctx* ctx, int chain, const void* phi, const void* b, void* x, i
     int rc;
     if ((rc = check_chain(ctx, chain)) || (rc = check_nrhs(ctx, nrhs)) || (rc = check_ptrs(ctx, {phi, b, x}))) return rc;
     if (b == x) return fail(ctx, HMC_ERR_ARG, "cg_solve: b and x must not overlap");
+    DevGuard g(ctx);
     if (tol <= 0.0) tol = ctx->p.cg_tol;
     if (maxit <= 0) maxit = ctx->p.cg_maxit;
     return cg_run(ctx, chain, (const double*)phi, (const double2*)b, (double2*)x, nrhs, tol, maxit, precond ? 1 : 0, st);
@@ -378,6 +384,7 @@ extern "C" int force(hmc_ctx* ctx, int chain, const void* phi, const void* phi_p
                      int include_boson, int precond, double* S_b, hmc_cg_stats* st) {
     int rc;
     if ((rc = check_chain(ctx, chain)) || (rc = check_nrhs(ctx, nrhs)) || (rc = check_ptrs(ctx, {phi, phi_pf, F}))) return rc;
+    DevGuard g(ctx);
     double sb = 0.0;
     rc = force_impl(ctx, chain, (const double*)phi, (const double2*)phi_pf, nrhs, (double*)F, include_boson,
                     precond, S_pf, (S_b || include_boson) ? &sb : nullptr, st, ctx->d_X, false);
@@ -405,6 +412,7 @@ extern "C" int metric_apply(hmc_ctx* ctx, int chain, int op, const void* sig, co
     } else if ((rc = check_ptrs(ctx, {out}))) {
         return rc;
     }
+    DevGuard g(ctx);
     const Lat& lat = ctx->chains[chain].lat;
     if ((rc = metric_op(ctx, lat, op, (const double*)sig, (const double*)in, (double*)out, 0.0, ctx->d_red))) return rc;
     if (op == HMC_METRIC_KINETIC || op == HMC_METRIC_MNORM) return fetch_red(ctx, 1, scalar);
@@ -415,12 +423,14 @@ extern "C" int green_estimate(hmc_ctx* ctx, int chain, const void* phi, const vo
                               int precond, hmc_cg_stats* st) {
     int rc;
     if ((rc = check_chain(ctx, chain)) || (rc = check_nrhs(ctx, nrhs)) || (rc = check_ptrs(ctx, {phi, v, out}))) return rc;
+    DevGuard g(ctx);
     return green_run(ctx, chain, (const double*)phi, (const double2*)v, nrhs, (double2*)out, precond ? 1 : 0, st);
 }
 
 extern "C" int philox_raw(hmc_ctx* ctx, uint64_t key, const uint32_t ctr[4], int64_t nblocks, void* out) {
     if (!ctx || !ctr || !out || nblocks < 0) return fail(ctx, HMC_ERR_ARG, "philox_raw: bad argument");
     if (nblocks == 0) return HMC_OK;
+    DevGuard g(ctx);
     U4 c;
     for (int q = 0; q < 4; ++q) c.v[q] = ctr[q];
     k_philox_raw<<<(unsigned)((nblocks + 255) / 256), 256, 0, ctx->stream>>>(key, c, nblocks, (uint32_t*)out);
@@ -441,6 +451,7 @@ extern "C" int philox_normal(hmc_ctx* ctx, uint64_t seed, uint64_t counter, int6
     if (!ctx || n < 0) return fail(ctx, HMC_ERR_ARG, "philox_normal: bad argument");
     int rc;
     if ((rc = check_ptrs(ctx, {out}))) return rc;
+    DevGuard g(ctx);
     return gen_normal(ctx, seed, counter, 0, n, complex_out ? 1 : 0, (double*)out);
 }
 
@@ -610,6 +621,7 @@ extern "C" int trajectory(hmc_ctx* ctx, const hmc_traj_in* in, hmc_traj_out* out
         if ((rc = check_ptrs(ctx, {in->phi[c], in->sigma_hat[c]}))) return rc;
         if (in->noise == HMC_NOISE_EXPLICIT && (rc = check_ptrs(ctx, {in->chi[c], in->z[c]}))) return rc;
     }
+    DevGuard g(ctx);
     int first_err = HMC_OK;
     for (int c = 0; c < nc; ++c) {
         double e[6] = {0, 0, 0, 0, 0, 0}, dh = 0.0, worst = 0.0, j2 = 0.0;

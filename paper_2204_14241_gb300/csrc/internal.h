@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -62,6 +63,7 @@ struct CgScalars {
 struct hmc_ctx {
     hmc_params p{};
     cudaStream_t stream = nullptr;
+    int device = 0;               // CUDA device current at hmc_init; every entry point runs on it
     std::vector<hmc::ChainDesc> chains;
     int64_t vmax = 0;
     int kmax = 1;
@@ -112,6 +114,35 @@ struct hmc_ctx {
 };
 
 namespace hmc {
+
+// cudaFuncSetAttribute applies to the current device only, so each kernel remembers, per device
+// ordinal, whether its attribute has been set there (ordinals >= 64 set it on every call).
+struct PerDevice {
+    std::atomic<uint64_t> done{0};
+    bool pending(uint64_t* bit) {
+        int d = 0;
+        *bit = 0;
+        if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= 64) return true;
+        *bit = 1ull << d;
+        return (done.load(std::memory_order_acquire) & *bit) == 0;
+    }
+    void mark(uint64_t bit) { done.fetch_or(bit, std::memory_order_acq_rel); }
+};
+
+// Makes the context's device current for the lifetime of the guard and restores the caller's.
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(const hmc_ctx* ctx) {
+        int cur = 0;
+        if (ctx && cudaGetDevice(&cur) == cudaSuccess && cur != ctx->device && cudaSetDevice(ctx->device) == cudaSuccess)
+            prev = cur;
+    }
+    ~DevGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DevGuard(const DevGuard&) = delete;
+    DevGuard& operator=(const DevGuard&) = delete;
+};
 
 // status helpers
 int fail(hmc_ctx* ctx, int code, const std::string& msg);

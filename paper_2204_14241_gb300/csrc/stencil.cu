@@ -607,8 +607,9 @@ int launch_apply_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x,
                    const cplx<R>* pold, cplx<R>* pnew) {
     if (nrhs <= 0) return HMC_OK;
     if (pnew && (!cgs || !pold || pold == pnew)) return fail(ctx, HMC_ERR_ARG, "apply_A: bad direction-update buffers");
-    static bool attr_set = false;
-    if (!attr_set) {
+    static PerDevice attr;
+    uint64_t bit;
+    if (attr.pending(&bit)) {
         HMC_CUDA(ctx, cudaFuncSetAttribute(k_apply_A<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         HMC_CUDA(ctx, cudaFuncSetAttribute(k_apply_A<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         if constexpr (sizeof(R) == 4)
@@ -616,7 +617,7 @@ int launch_apply_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x,
             HMC_CUDA(ctx, cudaFuncSetAttribute(k_apply_A4<16, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)A4Shape<16, 16>::smem));
         }
-        attr_set = true;
+        attr.mark(bit);
     }
     const int prec = sizeof(R) == 8 ? HMC_FP64 : HMC_FP32;
     ATile tl;
@@ -712,8 +713,9 @@ static int apply_A_static(const hmc_params* p, const Lat& lat, const R* phi, con
     const dim3 grid(tl.ntx * tl.nty, tl.nchunk, nrhs);
     const int64_t nblk = (int64_t)grid.x * grid.y;
     if (norm2 && nblk * nrhs > kStaticPartials)
-        return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: " + std::to_string(nblk * nrhs) +
-                    " partial sums exceed the static scratch of " + std::to_string(kStaticPartials));
+        return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: the norms need " + std::to_string(nblk * nrhs) +
+                    " partial sums (" + std::to_string(nblk) + " tile blocks x " + std::to_string(nrhs) +
+                    " right-hand sides), more than the " + std::to_string(kStaticPartials) + " slots of the static scratch");
     const size_t sm = a_smem_bytes<R>(tl);
     cudaError_t e = cudaFuncSetAttribute(k_apply_A<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return cuda_check(nullptr, e, "apply_MdagM_static: cudaFuncSetAttribute");
@@ -737,15 +739,23 @@ extern "C" int apply_MdagM_static(const hmc_params* p, int L, int Nt, int prec, 
     if (!p || !phi || !x || !y) return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: null argument");
     if ((((uintptr_t)phi) | ((uintptr_t)x) | ((uintptr_t)y)) & 15u)
         return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: pointer not 16-byte aligned");
-    if (x == y) return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: x and y must not overlap");
     if (L < 2 || (L & 1) || L > 4096 || Nt < 2 || Nt > 65536)
         return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: need even L in [2, 4096] and Nt in [2, 65536]");
-    if (nrhs < 1 || (norm2 && nrhs > kStaticRows) || nrhs > 65535)
-        return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: nrhs must be in [1, 64] when norms are requested");
+    if (nrhs < 1 || nrhs > 65535)
+        return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: nrhs must be in [1, 65535]");
+    if (norm2 && nrhs > kStaticRows)
+        return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: nrhs must be at most 64 when norms are requested");
+    if (prec != HMC_FP64 && prec != HMC_FP32) return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: unknown precision");
     Lat lat;
     lat.L = L;
     lat.Nt = Nt;
     lat.V = (int64_t)Nt * L * L;
+    // y is written while x and phi are read: their byte ranges must be disjoint from y's
+    const uintptr_t real_b = prec == HMC_FP64 ? 8 : 4;
+    const uintptr_t vb = (uintptr_t)nrhs * (uintptr_t)lat.V * 8 * real_b, pb = 3 * (uintptr_t)lat.V * real_b;
+    const uintptr_t xa = (uintptr_t)x, ya = (uintptr_t)y, pa = (uintptr_t)phi;
+    if (xa < ya + vb && ya < xa + vb) return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: x and y overlap");
+    if (pa < ya + vb && ya < pa + pb) return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: phi and y overlap");
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (prec == HMC_FP64)
         return apply_A_static<double>(p, lat, (const double*)phi, (const Site<double>*)x, (Site<double>*)y, nrhs,
@@ -753,13 +763,14 @@ extern "C" int apply_MdagM_static(const hmc_params* p, int L, int Nt, int prec, 
     if (prec == HMC_FP32)
         return apply_A_static<float>(p, lat, (const float*)phi, (const Site<float>*)x, (Site<float>*)y, nrhs,
                                      norm2, st);
-    return fail(nullptr, HMC_ERR_ARG, "apply_MdagM_static: unknown precision");
+    return HMC_ERR_ARG;
 }
 
 namespace hmc {
 
 // ---------------------------------------------------------------------------------------
-// Boson pieces: -dS_B/dphi and the S_B density (forward differences, see oracle reading).
+// Boson pieces: -dS_B/dphi and the S_B density of the forward-difference lattice action
+// S_B = dtau sum [(1/c^2)|phi(t+1) - phi(t)|^2 / dtau^2 + (1/2) sum_d |phi(r+d) - phi(r)|^2 + (r/2)|phi|^2 + (u/4)|phi|^4].
 struct BosonCoef {
     double dtau, kt, r, u;   // kt = 1 / (c^2 dtau^2)
 };

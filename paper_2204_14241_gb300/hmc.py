@@ -122,16 +122,28 @@ def apply_MdagM_static(params, L, Nt, phi, x, out, norms=False, stream=None):
     .params); `out` is caller-allocated like x. Returns out, or (out, norms) when norms is set."""
     lib_ = lib()
     if x.dtype == torch.complex128:
-        prec = FP64
+        prec, rdt = FP64, torch.float64
     elif x.dtype == torch.complex64:
-        prec = FP32
+        prec, rdt = FP32, torch.float32
     else:
         raise ValueError("fermion vectors must be complex128 or complex64")
+    for name, t in (("phi", phi), ("x", x), ("out", out)):
+        if t.device.type != "cuda" or t.device != x.device:
+            raise ValueError(f"{name} must be a CUDA tensor on {x.device}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if phi.dtype != rdt or tuple(phi.shape) != (3, Nt, L, L):
+        raise ValueError(f"phi must be {rdt} of shape (3, {Nt}, {L}, {L}) for {x.dtype} vectors")
+    if x.dim() != 6 or tuple(x.shape[1:]) != (Nt, L, L, 2, 2):
+        raise ValueError(f"x must have shape (nrhs, {Nt}, {L}, {L}, 2, 2), got {tuple(x.shape)}")
+    if out.dtype != x.dtype or tuple(out.shape) != tuple(x.shape):
+        raise ValueError("out must have the dtype and shape of x")
     k = x.shape[0]
     nrm = (ctypes.c_double * k)() if norms else None
-    st = stream if stream is not None else torch.cuda.current_stream(x.device)
-    rc = lib_.apply_MdagM_static(ctypes.byref(params), L, Nt, prec, _ptr(phi), _ptr(x), _ptr(out), k, nrm,
-                                 ctypes.c_void_p(st.cuda_stream))
+    with torch.cuda.device(x.device):
+        st = stream if stream is not None else torch.cuda.current_stream(x.device)
+        rc = lib_.apply_MdagM_static(ctypes.byref(params), L, Nt, prec, _ptr(phi), _ptr(x), _ptr(out), k, nrm,
+                                     ctypes.c_void_p(st.cuda_stream))
     if rc:
         raise HmcError(rc, lib_.hmc_last_error(None).decode())
     return (out, list(nrm)) if norms else out

@@ -57,3 +57,48 @@ def test_static_rejects_oversized_requests():
     with pytest.raises(HmcError) as e:
         apply_MdagM_static(p, L, Nt, phi, x, torch.empty_like(x), norms=True)
     assert e.value.code == HMC_ERR_ARG and "64" in str(e.value)
+
+
+def test_static_checks_arguments_before_launch():
+    # mismatched precisions, shapes, layouts and devices are refused by the binding before the
+    # library is called, so no kernel can read or write outside the tensors
+    from paper_2204_14241_gb300.hmc import Params, apply_MdagM_static
+    L, Nt = 4, 8
+    p = Params()
+    p.dtau, p.g = 0.1, 1.0
+    phi64 = torch.zeros((3, Nt, L, L), dtype=torch.float64, device="cuda")
+    x128 = torch.zeros((2, Nt, L, L, 2, 2), dtype=torch.complex128, device="cuda")
+    x64 = x128.to(torch.complex64)
+    bad = [
+        (phi64.float(), x128, torch.empty_like(x128)),                       # float32 phi, complex128 x
+        (phi64, x64, torch.empty_like(x64)),                                 # float64 phi, complex64 x
+        (phi64[:, :4].contiguous(), x128, torch.empty_like(x128)),           # phi smaller than (L, Nt)
+        (phi64, x128[:, :4].contiguous(), torch.empty_like(x128)),           # x smaller than (L, Nt)
+        (phi64, x128, torch.empty_like(x128)[:1]),                           # out smaller than x
+        (phi64, x128, torch.empty_like(x64)),                                # out of another dtype
+        (phi64, x128.transpose(2, 3), torch.empty_like(x128)),               # x not contiguous
+        (phi64.cpu(), x128, torch.empty_like(x128)),                         # phi on the host
+    ]
+    for phi, x, out in bad:
+        with pytest.raises(ValueError):
+            apply_MdagM_static(p, L, Nt, phi, x, out, norms=True)
+
+
+def test_static_partial_sum_limit_message():
+    # a 2912 x 2912 x 2 lattice in complex64 has 182 x 182 = 33124 blocks of 16 x 16 sites, so two
+    # right-hand sides with norms need 66248 partial sums, past the 65536 static slots; the call
+    # is refused before any launch (x and y are left uninitialised) and says so with both factors
+    from paper_2204_14241_gb300.hmc import HmcError, HMC_ERR_ARG, Params, apply_MdagM_static
+    L, Nt, K = 2912, 2, 2
+    p = Params()
+    p.dtau, p.g = 0.1, 1.0
+    phi = torch.empty((3, Nt, L, L), dtype=torch.float32, device="cuda")
+    x = torch.empty((K, Nt, L, L, 2, 2), dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    with pytest.raises(HmcError) as e:
+        apply_MdagM_static(p, L, Nt, phi, x, y, norms=True)
+    msg = str(e.value)
+    assert e.value.code == HMC_ERR_ARG
+    assert "66248" in msg and "33124" in msg and "65536" in msg, msg
+    del phi, x, y
+    torch.cuda.empty_cache()
