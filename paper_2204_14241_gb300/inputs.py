@@ -12,7 +12,8 @@ The helpers ``to_paper_*`` / ``from_paper_*`` permute to and from the paper's in
 Synthetic workload recipe: phi is either i.i.d. N(0, 1) per component, or a smooth
 Gaussian random field whose Fourier variance is 1 / (m2 + kt * (2 - 2 cos w)
 + (4 - 2 cos kx - 2 cos ky)) (``smooth_field``), the shape of a thermalised
-free-boson configuration.
+free-boson configuration, optionally shifted by a uniform amplitude along one component
+(``ordered_field``).
 """
 
 import numpy as np
@@ -42,6 +43,14 @@ def smooth_field(seed, L, Nt, m2, kt):
     zh = np.fft.fftn(z, axes=(1, 2, 3), norm="ortho")
     return np.fft.ifftn(zh * np.sqrt(spectrum(L, Nt, m2, kt))[None], axes=(1, 2, 3),
                         norm="ortho").real
+
+
+def ordered_field(seed, L, Nt, m2, kt, scale, amp):
+    """``scale * smooth_field`` plus the constant ``amp`` on component 3: a uniform (ordered)
+    field with Gaussian fluctuations of the ``spectrum`` shape, library layout."""
+    f = scale * smooth_field(seed, L, Nt, m2, kt)
+    f[2] += amp
+    return f
 
 
 def complex_normal(seed, shape):

@@ -1,7 +1,7 @@
 """S(phi) = varphi^dagger A^{-1} varphi as a torch.autograd.Function whose backward is the
 libhmc force kernel: central finite differences at 32 random sites of a 40 x 40 x 80 lattice
 (complex64 PCG with FP64 reliable updates, solution recomputed in backward), and the full
-gradient against the oracle on a 12 x 12 x 24 lattice.
+gradient against the oracle on a 12 x 12 x 24 lattice to 1e-10 relative in both solver modes.
 
 Finite-difference tolerance: S ~ 1e5 is exact to ~1e-16 relative in FP64, so the central
 difference with step 1e-6 carries an absolute error ~ 1e-16 * |S| / 1e-6 ~ 1e-5; the solver
@@ -52,10 +52,14 @@ def test_autograd_finite_differences_40x40x80():
         assert abs(fd - g[idx]) < 1e-4 * max(1.0, abs(g[idx])), (idx, fd, g[idx])
 
 
-def test_autograd_gradient_matches_oracle():
+@pytest.mark.parametrize("mode,tol", [("fp64", 1e-14), ("mixed", 1e-13)])
+def test_autograd_gradient_matches_oracle(mode, tol):
+    # FP64-mode bar 1e-10 relative on the gradient; the mixed mode refines to an FP64 true
+    # residual and is held to the same bar
     from paper_2204_14241_gb300.action import pseudofermion_action
+    from paper_2204_14241_gb300.hmc import Context
     L, Nt, K = 12, 24, 2
-    ctx = make(L, Nt, nrhs=K)
+    ctx = Context(L, Nt, solver=mode, nrhs_max=K, cg_tol=tol, **COUPLINGS)
     phi0 = I.gaussian_field(93, L, Nt) * 0.5
     pf0 = I.fermion_noise(94, K, L, Nt)
     phi = torch.from_numpy(phi0).cuda().requires_grad_(True)
@@ -63,7 +67,7 @@ def test_autograd_gradient_matches_oracle():
     S.backward()
     P = Params(L=L, Nt=Nt, **COUPLINGS)
     F, s_ref, _ = ohmc.force(P, I.to_paper_boson(phi0), [I.to_paper_fermion(pf0[k]) for k in range(K)],
-                             method="cg", tol=1e-13, include_boson=False)
+                             method="cg", tol=1e-15, include_boson=False)
     g = I.to_paper_boson(phi.grad.cpu().numpy())
     assert abs(S.item() - s_ref) < 1e-10 * abs(s_ref)
-    assert np.abs(g + F).max() < 1e-7 * np.abs(F).max()
+    assert np.abs(g + F).max() < 1e-10 * np.abs(F).max()
