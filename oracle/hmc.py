@@ -152,6 +152,21 @@ def trajectory(p: Params, phi, sigma_hat, chis, z, u, eps, n_leap, method="dense
     }
 
 
+def sigma_estimate_centered(samples):
+    """Covariance of the batch about its own mean, per Fourier mode:
+    sigma-hat = (1/S) sum_s |F phi_s|^2 - |F phi-bar|^2 with phi-bar the batch mean.
+
+    Reading of Section "Online metric estimation": Sigma_true = <phi phi^T> is the covariance of
+    the target, whose mean vanishes by O(3) symmetry, and the metric is to rescale the target to
+    unit covariance. A warm-up batch of an ordered chain does not turn its condensate, so the
+    uncentered moment of Eq. (covest) books the condensate V |phi-bar|^2 on the zero mode as a
+    fluctuation; this estimate equals Eq. (covest) whenever the batch mean vanishes."""
+    S = len(samples)
+    mean = sum(samples) / S
+    mh = fourier(mean)
+    return sigma_estimate(samples) - (mh * np.conj(mh)).real
+
+
 def sigma_estimate(samples):
     """Eq. (covest): sigma-hat = (1/S) sum_s F phi_s . conj(F phi_s)."""
     acc = None

@@ -6,7 +6,9 @@ alternating sizes eps and eps/2 from the current chain state; eps grows by a fac
 alpha(eps/2)^2 <= 2 alpha(eps) holds and shrinks by the same factor otherwise. (Reading: the
 printed form (1 - alpha(eps/2))^2 <= 2 (1 - alpha(eps)) holds for any acceptance curve that
 falls with eps; the passage itself compares the probability of accepting two half steps,
-alpha(eps/2)^2, with that of one full step at half the cost, 2 alpha(eps).)
+alpha(eps/2)^2, with that of one full step at half the cost, 2 alpha(eps).) When no proposal
+of size eps is accepted (alpha(eps) = 0) the comparison is vacuous and eps shrinks: the rule is
+to take eps as large as possible without losing the acceptance.
 
 Trajectory length, Eq. (ESJD): ESJD(n) = < (phi - phi')^T M (phi - phi') alpha > over proposals
 with n_leap = n, M = Sigma^{-1} (so the norm is sum |F (phi' - phi)|^2 / sigma-hat); n_max is
@@ -35,7 +37,7 @@ class Tuner:
         chis, z, u = self.noise(self.t)
         self.t += 1
         out = hmc.trajectory(self.p, self.phi, self.sigma_hat, chis, z, u, eps, n_leap, self.method, self.tol)
-        alpha = min(1.0, float(np.exp(-out["dH"])))
+        alpha = min(1.0, float(np.exp(-out["dH"]))) if np.isfinite(out["dH"]) else 0.0
         jump2 = jump_norm2(self.sigma_hat, out["phi_proposed"] - self.phi)
         self.phi = out["phi"]
         return alpha, jump2, out["dH"], out["accept"]
@@ -45,7 +47,7 @@ class Tuner:
         for _ in range(rounds):
             a_eps = np.mean([self.propose_pair(eps, k) for k in range(window)], axis=0)
             hist.append((eps, a_eps[0], a_eps[1]))
-            eps = eps * grow if a_eps[1] ** 2 <= 2.0 * a_eps[0] else eps / grow
+            eps = eps * grow if (a_eps[0] > 0.0 and a_eps[1] ** 2 <= 2.0 * a_eps[0]) else eps / grow
         return eps, hist
 
     def propose_pair(self, eps, _k):

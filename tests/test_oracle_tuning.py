@@ -56,3 +56,39 @@ def test_esjd_peaks_near_half_period():
         assert v < ref + 0.2 * nmodes, (n, v, ref)
     assert esjd[10] > 0.7 * nmodes * 2 * (1 - np.cos(w_eff * eps * 10))
     assert n_max == 10
+
+
+def test_step_size_shrinks_when_nothing_is_accepted():
+    # Eq. (acc_ineq) is vacuous when neither size is ever accepted (0 <= 0): eps must shrink.
+    # A step far above the leapfrog stability limit of the Gaussian target (omega eps >> 2) gives
+    # dH ~ exp(huge), never accepted.
+    p, phi, sig = gaussian_setup()
+    tu = tuning.Tuner(p, phi, sig, noise_for(p, 4))
+    eps, hist = tu.tune_eps(40.0, rounds=2, window=4)
+    assert all(h[1] == 0.0 and h[2] == 0.0 for h in hist)
+    assert abs(eps - 40.0 / 1.2 ** 2) < 1e-12
+
+
+def test_centered_metric_estimate_removes_the_batch_mean():
+    # Samples phi_s = mu + Gaussian field with Fourier variance sigma: the centered estimate
+    # approaches sigma on every mode (the mean enters only the zero mode, as V |mu|^2 in the
+    # uncentered moment of Eq. covest); with mu = 0 the two estimates differ by |F phi-bar|^2,
+    # which is O(sigma / S).
+    from oracle import hmc
+    p, _, sig = gaussian_setup(L=4, Nt=4)
+    rng = np.random.default_rng(5)
+    S = 4000
+    mu = np.array([0.3, -0.2, 2.5])[:, None, None, None]
+    samples = []
+    for _ in range(S):
+        z = rng.standard_normal(sig.shape)
+        f = np.fft.ifftn(np.fft.fftn(z, axes=(1, 2, 3), norm="ortho") * np.sqrt(sig), axes=(1, 2, 3),
+                         norm="ortho").real
+        samples.append(f + mu)
+    c = hmc.sigma_estimate_centered(samples)
+    u = hmc.sigma_estimate(samples)
+    V = sig[0].size
+    assert np.abs(c / sig - 1).max() < 0.15
+    assert abs(u[2, 0, 0, 0] - (sig[2, 0, 0, 0] + V * 2.5 ** 2)) < 0.05 * V * 2.5 ** 2
+    zero = [s - mu for s in samples[:50]]
+    assert np.abs(hmc.sigma_estimate_centered(zero) - hmc.sigma_estimate(zero)).max() < 5 * sig.max()
