@@ -1,13 +1,18 @@
 """Benchmark: HMC trajectories per second for the pseudofermion HMC of the O(3) spin-fermion
-model on an 80 x 80 x 160 lattice (dtau = 0.1), 8 pseudofermion right-hand sides per chain,
-n_leap = 40, mixed-precision preconditioned CG (FP32 inner, FP64 reliable updates, tolerance
-1e-10 on the FP64 true residual), one chain per GPU.
+model on an 80 x 80 x 160 lattice (dtau = 0.1), Yukawa coupling lambda = 1 in D's on-site term,
+8 pseudofermion right-hand sides per chain, n_leap = 40, complex64 CG with FP64 reliable updates
+(tolerance 1e-10 on the FP64 true residual), one chain per GPU.
+
+Before the timed region the chain is thermalised and its HMC hyperparameters are tuned as the
+paper's warm-up does: the start is an ordered field (the mean-field amplitude along one component
+plus free-boson fluctuations), N_THERM trajectories at a small step with the free-boson metric,
+sigma-hat from Eq. (covest) over the last N_COVEST of them, then eps by Eq. (acc_ineq). The timed
+trajectories use the tuned sigma-hat and eps.
 
 A step is one full trajectory (heatbath, momentum draw, 41 force evaluations, Metropolis).
-The line also reports the fused A = D D^dagger matvec (complex64, 8 RHS) against the
-measured HBM copy bandwidth, one solve in FP64 vs mixed precision at equal true residual,
-the trajectory measured end to end from host buffers, and the FP64 oracle's throughput on
-the host cores.
+The line also reports the fused A = D D^dagger matvec (complex64, 8 RHS) against the measured
+HBM copy bandwidth, one solve in FP64 vs mixed precision at equal true residual, the trajectory
+measured end to end from host buffers, and the FP64 oracle's throughput on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Multi-GPU (replicas, weak scaling): torchrun --nproc-per-node N bench.py --gpus N ...
@@ -27,25 +32,41 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "HMC traj/s and M†M matvec GB/s at 80×80; mixed vs FP64 at equal CG residual"
-L, NT, NRHS, NLEAP, EPS, TOL, MAXIT = 80, 160, 8, 40, 0.01, 1e-10, 20000
+L, NT, NRHS, NLEAP, TOL, MAXIT = 80, 160, 8, 40, 1e-10, 20000
 GUESS = 4   # force solves start from the degree-4 extrapolation of the previous solutions (same stopping test)
-# Yukawa coupling lambda = 1 in the paper's convention g / sqrt(N_f): with k pseudofermion fields
-# (N_f = 2k) the on-site coefficient of D is lambda * sqrt(2 / N_f) = lambda / sqrt(k)
-LAMBDA = 1.0
-COUPLINGS = dict(dtau=0.1, t_h=(1.0, 0.5), t_v=(0.5, 1.0), mu=(-0.5, -0.5), g=LAMBDA / NRHS ** 0.5, r=0.5,
-                 u=1.0, c=3.0)
-WORKLOAD = (f"L={L}x{L}, Nt={NT} (dtau=0.1), 2 bands x 2 spins, {NRHS} pseudofermion RHS (N_f={2 * NRHS}, "
-            f"Yukawa lambda={LAMBDA} as g/sqrt(N_f): D coefficient {LAMBDA / NRHS ** 0.5:.4f}), n_leap={NLEAP}, "
-            f"eps={EPS}, complex64 PCG with FP64 reliable updates to true residual {TOL}, "
-            "degree-4 chronological initial guess, phi = free-boson-spectrum Gaussian field, sigma-hat = its spectrum")
+LAMBDA = 1.0   # Yukawa coupling: D's on-site term is dtau * LAMBDA * (-1)^(x+y) phi.sigma sigma^x
+COUPLINGS = dict(dtau=0.1, t_h=(1.0, 0.5), t_v=(0.5, 1.0), mu=(-0.5, -0.5), g=LAMBDA, r=0.5, u=1.0, c=3.0)
+# Ordered start: the uniform amplitude that minimises S_B - 8 log det(D D^dagger) over uniform
+# fields of this lattice (mean field for eight right-hand sides), plus free-boson fluctuations.
+AMP = 2.8
+EPS0 = 0.01                 # thermalisation step
+# Eq. (covest) about the batch mean: the ordered chain keeps its condensate over the warm-up, and
+# the uncentered moment would book V |phi-bar|^2 on the zero mode as a fluctuation (a leapfrog
+# frequency ~ 4500 for that mode, far past any usable step)
+SIGMA_CENTERED = True
+N_THERM, N_COVEST = 12, 8   # thermalisation trajectories; the last N_COVEST feed Eq. (covest)
+# Eq. (acc_ineq): rounds of TUNE_WINDOW single-step proposals at eps and eps/2, eps scaled by
+# TUNE_GROW each round, until it has turned TUNE_TURNS times (at most TUNE_ROUNDS rounds)
+TUNE_ROUNDS, TUNE_WINDOW, TUNE_GROW, TUNE_TURNS = 24, 2, 1.5, 2
+# Solver: plain CG. On this ordered workload the fermions are gapped and the preconditioner of
+# Eq. (precon), exact for the free Fermi surface, saves few iterations (69 against 58 per solve
+# measured on GB300) while each preconditioned iteration streams about 1.4x the bytes.
+PRECOND = False
+WORKLOAD_BASE = (f"L={L}x{L}, Nt={NT} (dtau=0.1), 2 bands x 2 spins, {NRHS} pseudofermion RHS (N_f={2 * NRHS}), "
+                 f"Yukawa lambda={LAMBDA} (D coefficient dtau*lambda), n_leap={NLEAP}, "
+                 f"complex64 {'PCG' if PRECOND else 'CG'} with FP64 reliable updates to true residual {TOL}, "
+                 f"degree-{GUESS} chronological initial guess; start: ordered field (amplitude {AMP} on one "
+                 f"component + free-boson fluctuations), {N_THERM} thermalisation trajectories at eps={EPS0}, "
+                 f"sigma-hat from Eq. (covest){' about the batch mean' if SIGMA_CENTERED else ''} over the last "
+                 f"{N_COVEST}, eps by Eq. (acc_ineq)")
 # DRAM bytes (read + write) of one launch of the roofline kernel, the plain fused A on 8 RHS at
-# 80x80x160, from one ncu capture of `bench.py --profile-matvec 3`; set to None when that kernel
-# changes until it is captured again.
-ROOFLINE_TRAFFIC_BYTES = 550_630_144
-# PCG iterations per solve of this workload with the degree-4 chronological start (20.3 measured
-# on a GB300), used only to scale the oracle's timed sample (a few PCG iterations) to a
-# trajectory when no GPU run is available in the process.
-ITERS_PER_SOLVE_DEFAULT = 21
+# 80x80x160, from one ncu capture of `bench.py --profile-matvec 3`; None until that kernel has
+# been captured.
+ROOFLINE_TRAFFIC_BYTES = None
+# CG iterations per solve of this workload with the degree-4 chronological start, used only to
+# scale the oracle's timed sample (a few iterations) to a trajectory when no GPU run is available
+# in the process.
+ITERS_PER_SOLVE_DEFAULT = 40
 
 
 def kt():
@@ -53,10 +74,11 @@ def kt():
 
 
 def synthetic_inputs(seed):
-    """phi: Gaussian field with the free-boson spectrum 1/(dtau B(k)); sigma-hat: that spectrum."""
+    """phi: the ordered start (AMP on component 3 plus a Gaussian field with the free-boson
+    spectrum 1/(dtau B(k))); sigma-hat: that spectrum (the thermalisation metric)."""
     from paper_2204_14241_gb300 import inputs as I
     dt = COUPLINGS["dtau"]
-    phi = I.smooth_field(seed, L, NT, COUPLINGS["r"], kt()) / np.sqrt(dt)
+    phi = I.ordered_field(seed, L, NT, COUPLINGS["r"], kt(), 1.0 / np.sqrt(dt), AMP)
     sig = np.broadcast_to(I.spectrum(L, NT, COUPLINGS["r"], kt())[None] / dt, (3, NT, L, L)).copy()
     return phi, sig
 
@@ -154,8 +176,9 @@ _ORACLE_INPUTS = {}
 
 
 def oracle_iteration_time(n_iter=2):
-    """Seconds per PCG iteration of the FP64 oracle on the full lattice, one right-hand side.
-    Returns (seconds per iteration, threads used)."""
+    """Seconds per solver iteration of the FP64 oracle on the full lattice, one right-hand side:
+    one A apply, the preconditioner when the workload uses it, the vector updates and the dot
+    products. Returns (seconds per iteration, threads used)."""
     from oracle.model import Params
     from oracle import solver, fermion
     from paper_2204_14241_gb300 import inputs as I
@@ -165,14 +188,16 @@ def oracle_iteration_time(n_iter=2):
         _ORACLE_INPUTS["b"] = I.to_paper_fermion(I.fermion_noise(2, 1, L, NT)[0])
     P = Params(L=L, Nt=NT, **COUPLINGS)
     phi_o, b = _ORACLE_INPUTS["phi"], _ORACLE_INPUTS["b"]
-    # one PCG iteration = one A apply + one preconditioner apply + vector updates
-    x = b.copy()
+    x, r, pdir = np.zeros_like(b), b.copy(), b.copy()
     t0 = time.perf_counter()
     for _ in range(n_iter):
-        q = fermion.apply_A(P, phi_o, x)
-        z = solver.apply_precond(P, q)
-        x = x + 1e-3 * z - 1e-3 * q
-        solver.vdot(q, z)
+        q = fermion.apply_A(P, phi_o, pdir)
+        a = solver.vdot(r, r).real / solver.vdot(pdir, q).real
+        x = x + a * pdir
+        r = r - a * q
+        z = solver.apply_precond(P, r) if PRECOND else r
+        pdir = z + 0.5 * pdir
+        solver.vdot(r, z)
     dt = (time.perf_counter() - t0) / n_iter
     return dt, 1
 
@@ -181,6 +206,10 @@ def oracle_traj_per_s(iters_per_solve, n_iter=2):
     t_it, threads = oracle_iteration_time(n_iter)
     t_traj = (NLEAP + 1) * NRHS * iters_per_solve * t_it
     return 1.0 / t_traj, t_it, threads
+
+
+def solver_name():
+    return "PCG" if PRECOND else "CG"
 
 
 def run_reference(args):
@@ -195,13 +224,13 @@ def run_reference(args):
         vals.append(v)
     wall = time.perf_counter() - t0
     value = float(np.mean(vals))
-    sample = (f"per step: 1 PCG iteration of the FP64 numpy oracle (A apply + preconditioner + updates) on one RHS "
+    sample = (f"per step: 1 {solver_name()} iteration of the FP64 numpy oracle (A apply + updates) on one RHS "
               f"at {L}x{L}x{NT}, scaled to a trajectory as {NLEAP + 1} solves x {NRHS} RHS x "
               f"{ITERS_PER_SOLVE_DEFAULT} iterations per solve")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "traj/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "data": "synthetic", "config": {"workload": WORKLOAD_BASE},
             "cpu_baseline": {"value": value, "unit": "traj/s", "cores": threads, "kind": "oracle",
                              "sample": sample, "host_cpus": os.cpu_count()},
             "e2e": {"value": value, "unit": "traj/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -245,15 +274,31 @@ def run_ours(args):
                   **COUPLINGS)
     st = ctx.stream
 
-    # warm-up trajectories; they also accumulate the metric estimate of Eq. (covest)
-    acc = torch.zeros_like(sig)
-    from paper_2204_14241_gb300.hmc import METRIC_ACCUM
+    # warm-up as in the paper (Sections "Online metric estimation" and "Online HMC hyperparameter
+    # tuning"): thermalisation with the free-boson metric, sigma-hat by Eq. (covest) over the last
+    # N_COVEST states, then eps by Eq. (acc_ineq); none of it is timed
+    from paper_2204_14241_gb300.tuning import SigmaEstimator, Tuner
+    t_w0 = time.perf_counter()
+    est = SigmaEstimator(ctx, sig, centered=SIGMA_CENTERED)
+    therm = []
+    for w in range(N_THERM):
+        o = ctx.trajectory([phi], [sig], EPS0, NLEAP, nrhs=NRHS, precond=PRECOND, seed=seed, counter=w, check=False)
+        therm.append(o)
+        if w >= N_THERM - N_COVEST:
+            est.add(phi)
+    sig_free = sig.clone()
+    sig = est.value()
+    sigma_ratio = (sig / sig_free)
+    tuner = Tuner(ctx, phi, sig, nrhs=NRHS, precond=PRECOND, seed=seed + 1)
+    eps, eps_hist = tuner.tune_eps(EPS0, TUNE_ROUNDS, TUNE_WINDOW, grow=TUNE_GROW, stop_after_turns=TUNE_TURNS)
     warm = []
     for w in range(args.warmup):
-        o = ctx.trajectory([phi], [sig], EPS, NLEAP, nrhs=NRHS, precond=True, seed=seed, counter=w, check=False)
-        ctx.metric(METRIC_ACCUM, sig, phi, out=acc)
+        o = ctx.trajectory([phi], [sig], eps, NLEAP, nrhs=NRHS, precond=PRECOND, seed=seed, counter=500 + w,
+                           check=False)
         warm.append(o)
-    sigma_ratio = float((acc / max(args.warmup, 1) / sig).mean().item()) if args.warmup else None
+    t_warm = time.perf_counter() - t_w0
+    sig_np = sig.cpu().numpy()
+    workload = WORKLOAD_BASE + f"; tuned eps={eps:.4g}"
 
     # timed trajectories. Each step: H2D copy of the step's inputs (phi, sigma-hat) from pinned
     # host memory, the trajectory (CUDA events around it give the device-resident value), D2H
@@ -274,7 +319,7 @@ def run_ours(args):
         phi.copy_(h_phi, non_blocking=True)
         sig.copy_(h_sig, non_blocking=True)
         e0.record(st)
-        o = ctx.trajectory([phi], [sig], EPS, NLEAP, nrhs=NRHS, precond=True, seed=seed, counter=1000 + k,
+        o = ctx.trajectory([phi], [sig], eps, NLEAP, nrhs=NRHS, precond=PRECOND, seed=seed, counter=1000 + k,
                            check=False)
         e1.record(st)
         h_out.copy_(phi, non_blocking=True)
@@ -317,42 +362,59 @@ def run_ours(args):
     for mode in ("mixed", "fp64"):
         c2 = ctx if mode == "mixed" else Context(L, NT, solver="fp64", nrhs_max=NRHS, cg_tol=TOL, cg_maxit=MAXIT,
                                                    device=dev, **COUPLINGS)
-        c2.cg_solve(phi, b, precond=True, maxit=16, raise_on_noconv=False)   # warm (first launches)
+        c2.cg_solve(phi, b, precond=PRECOND, maxit=16, raise_on_noconv=False)   # warm (first launches)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, s = c2.cg_solve(phi, b, precond=True, raise_on_noconv=False)
+        _, s = c2.cg_solve(phi, b, precond=PRECOND, raise_on_noconv=False)
         torch.cuda.synchronize()
         solve[mode] = {"seconds": time.perf_counter() - t0, "iterations": s["iterations"],
                        "true_rel_resid": s["true_rel_resid"], "reliable_updates": s["reliable_updates"]}
         if c2 is not ctx:
             c2.close()
 
+    # FP64 arithmetic peak of this GPU's CUDA cores (the roofline of the FP64 operator passes of the
+    # reliable updates and of the force), measured by the library's FMA-chain kernel
+    from paper_2204_14241_gb300.hmc import fma_peak, FP64
+    fp64_peak = fma_peak(FP64, dev) / 1e12
+
     if rank == 0:
         cpu = None
         if ws == 1 and not args.no_cpu_baseline:
             v, t_it, threads = oracle_traj_per_s(iters_per_solve, 2)
             cpu = {"value": v, "unit": "traj/s", "cores": threads, "kind": "oracle", "host_cpus": os.cpu_count(),
-                   "sample": (f"2 PCG iterations of the FP64 numpy oracle on one RHS at {L}x{L}x{NT} "
+                   "sample": (f"2 {solver_name()} iterations of the FP64 numpy oracle on one RHS at {L}x{L}x{NT} "
                               f"({t_it:.2f} s each), scaled to a trajectory as {NLEAP + 1} solves x {NRHS} RHS x "
                               f"{iters_per_solve:.0f} iterations per solve (the GPU run's count)")}
+        acc_rate = float(np.mean([bool(o["accepted"][0]) for o in outs]))
+        sr = sigma_ratio.flatten()
         line = {"metric": METRIC, "value": value, "unit": "traj/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (8 x 33 MB fermion fields + "
+                "config": {"workload": workload, "l2": "inputs larger than L2 (8 x 33 MB fermion fields + "
                            "workspace per solve; matvec timed on 537 MB in/out)", "parallelism": f"replicas x{ws}"},
                 "matvec_gbs": achieved,
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": ROOFLINE_TRAFFIC_BYTES,
-                             "kernel": "k_apply_A4<16, 16> (plain FP32 A = D D^dagger)",
+                             "kernel": "k_apply_A_strip<80> (complex64 A = D D^dagger, 8 RHS)",
                              "peak_source": peak_src, "algorithmic_bytes": mv_bytes,
                              "launch_us": t_mv * 1e6},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-                "hmc": {"accept": [bool(o["accepted"][0]) for o in outs], "dH": [o["dH"][0] for o in outs],
-                        "status": [o["status"] for o in outs],
-                        "warmup_dH": [o["dH"][0] for o in warm], "warmup_status": [o["status"] for o in warm],
+                "hmc": {"acceptance_rate": acc_rate, "eps": eps, "n_leap": NLEAP, "solver": solver_name(),
                         "cg_iters_per_solve": iters_per_solve,
+                        "accept": [bool(o["accepted"][0]) for o in outs], "dH": [o["dH"][0] for o in outs],
+                        "status": [o["status"] for o in outs],
                         "max_true_resid": max(o["max_true_resid"][0] for o in outs),
-                        "sigma_estimate_over_used": sigma_ratio},
+                        "phi_mean_component3": float(phi[2].mean().item()),
+                        "thermalisation": {"trajectories": N_THERM, "eps": EPS0,
+                                           "dH": [o["dH"][0] for o in therm], "status": [o["status"] for o in therm],
+                                           "cg_iters_per_solve": [o["cg_iterations"][0] / (NLEAP + 1) for o in therm]},
+                        "sigma_hat_over_free_spectrum": {"median": float(sr.median().item()),
+                                                          "mean": float(sr.mean().item()),
+                                                          "max": float(sr.max().item())},
+                        "eps_tuning": [list(h) for h in eps_hist],
+                        "warmup_dH": [o["dH"][0] for o in warm], "warmup_status": [o["status"] for o in warm],
+                        "untimed_warmup_seconds": t_warm},
+                "fp64_fma_peak_tflops": fp64_peak,
                 "solve_mixed_vs_fp64": solve}
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -362,8 +424,8 @@ def run_ours(args):
 
 
 def run_profile_solve(args):
-    """A capture-sized sample of the workload for ncu: on the full lattice, one 8-RHS
-    preconditioned solve cut at a fixed iteration count, run twice (the second is the one to
+    """A capture-sized sample of the workload for ncu: on the full lattice, one 8-RHS solve of
+    the workload's solver cut at a fixed iteration count, run twice (the second is the one to
     capture), plus one fused A apply. Prints the solve statistics."""
     import torch
     from paper_2204_14241_gb300.hmc import Context
@@ -375,7 +437,7 @@ def run_profile_solve(args):
     for rep in range(2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, st = ctx.cg_solve(phi, b, precond=True, maxit=args.profile_solve, raise_on_noconv=False)
+        _, st = ctx.cg_solve(phi, b, precond=PRECOND, maxit=args.profile_solve, raise_on_noconv=False)
         torch.cuda.synchronize()
         print(json.dumps({"profile_solve": args.profile_solve, "seconds": time.perf_counter() - t0, **st}))
     x = b.to(torch.complex64)
@@ -400,7 +462,8 @@ def run_profile_trajectory(args):
         n0 = ctx.launches()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        o = ctx.trajectory([phi], [sig], EPS, NLEAP, nrhs=NRHS, precond=True, seed=args.seed, counter=rep, check=False)
+        o = ctx.trajectory([phi], [sig], EPS0, NLEAP, nrhs=NRHS, precond=PRECOND, seed=args.seed, counter=rep,
+                           check=False)
         torch.cuda.synchronize()
         if rep == 1:
             torch.cuda.nvtx.range_pop()

@@ -42,7 +42,7 @@ enum hmc_status {
     HMC_ERR_ARG = 1,        /* bad size, chain index, null pointer, or misaligned pointer */
     HMC_ERR_NOCONV = 2,     /* CG hit maxit; x holds the last iterate, stats the true residual */
     HMC_ERR_NONFINITE = 3,  /* NaN or Inf seen in a residual norm or an energy */
-    HMC_ERR_TIMEOUT = 4,    /* reserved for bounded device-side waits that gave up */
+    HMC_ERR_TIMEOUT = 4,    /* a bounded device-side wait gave up (the work of that launch is incomplete) */
     HMC_ERR_CUDA = 5,       /* a CUDA runtime call failed; see hmc_last_error */
     HMC_ERR_STATE = 6       /* call not valid in the context's current state */
 };
@@ -84,6 +84,10 @@ typedef struct {
                            reduction order, hence every bit of the results, is reproducible);
                            1: on first use per (L, Nt, nrhs, precision) time the valid tile and
                            time-chunk shapes on the call's own buffers and keep the fastest */
+    int wait_spin_limit;   /* polls of a device-side wait before it gives up (0: 1 << 20); a wait
+                              that gives up makes the call return HMC_ERR_TIMEOUT */
+    int test_wait_timeout; /* nonzero (tests only): the first device-side wait of every fused-A
+                              launch targets a barrier that is never armed, so it always gives up */
 } hmc_params;
 
 /* Per-chain lattice (batched chains of uneven sizes). Coupling constants other than r
@@ -233,9 +237,43 @@ typedef struct {
  * failed or an energy is not finite (phi is then restored to its input value). */
 int trajectory(hmc_ctx* ctx, const hmc_traj_in* in, hmc_traj_out* out);
 
+/* Per-solve and per-phase record of a chain's last trajectory (tracing, per-trajectory logs).
+ * Phases (GPU time from CUDA events on the context's stream, milliseconds):
+ *   phase_ms[0] the force solves (CG/PCG with reliable updates and chronological starts),
+ *   phase_ms[1] the force kernel (D^dagger X contraction and boson force) and action reductions,
+ *   phase_ms[2] the metric FFTs (momentum draw, drift, kinetic energy),
+ *   phase_ms[3] everything else (heatbath, noise, kicks, energies). */
+#define HMC_MAX_SOLVES 256
+typedef struct {
+    int n_solves;                       /* force solves in the trajectory (entries past HMC_MAX_SOLVES are not kept) */
+    int reliable_updates;               /* FP64 true-residual evaluations over all solves */
+    int iterations[HMC_MAX_SOLVES];     /* inner iterations of each solve (slowest right-hand side) */
+    double true_resid[HMC_MAX_SOLVES];  /* final FP64 true relative residual of each solve (worst right-hand side) */
+    double phase_ms[4];
+} hmc_traj_stats;
+
+/* Copies the record of the last trajectory() of `chain` into *out (host). Errors: HMC_ERR_ARG;
+ * HMC_ERR_STATE if the chain has not run a trajectory. */
+int hmc_trajectory_stats(const hmc_ctx* ctx, int chain, hmc_traj_stats* out);
+
 /* Tracing: *kernel_launches receives the number of kernels this context has launched since
  * hmc_init (host-side count, no synchronisation). */
 int hmc_counters(const hmc_ctx* ctx, int64_t* kernel_launches);
+
+/* Measured arithmetic peak of the current device's CUDA cores, in flop/s (an FMA counts two):
+ * dependent fused multiply-add chains in FP64 (prec = HMC_FP64) or FP32 (HMC_FP32), 8 chains
+ * per thread, 8 blocks of 256 threads per SM, best of four timed launches on a private stream.
+ * The roofline denominator of FP64-bound kernels. Allocates and frees a small scratch buffer;
+ * not for use inside stream capture. Errors: HMC_ERR_ARG, HMC_ERR_CUDA. */
+int hmc_fma_peak(int prec, double* flop_per_s);
+
+/* Index checks of a library built with -DHMC_BOUNDS: the operator, force and strip kernels check
+ * their global and shared-memory indices, record a failed check in a device error word and skip
+ * the access (no trap). *word receives the OR of the codes recorded since the last call (1: D
+ * operator, 2: force, 4: strip kernel global access, 8: strip kernel shared access) and clears
+ * them; *enabled (may be NULL) is 1 in the bounds build. In the normal build *word is 0 and the
+ * checks compile to nothing. Synchronises the device. */
+int hmc_bounds_status(unsigned int* word, int* enabled);
 
 /* Counter-based random numbers used by HMC_NOISE_PHILOX: Philox4x32-10 (Salmon, Moraes,
  * Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11).

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhmc.so")
-SOURCES = ["stencil.cu", "cg.cu", "fft.cu", "fft_ct.cu", "hmc.cu"]
+SOURCES = ["stencil.cu", "cg.cu", "fft.cu", "fft_ct.cu", "hmc.cu", "peak.cu", "strip.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -29,13 +29,18 @@ def flags(extra=()):
                    "-I", CSRC, "--expt-relaxed-constexpr"] + list(extra)
 
 
-def build(verbose=False, extra=()):
-    """Compile every source (in parallel) and link libhmc.so; returns the library path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose=False, extra=(), variant=""):
+    """Compile every source (in parallel) and link libhmc{variant}.so; returns the library path.
+    variant="_bounds" builds the index-checking library (-DHMC_BOUNDS) beside the normal one."""
+    build_dir = BUILD + variant
+    lib_path = os.path.join(HERE, f"libhmc{variant}.so")
+    if variant == "_bounds":
+        extra = tuple(extra) + ("-DHMC_BOUNDS",)
+    os.makedirs(build_dir, exist_ok=True)
     procs = []
     objs = []
     for src in SOURCES:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(build_dir, src.replace(".cu", ".o"))
         objs.append(obj)
         cmd = [nvcc()] + flags(extra) + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
@@ -52,17 +57,17 @@ def build(verbose=False, extra=()):
     if failed:
         msg = "\n".join(f"--- {s}\n{t}" for s, t in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
-    tmp = LIB + ".tmp"
+    tmp = lib_path + ".tmp"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    build(verbose="-v" in sys.argv, extra=[a for a in sys.argv[1:] if a != "-v"])
-    print(LIB)
+    args = [a for a in sys.argv[1:] if a not in ("-v", "--bounds")]
+    print(build(verbose="-v" in sys.argv, extra=args, variant="_bounds" if "--bounds" in sys.argv else ""))

@@ -358,8 +358,17 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
             }
         }
         if (!xy) {
-        // p = z + beta p (fused into the operator), q = A p, partial <p, A p>
-        if ((rc = launch_apply_A<R>(ctx, lat, phiR, zv, qv, nrhs, part, &nb, cgs, pv, pw))) return rc;
+        if (kMixed && strip_supported(lat)) {
+            // p = z + beta p as a streaming pass, then q = A p on the complex64 strip kernel (the
+            // operator with the update folded in has no strip form: it would stage two vectors)
+            k_pupd<<<vgrid, 256, 0, sm>>>(reinterpret_cast<float4*>(pw), reinterpret_cast<const float4*>(zv),
+                                          reinterpret_cast<const float4*>(pv), n / 2, cgs);
+            HMC_LAUNCH(ctx, "k_pupd");
+            if ((rc = launch_apply_A<R>(ctx, lat, phiR, pw, qv, nrhs, part, &nb, cgs))) return rc;
+        } else {
+            // p = z + beta p (fused into the operator), q = A p, partial <p, A p>
+            if ((rc = launch_apply_A<R>(ctx, lat, phiR, zv, qv, nrhs, part, &nb, cgs, pv, pw))) return rc;
+        }
         { C* t = pv; pv = pw; pw = t; }
         k_cg_alpha<<<nrhs, 256, 0, sm>>>(cgs, part, nb);
         HMC_LAUNCH(ctx, "k_cg_alpha");
@@ -380,7 +389,7 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
         ++it;
         if (it % check_every == 0 || it >= maxit) {
             HMC_CUDA(ctx, cudaMemcpyAsync(ctx->h_cg, cgs, nrhs * sizeof(CgScalars), cudaMemcpyDeviceToHost, sm));
-            HMC_CUDA(ctx, cudaStreamSynchronize(sm));
+            if ((rc = check_device_flags(ctx))) return rc;   // synchronises the stream
             bool any_ru = false, any_active = false;
             for (int k = 0; k < nrhs; ++k) {
                 if (ctx->h_cg[k].nonfinite) nonfinite = true;

@@ -131,6 +131,25 @@ __device__ __forceinline__ double block_sum(double v, double* smem) {
     return t;
 }
 
+// ---- index checks of the bounds build ----------------------------------------------------------
+// Built with -DHMC_BOUNDS, each translation unit has a device error word; a failed check ORs its
+// code into the word and the guarded access is skipped (never a trap). Otherwise the checks
+// compile to nothing. hmc_bounds_status() (hmc.h) reads and clears the words.
+#ifdef HMC_BOUNDS
+static __device__ unsigned int hmc_bounds_word;
+#define HMC_IN(cond, code) ((cond) ? true : (atomicOr(&hmc_bounds_word, (unsigned)(code)), false))
+static inline unsigned int bounds_take_tu() {
+    unsigned int w = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&w, hmc_bounds_word, sizeof(w)) != cudaSuccess) return 0x80000000u;
+    cudaMemcpyToSymbol(hmc_bounds_word, &z, sizeof(z));
+    return w;
+}
+#else
+#define HMC_IN(cond, code) true
+static inline unsigned int bounds_take_tu() { return 0; }
+#endif
+enum { kBndApplyD = 1, kBndForce = 2, kBndStripGlobal = 4, kBndStripShared = 8 };
+
 // ---- asynchronous global -> shared copies (cp.async) ------------------------------------------
 // 16-byte copies bypass L1 (.cg); both addresses 16-byte aligned. 4-byte copies go through L1.
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {

@@ -188,12 +188,24 @@ static void free_all(hmc_ctx* ctx) {
     void* ps[] = {ctx->d_r64, ctx->d_p64, ctx->d_p64b, ctx->d_p32b, ctx->d_q64, ctx->d_z64, ctx->d_X, ctx->d_pf, ctx->d_chi,
                   ctx->d_x32, ctx->d_r32, ctx->d_p32, ctx->d_q32, ctx->d_z32, ctx->d_phi32,
                   ctx->d_phi_save, ctx->d_pi, ctx->d_F, ctx->d_vel, ctx->d_z, ctx->d_fft,
-                  ctx->d_part, ctx->d_red, ctx->d_cg, ctx->d_u32};
+                  ctx->d_part, ctx->d_red, ctx->d_cg, ctx->d_u32, ctx->d_flags};
     for (void* p : ps)
         if (p) cudaFree(p);
+    for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
+    ctx->events.clear();
     if (ctx->h_cg) cudaFreeHost(ctx->h_cg);
     if (ctx->h_red) cudaFreeHost(ctx->h_red);
+    if (ctx->h_flags) cudaFreeHost(ctx->h_flags);
     free_plans(ctx);
+}
+
+int hmc::check_device_flags(hmc_ctx* ctx) {
+    HMC_CUDA(ctx, cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    HMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const int f = ctx->h_flags[0];
+    if (!f) return HMC_OK;
+    HMC_CUDA(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), ctx->stream));
+    return fail(ctx, HMC_ERR_TIMEOUT, std::string("a device-side wait gave up (flags ") + std::to_string(f) + ")");
 }
 
 // synchronise and copy `count` reduced scalars d_red[0..count) to host
@@ -247,6 +259,8 @@ int hmc_init(const hmc_params* p, int n_chains, const hmc_chain* chains, void* c
         ctx->chains.push_back(d);
         if (d.lat.V > ctx->vmax) ctx->vmax = d.lat.V;
     }
+    ctx->tstats.assign(n_chains, hmc_traj_stats{});
+    ctx->tstats_valid.assign(n_chains, 0);
     int dev = 0;
     int rc = HMC_OK;
     cudaError_t e = cudaGetDevice(&dev);
@@ -276,7 +290,8 @@ int hmc_init(const hmc_params* p, int n_chains, const hmc_chain* chains, void* c
         (rc = dalloc(ctx, &ctx->d_pi, nb)) || (rc = dalloc(ctx, &ctx->d_F, nb)) || (rc = dalloc(ctx, &ctx->d_vel, nb)) ||
         (rc = dalloc(ctx, &ctx->d_z, nb)) || (rc = dalloc(ctx, &ctx->d_fft, nb)) ||
         (rc = dalloc(ctx, &ctx->d_part, ctx->part_cap)) || (rc = dalloc(ctx, &ctx->d_red, 64)) ||
-        (rc = dalloc(ctx, &ctx->d_cg, ctx->kmax)) || (rc = dalloc(ctx, &ctx->d_u32, 4))) {
+        (rc = dalloc(ctx, &ctx->d_cg, ctx->kmax)) || (rc = dalloc(ctx, &ctx->d_u32, 4)) ||
+        (rc = dalloc(ctx, &ctx->d_flags, 16))) {
         std::string m = ctx->err;
         free_all(ctx);
         delete ctx;
@@ -284,6 +299,9 @@ int hmc_init(const hmc_params* p, int n_chains, const hmc_chain* chains, void* c
     }
     e = cudaMallocHost((void**)&ctx->h_cg, ctx->kmax * sizeof(CgScalars));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_red, 64 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_flags, 16 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->d_flags, 0, 16 * sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         rc = cuda_check(nullptr, e, "hmc_init: pinned host buffers");
         free_all(ctx);
@@ -335,7 +353,8 @@ int apply_MdagM(hmc_ctx* ctx, int chain, int prec, const void* phi, const void* 
     else return fail(ctx, HMC_ERR_ARG, "apply_MdagM: unknown precision");
     if (rc || !norm2) return rc;
     if ((rc = reduce_rows(ctx, part, nrhs, nb, ctx->d_red))) return rc;
-    return fetch_red(ctx, nrhs, norm2);
+    if ((rc = fetch_red(ctx, nrhs, norm2))) return rc;
+    return check_device_flags(ctx);
 }
 
 int apply_precond(hmc_ctx* ctx, int chain, int prec, const void* x, void* y, int nrhs) {
@@ -361,14 +380,47 @@ int cg_solve(hmc_ctx* ctx, int chain, const void* phi, const void* b, void* x, i
 
 }  // extern "C"
 
+// Per-phase GPU time of one trajectory: an event is recorded on the context's stream at every
+// phase boundary, and after the trajectory's final synchronisation the time between consecutive
+// events is added to the phase that started at the first of them.
+struct PhaseTimer {
+    hmc_ctx* ctx;
+    std::vector<std::pair<int, int>> marks;   // (event index, phase starting there)
+    explicit PhaseTimer(hmc_ctx* c) : ctx(c) {}
+    int mark(int phase) {
+        const int i = (int)marks.size();
+        if (i >= (int)ctx->events.size()) {
+            cudaEvent_t e;
+            HMC_CUDA(ctx, cudaEventCreate(&e));
+            ctx->events.push_back(e);
+        }
+        HMC_CUDA(ctx, cudaEventRecord(ctx->events[i], ctx->stream));
+        marks.emplace_back(i, phase);
+        return HMC_OK;
+    }
+    // call after the stream has been synchronised
+    void collect(double ms[4]) {
+        for (int q = 0; q < 4; ++q) ms[q] = 0.0;
+        for (size_t j = 0; j + 1 < marks.size(); ++j) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, ctx->events[marks[j].first], ctx->events[marks[j + 1].first]) == cudaSuccess)
+                ms[marks[j].second] += t;
+        }
+    }
+};
+enum { kPhaseSolve = 0, kPhaseForce = 1, kPhaseMetric = 2, kPhaseOther = 3 };
+
 // F, S_pf and S_b at phi for the pseudofermions pf; X receives A^{-1} pf (starting from the
 // contents of X when use_x0).
 static int force_impl(hmc_ctx* ctx, int chain, const double* phi, const double2* pf, int nrhs, double* F,
                       int include_boson, int precond, double* s_pf, double* s_b, hmc_cg_stats* st,
-                      double2* X, bool use_x0) {
+                      double2* X, bool use_x0, PhaseTimer* tm = nullptr) {
     const ChainDesc& ch = ctx->chains[chain];
-    int rc = cg_run(ctx, chain, phi, pf, X, nrhs, ctx->p.cg_tol, ctx->p.cg_maxit, precond, st, use_x0);
+    int rc;
+    if (tm && (rc = tm->mark(kPhaseSolve))) return rc;
+    rc = cg_run(ctx, chain, phi, pf, X, nrhs, ctx->p.cg_tol, ctx->p.cg_maxit, precond, st, use_x0);
     if (rc) return rc;
+    if (tm && (rc = tm->mark(kPhaseForce))) return rc;
     int nb = 0;
     if ((rc = launch_force(ctx, ch.lat, ch.r, phi, X, pf, nrhs, F, include_boson, ctx->d_part, &nb))) return rc;
     if (!s_pf && !s_b) return HMC_OK;
@@ -473,6 +525,11 @@ static int run_chain(hmc_ctx* ctx, int c, const hmc_traj_in* in, double out_e[6]
     const double* sig = (const double*)in->sigma_hat[c];
     cudaStream_t sm = ctx->stream;
     int rc;
+    PhaseTimer tm(ctx);
+    hmc_traj_stats& ts = ctx->tstats[c];
+    ts = hmc_traj_stats{};
+    ctx->tstats_valid[c] = 0;
+    if ((rc = tm.mark(kPhaseOther))) return rc;
     HMC_CUDA(ctx, cudaMemcpyAsync(ctx->d_phi_save, phi, nb * sizeof(double), cudaMemcpyDeviceToDevice, sm));
 
     // noise
@@ -498,8 +555,10 @@ static int run_chain(hmc_ctx* ctx, int c, const hmc_traj_in* in, double out_e[6]
 
     // heatbath varphi = D chi, momentum, initial energies
     if ((rc = launch_apply_D<double>(ctx, lat, phi, chi, ctx->d_pf, 0, K))) return rc;
+    if ((rc = tm.mark(kPhaseMetric))) return rc;
     if ((rc = metric_op(ctx, lat, HMC_METRIC_MOMENTUM, sig, z, ctx->d_pi, 0.0, nullptr))) return rc;
     if ((rc = metric_op(ctx, lat, HMC_METRIC_KINETIC, sig, ctx->d_pi, nullptr, 0.0, ctx->d_red))) return rc;
+    if ((rc = tm.mark(kPhaseOther))) return rc;
     int nbb = 0;
     if ((rc = launch_boson(ctx, lat, ch.r, phi, nullptr, ctx->d_part, &nbb))) return rc;
     if ((rc = reduce_rows(ctx, ctx->d_part, 1, nbb, ctx->d_red + 1))) return rc;
@@ -552,7 +611,14 @@ static int run_chain(hmc_ctx* ctx, int c, const hmc_traj_in* in, double out_e[6]
             HMC_LAUNCH(ctx, "k_extrap");
         }
         int r2 = force_impl(ctx, c, phi, ctx->d_pf, K, ctx->d_F, 1, in->precond, want ? &s_pf : nullptr,
-                            want ? &s_b : nullptr, &st, xo, guess);
+                            want ? &s_b : nullptr, &st, xo, guess, &tm);
+        if (!r2) r2 = tm.mark(kPhaseOther);
+        if (ts.n_solves < HMC_MAX_SOLVES) {
+            ts.iterations[ts.n_solves] = st.iterations;
+            ts.true_resid[ts.n_solves] = st.true_rel_resid;
+        }
+        ts.n_solves += 1;
+        ts.reliable_updates += st.reliable_updates;
         if (guess) {
             for (int j = io; j > 0; --j) hist[j] = hist[j - 1];   // buffers past io keep their place
             hist[0] = xo;
@@ -567,6 +633,7 @@ static int run_chain(hmc_ctx* ctx, int c, const hmc_traj_in* in, double out_e[6]
         k_axpy<<<gb, 256, 0, sm>>>(0.5 * eps, ctx->d_F, ctx->d_pi, nb);
         HMC_LAUNCH(ctx, "k_axpy");
         for (int i = 1; i <= in->n_leap && !rc; ++i) {
+            if ((rc = tm.mark(kPhaseMetric))) break;
             if ((rc = metric_op(ctx, lat, HMC_METRIC_VELOCITY, sig, ctx->d_pi, phi, eps, nullptr))) break;
             if ((rc = do_force(i == in->n_leap))) break;
             k_axpy<<<gb, 256, 0, sm>>>(i < in->n_leap ? eps : 0.5 * eps, ctx->d_F, ctx->d_pi, nb);
@@ -574,7 +641,9 @@ static int run_chain(hmc_ctx* ctx, int c, const hmc_traj_in* in, double out_e[6]
         }
         if (in->n_leap == 0 && !rc) rc = do_force(true);
     }
+    if (!rc) rc = tm.mark(kPhaseMetric);
     if (!rc) rc = metric_op(ctx, lat, HMC_METRIC_KINETIC, sig, ctx->d_pi, nullptr, 0.0, ctx->d_red);
+    if (!rc) rc = tm.mark(kPhaseOther);
     double k1 = 0.0;
     if (!rc) rc = fetch_red(ctx, 1, &k1);
     if (!rc && jump2) {
@@ -603,7 +672,30 @@ static int run_chain(hmc_ctx* ctx, int c, const hmc_traj_in* in, double out_e[6]
     }
     *acc = u < std::exp(-h) ? 1 : 0;
     if (!*acc) HMC_CUDA(ctx, cudaMemcpyAsync(phi, ctx->d_phi_save, nb * sizeof(double), cudaMemcpyDeviceToDevice, sm));
+    if ((rc = tm.mark(kPhaseOther))) return rc;
     HMC_CUDA(ctx, cudaStreamSynchronize(sm));
+    tm.collect(ts.phase_ms);
+    ctx->tstats_valid[c] = 1;
+    return HMC_OK;
+}
+
+extern "C" int hmc_bounds_status(unsigned int* word, int* enabled) {
+    if (!word) return fail(nullptr, HMC_ERR_ARG, "hmc_bounds_status: null argument");
+#ifdef HMC_BOUNDS
+    if (enabled) *enabled = 1;
+#else
+    if (enabled) *enabled = 0;
+#endif
+    *word = bounds_take_stencil() | bounds_take_strip();
+    return HMC_OK;
+}
+
+extern "C" int hmc_trajectory_stats(const hmc_ctx* ctx, int chain, hmc_traj_stats* out) {
+    if (!ctx || !out) return fail(nullptr, HMC_ERR_ARG, "hmc_trajectory_stats: null argument");
+    if (chain < 0 || chain >= (int)ctx->chains.size())
+        return fail(nullptr, HMC_ERR_ARG, "hmc_trajectory_stats: chain index out of range");
+    if (!ctx->tstats_valid[chain]) return fail(nullptr, HMC_ERR_STATE, "hmc_trajectory_stats: no completed trajectory");
+    *out = ctx->tstats[chain];
     return HMC_OK;
 }
 

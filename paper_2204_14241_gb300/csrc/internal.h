@@ -75,6 +75,9 @@ struct hmc_ctx {
     std::vector<hmc::FftPlan> plans;
     std::vector<hmc::PcTables> pcs;
     std::vector<hmc::ATuned> atuned;   // tile shapes picked for the fused A kernel
+    std::vector<hmc_traj_stats> tstats;   // per chain: record of its last trajectory
+    std::vector<int> tstats_valid;
+    std::vector<cudaEvent_t> events;      // pool for the per-phase timing of trajectory()
 
     // fermion workspace (complex, K * 4 * vmax entries each)
     double2* d_r64 = nullptr;     // FP64 residual / true residual
@@ -110,6 +113,8 @@ struct hmc_ctx {
     hmc::CgScalars* h_cg = nullptr;   // pinned mirror
     double* h_red = nullptr;          // pinned, 64 doubles
     uint32_t* d_u32 = nullptr;        // 4 words scratch for uniforms
+    int* d_flags = nullptr;           // device error word [0]: bit 0 a bounded wait gave up, bit 1 its drain did too
+    int* h_flags = nullptr;           // pinned mirror
 
 };
 
@@ -173,6 +178,11 @@ template <typename R>
 int launch_apply_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x, cplx<R>* y,
                    int nrhs, double* part, int* nblk_out, const CgScalars* cgs = nullptr,
                    const cplx<R>* pold = nullptr, cplx<R>* pnew = nullptr);
+// strip.cu: the complex64 plain operator on full-height strips (L a multiple of 16 up to 80);
+// same contract as launch_apply_A without the direction update.
+bool strip_supported(const Lat& lat);
+int launch_apply_A_strip(hmc_ctx* ctx, const Lat& lat, const float* phi, const float2* x, float2* y, int nrhs,
+                         double* part, int* nblk_out, const CgScalars* cgs);
 // fermion (+ boson) force and the action pieces, see force() in hmc.h.
 int launch_force(hmc_ctx* ctx, const Lat& lat, double r, const double* phi, const double2* X,
                  const double2* pf, int nrhs, double* F, int include_boson, double* part,
@@ -215,6 +225,14 @@ int metric_op(hmc_ctx* ctx, const Lat& lat, int op, const double* sig, const dou
 // randomized diagonal estimator of F~^* D^{-1} F~ over nrhs probes (fft.cu)
 int green_run(hmc_ctx* ctx, int chain, const double* phi, const double2* v, int nrhs, double2* out, int precond,
               hmc_cg_stats* st);
+
+// bounds build: per-translation-unit device error words (0 in the normal build)
+unsigned int bounds_take_stencil();
+unsigned int bounds_take_strip();
+
+// device error word: reads it (synchronising the stream) and returns HMC_ERR_TIMEOUT, clearing
+// it, if a bounded device-side wait gave up since the last check (hmc.cu)
+int check_device_flags(hmc_ctx* ctx);
 
 // reductions: sum nblk partials for each of k rows into out[k] (device)
 int reduce_rows(hmc_ctx* ctx, const double* part, int k, int nblk, double* out);

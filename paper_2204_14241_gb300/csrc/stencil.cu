@@ -38,11 +38,13 @@ __global__ void __launch_bounds__(256) k_apply_D(Lat lat, Coef<R> cf, const R* _
     const int tn = DAG ? tprev(t, lat.Nt) : tnext(t, lat.Nt);
     const R tsign = DAG ? (t == 0 ? R(-1) : R(1)) : (t == lat.Nt - 1 ? R(-1) : R(1));
     const R eta = ((xx + yy) & 1) ? R(-1) : R(1);
-    Site<R> o = site_op<R>(cf, load_site(xk + s), load_site(xk + row + wrap_dec(xx, L)),
-                           load_site(xk + row + wrap_inc(xx, L)),
-                           load_site(xk + slice + (int64_t)wrap_dec(yy, L) * L + xx),
-                           load_site(xk + slice + (int64_t)wrap_inc(yy, L) * L + xx),
-                           load_site(xk + (int64_t)tn * L * L + (s - slice)), tsign,
+    auto ld = [&](int64_t i) {
+        Site<R> z{};
+        return HMC_IN(i >= 0 && i < V, kBndApplyD) ? load_site(xk + i) : z;
+    };
+    Site<R> o = site_op<R>(cf, ld(s), ld(row + wrap_dec(xx, L)), ld(row + wrap_inc(xx, L)),
+                           ld(slice + (int64_t)wrap_dec(yy, L) * L + xx), ld(slice + (int64_t)wrap_inc(yy, L) * L + xx),
+                           ld((int64_t)tn * L * L + (s - slice)), tsign,
                            __ldg(phi + s), __ldg(phi + V + s), __ldg(phi + 2 * V + s), eta);
     store_site(y + blockIdx.y * V + s, o);
 }
@@ -607,6 +609,10 @@ int launch_apply_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x,
                    const cplx<R>* pold, cplx<R>* pnew) {
     if (nrhs <= 0) return HMC_OK;
     if (pnew && (!cgs || !pold || pold == pnew)) return fail(ctx, HMC_ERR_ARG, "apply_A: bad direction-update buffers");
+    if constexpr (sizeof(R) == 4) {
+        if (!pnew && strip_supported(lat))
+            return launch_apply_A_strip(ctx, lat, phi, x, y, nrhs, part, nblk_out, cgs);
+    }
     static PerDevice attr;
     uint64_t bit;
     if (attr.pending(&bit)) {
@@ -833,12 +839,15 @@ __global__ void __launch_bounds__(256) k_force(Lat lat, Coef<double> cf, BosonCo
         const double eta = ((xx + yy) & 1) ? -1.0 : 1.0;
         const double p1 = __ldg(phi + s), p2 = __ldg(phi + V + s), p3 = __ldg(phi + 2 * V + s);
         double acc[3] = {0.0, 0.0, 0.0};
+        auto ld = [&](const Site<double>* base, int64_t i) {
+            Site<double> z{};
+            return HMC_IN(i >= 0 && i < V, kBndForce) ? load_site(base + i) : z;
+        };
         for (int k = 0; k < nrhs; ++k) {
             const Site<double>* Xk = X + k * V;
-            const Site<double> xc = load_site(Xk + s);
-            const Site<double> Y = site_op<double>(cf, xc, load_site(Xk + sxm), load_site(Xk + sxp),
-                                                   load_site(Xk + sym), load_site(Xk + syp),
-                                                   load_site(Xk + stm), tsign, p1, p2, p3, eta);
+            const Site<double> xc = ld(Xk, s);
+            const Site<double> Y = site_op<double>(cf, xc, ld(Xk, sxm), ld(Xk, sxp), ld(Xk, sym), ld(Xk, syp),
+                                                   ld(Xk, stm), tsign, p1, p2, p3, eta);
             const Site<double> pk = load_site(pf + k * V + s);
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
@@ -923,4 +932,8 @@ int launch_boson(hmc_ctx* ctx, const Lat& lat, double r, const double* phi, doub
     return HMC_OK;
 }
 
+}  // namespace hmc
+
+namespace hmc {
+unsigned int bounds_take_stencil() { return bounds_take_tu(); }
 }  // namespace hmc

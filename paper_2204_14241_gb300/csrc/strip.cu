@@ -1,0 +1,545 @@
+// Fused complex64 y = A x = D (D^dagger x) (Eq. linsys) on full-height strips, for L a multiple
+// of 16 up to 80.
+//
+// A block owns one strip of 16 columns x all L rows of one right-hand side and marches through a
+// chunk of time slices. Because the strip spans the whole periodic y extent there is no halo in
+// y; in x it stages two extra columns on each side (20 columns of x) and computes t_ = D^dagger x
+// on one extra column on each side (18 columns). 256 threads own a column of NY = L / 16
+// consecutive rows each (16 columns x 16 row segments); a ninth warp computes t_ on the two extra
+// columns. A thread walks down its column with a three-row window in registers, so each row's
+// y-neighbours cost one shared-memory site read instead of two: about 3.4 site reads of x and 3.4
+// of t_ per output site, against 5 and 5 for one site per thread; x(t-1) of its rows stays in
+// registers for the time hop.
+//
+// Per step t (x(t+1) landed in the three-slice cp.async ring): barrier; t_(t+1) = D^dagger x on
+// the thread's rows into registers; y(t) = D t_ from t_(t) in shared memory and t_(t+1) in
+// registers, stored to global; barrier; t_(t+1) into shared memory, x(t+4) issued into the
+// buffer that held x(t+1). The site arithmetic runs on packed (re, im) pairs with Blackwell's
+// two-wide FP32 instructions (add/mul/fma .f32x2).
+#include <cuda.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "internal.h"
+
+namespace hmc {
+
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 pk2(float a, float b) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(u64 r, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r)); }
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+    u64 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+    u64 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ u64 swp2(u64 a) {   // (re, im) -> (im, re)
+    float x, y;
+    upk2(a, x, y);
+    return pk2(y, x);
+}
+
+// One site, four complex components packed as (re, im) pairs; index c = alpha * 2 + spin.
+struct P4 { u64 c[4]; };
+
+// Coefficients of D with the real scalars broadcast to both halves of a pair.
+struct CoefP {
+    u64 d[2], hx[2], hy[2];
+    float cpl;
+};
+
+static CoefP make_coef_p(const hmc_params& p) {
+    CoefP c;
+    auto bc = [](double v) {
+        const float f = (float)v;
+        u64 b;
+        unsigned u;
+        memcpy(&u, &f, 4);
+        b = ((u64)u << 32) | u;
+        return b;
+    };
+    for (int a = 0; a < 2; ++a) {
+        c.d[a] = bc(-1.0 - p.dtau * p.mu[a]);
+        c.hx[a] = bc(-p.dtau * p.t_h[a]);
+        c.hy[a] = bc(-p.dtau * p.t_v[a]);
+    }
+    c.cpl = (float)(p.dtau * p.g);
+    return c;
+}
+
+// One site of D v (time hop from v(t+1), ts = b(t)) or D^dagger v (from v(t-1), ts = b(t-1)):
+//   out = d c + ts tn + hx (xm + xp) + hy (ym + yp) + cpl eta (phi.sigma) c[other band]
+// with phi.sigma = [[p3, p1 - i p2], [p1 + i p2, -p3]] on spin and sigma^x swapping the bands.
+__device__ __forceinline__ P4 site_op_p(const CoefP& cf, const P4& c, const P4& xm, const P4& xp, const P4& ym,
+                                        const P4& yp, const P4& tn, u64 ts, float p1, float p2, float p3, float eta) {
+    const float f = cf.cpl * eta;
+    const float q1 = f * p1, q2 = f * p2, q3 = f * p3;
+    const u64 Q1 = pk2(q1, q1), Q3 = pk2(q3, q3), NQ3 = pk2(-q3, -q3), Q2 = pk2(q2, -q2), NQ2 = pk2(-q2, q2);
+    P4 o;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int i = a * 2 + s;
+            const u64 u = add2(xm.c[i], xp.c[i]);
+            const u64 v = add2(ym.c[i], yp.c[i]);
+            u64 r = mul2(cf.d[a], c.c[i]);
+            r = fma2(ts, tn.c[i], r);
+            r = fma2(cf.hx[a], u, r);
+            o.c[i] = fma2(cf.hy[a], v, r);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const u64 w0 = c.c[(1 - a) * 2], w1 = c.c[(1 - a) * 2 + 1];
+        u64 r0 = fma2(Q3, w0, o.c[a * 2]);
+        r0 = fma2(Q1, w1, r0);
+        o.c[a * 2] = fma2(Q2, swp2(w1), r0);          // re += q2 w1.im, im -= q2 w1.re
+        u64 r1 = fma2(Q1, w0, o.c[a * 2 + 1]);
+        r1 = fma2(NQ2, swp2(w0), r1);                  // re -= q2 w0.im, im += q2 w0.re
+        o.c[a * 2 + 1] = fma2(NQ3, w1, r1);
+    }
+    return o;
+}
+
+template <int L, int NY> struct StripShape {
+    static constexpr int NSEG = L / NY;               // row segments
+    static constexpr int NMAIN = 16 * NSEG;           // threads that own output columns
+    static constexpr int NRING = 2 * NSEG;            // threads for the two side columns of t_
+    static constexpr int NTHR = (NMAIN + NRING + 31) / 32 * 32;
+    static constexpr int TC = 18;                     // columns of t_ computed
+    // one staging slot (bytes): x of the 16 own columns [row][16 sites][32 B], of the two columns
+    // left of the strip [row][2][32 B] and of the two right of it [row][2][32 B], each site's two
+    // 16-byte halves swapped where bit 2 of the site index is set (the TMA 32-byte swizzle, which
+    // makes a quarter warp's reads of one half of eight consecutive sites hit eight distinct bank
+    // groups); phi of the own columns [component][row][16]. Regions are multiples of 1024 bytes.
+    static constexpr int XMAIN = L * 16 * 32;
+    static constexpr int XHALO = L * 2 * 32;
+    static constexpr int PHI = 3 * L * 16 * 4;
+    static constexpr int OFF_XL = XMAIN, OFF_XR = OFF_XL + XHALO, OFF_PHI = OFF_XR + XHALO;
+    static constexpr int SLOT = OFF_PHI + PHI;
+    static constexpr int TS = 2 * L * TC;             // 16-byte units per t_ slice [plane][row][18]
+    static constexpr size_t smem = (size_t)2 * SLOT + (size_t)2 * TS * 16 + 1024;   // + alignment slack
+    static_assert(L % 16 == 0 && L <= 80 && L % NY == 0, "strip kernel: L a multiple of 16 up to 80");
+    static_assert(XMAIN % 1024 == 0 && XHALO % 1024 == 0 && PHI % 1024 == 0, "swizzled TMA regions 1024-byte aligned");
+};
+
+// Site `site` of a swizzled site-major region (16-byte units from `region`): its halves sit at
+// 2 site + s and 2 site + 1 - s, s = bit 2 of the site index.
+__device__ __forceinline__ P4 lds_site(const ulonglong2* region, int site, int lim) {
+    if (!HMC_IN(site >= 0 && 2 * site + 1 < lim, kBndStripShared)) return P4{};
+    const int sw = (site >> 2) & 1;
+    const ulonglong2 a = region[2 * site + sw], b = region[2 * site + 1 - sw];
+    P4 r;
+    r.c[0] = a.x; r.c[1] = a.y; r.c[2] = b.x; r.c[3] = b.y;
+    return r;
+}
+
+// Site i of a two-plane region starting at plane0 (plane stride pstride); lim bounds the 16-byte
+// units readable from plane0 (checked in the bounds build only).
+__device__ __forceinline__ P4 lds_p4(const ulonglong2* plane0, int pstride, int i, int lim) {
+    if (!HMC_IN(i >= 0 && i + pstride < lim, kBndStripShared)) return P4{};
+    const ulonglong2 a = plane0[i], b = plane0[pstride + i];
+    P4 s;
+    s.c[0] = a.x; s.c[1] = a.y; s.c[2] = b.x; s.c[3] = b.y;
+    return s;
+}
+__device__ __forceinline__ void sts_p4(ulonglong2* plane0, int pstride, int i, const P4& s) {
+    plane0[i] = make_ulonglong2(s.c[0], s.c[1]);
+    plane0[pstride + i] = make_ulonglong2(s.c[2], s.c[3]);
+}
+__device__ __forceinline__ P4 ldg_p4(const Site<float>* p) {
+    const ulonglong2* q = reinterpret_cast<const ulonglong2*>(p);
+    const ulonglong2 a = __ldg(q), b = __ldg(q + 1);
+    P4 s;
+    s.c[0] = a.x; s.c[1] = a.y; s.c[2] = b.x; s.c[3] = b.y;
+    return s;
+}
+__device__ __forceinline__ void stg_p4(Site<float>* p, const P4& s) {
+    ulonglong2* q = reinterpret_cast<ulonglong2*>(p);
+    q[0] = make_ulonglong2(s.c[0], s.c[1]);
+    q[1] = make_ulonglong2(s.c[2], s.c[3]);
+}
+
+// ---- TMA and mbarrier primitives (inline PTX) ---------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Bounded wait for the phase of parity `par` of the barrier: at most `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t par, int limit) {
+    for (int i = 0; i < limit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok) : "r"(bar), "r"(par) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// Tensor maps of one launch: x viewed as [slice = k * Nt + t][y][x][8 floats] (box: whole sites of
+// 16 or 2 columns x all rows, 32-byte swizzle), phi as [component][t][y][x] (box: 16 columns x all
+// rows x 3 components).
+struct StripMaps {
+    CUtensorMap xmain, xhalo, phi;
+};
+
+// Grid: nch time chunks of C slices x P = nrhs * (L / 16) pipelines, block = c * P + p with
+// p = k * (L / 16) + strip. part (if not null): part[k * nblk + c * (L / 16) + strip], nblk =
+// nch * (L / 16), the partial sums of ||D^dagger x_k||^2 over the block's output sites.
+//
+// Staging: two slots; slice x(ta + m) (and phi(ta + m) of the own columns) arrives by TMA in slot
+// m & 1 on that slot's mbarrier, issued by thread 0 one step ahead. t_ lives in two slices.
+// Step m: wait for slot m & 1; barrier (also the end of step m - 1); thread 0 issues slice m + 1
+// into the other slot (read in step m - 1; phi of the rows a thread needs for y is kept in its
+// registers from step m - 1); t_(ta + m) = D^dagger x on the own rows, written to the
+// t_ slice that y(ta + m - 2) read one step earlier; y(ta + m - 1) = D t_ from t_(ta + m - 1) and
+// the thread's own t_(ta + m). A thread reads its own t_(ta + m) only, so one barrier per step.
+// Waits are bounded (wait_limit polls): on a timeout the block drains the copy in flight, sets
+// err[0] and returns. test_timeout makes the first wait target a barrier that is never armed.
+template <int L, int NY>
+__global__ void __launch_bounds__(StripShape<L, NY>::NTHR, 1)
+k_apply_A_strip(const __grid_constant__ StripMaps maps, Lat lat, CoefP cf, int nch, int C,
+                const float* __restrict__ phi, const Site<float>* __restrict__ x, Site<float>* __restrict__ y,
+                double* __restrict__ part, const CgScalars* __restrict__ cgs, int* __restrict__ err, int wait_limit,
+                int test_timeout) {
+    using S = StripShape<L, NY>;
+    constexpr int TC = S::TC;
+    constexpr int nstrip = L / 16, LL = L * L;
+    const int P = gridDim.x / nch;
+    const int c = blockIdx.x / P, p = blockIdx.x - c * P;
+    const int k = p / nstrip, sx = p - k * nstrip;
+    if (cgs && !cgs[k].active) return;
+    const int Nt = lat.Nt;
+    const int64_t V = lat.V;
+    const int ta = c * C;
+    const int tb = min(ta + C, Nt);            // outputs y(ta .. tb-1); slices x(ta - 1 .. tb)
+    const int x0 = sx * 16;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sbase = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    ulonglong2* tr = reinterpret_cast<ulonglong2*>(sbase + 2 * S::SLOT);   // 2 slices x [2 planes][L rows][18 columns]
+    __shared__ __align__(8) uint64_t bars[3];   // two staging slots; the third is never armed (timeout test)
+    __shared__ double red[S::NTHR / 32];
+
+    const int tid = threadIdx.x;
+    const bool own_y = tid < S::NMAIN;
+    const bool has_t = tid < S::NMAIN + S::NRING;
+    int tcol = 0, seg = 0;
+    if (own_y) {
+        tcol = 1 + (tid & 15);
+        seg = tid >> 4;
+    } else if (has_t) {
+        const int r = tid - S::NMAIN;
+        tcol = (r & 1) ? TC - 1 : 0;
+        seg = r >> 1;
+    }
+    // staged x column of strip column j (j in [-2, 17]): its region (16-byte units from the slot),
+    // the column within the region and the region's sites per row
+    auto xcol_of = [&](int j, int& reg, int& col, int& rs) {
+        if (j < 0) { reg = S::OFF_XL / 16; col = j + 2; rs = 2; }
+        else if (j >= 16) { reg = S::OFF_XR / 16; col = j - 16; rs = 2; }
+        else { reg = 0; col = j; rs = 16; }
+    };
+    int gc, oc, rc_, gl, ol, rl, gr, orr, rr;   // own column, left and right neighbour columns
+    xcol_of(tcol - 1, gc, oc, rc_);
+    xcol_of(tcol - 2, gl, ol, rl);
+    xcol_of(tcol, gr, orr, rr);
+    int gx = x0 - 1 + tcol;
+    gx = gx < 0 ? gx + L : (gx >= L ? gx - L : gx);
+    const int row0 = seg * NY;
+    const int rup = row0 == 0 ? L - 1 : row0 - 1;          // row above the thread's column
+    const int rdn = row0 + NY == L ? 0 : row0 + NY;         // row below it
+    const Site<float>* xk = x + (int64_t)k * V;
+    Site<float>* yk = y + (int64_t)k * V;
+
+    const uint32_t bar0 = smem_u32(&bars[0]);
+    if (tid == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        mbar_init(bar0 + 16, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int xl_col = x0 - 2 < 0 ? x0 - 2 + L : x0 - 2;
+    const int xr_col = x0 + 16 >= L ? x0 + 16 - L : x0 + 16;
+    constexpr uint32_t kSlotBytes = (uint32_t)S::SLOT;
+    auto issue = [&](int slot, int t) {   // thread 0 only
+        const uint32_t bar = bar0 + 8 * slot;
+        const uint32_t dst = smem_u32(sbase + slot * S::SLOT);
+        const int sl = k * Nt + t;
+        mbar_expect_tx(bar, kSlotBytes);
+        tma_load_4d(dst, &maps.xmain, 0, x0, 0, sl, bar);
+        tma_load_4d(dst + S::OFF_XL, &maps.xhalo, 0, xl_col, 0, sl, bar);
+        tma_load_4d(dst + S::OFF_XR, &maps.xhalo, 0, xr_col, 0, sl, bar);
+        tma_load_4d(dst + S::OFF_PHI, &maps.phi, x0, 0, t, 0, bar);
+    };
+    const float eta0 = ((gx + row0) & 1) ? -1.f : 1.f;   // (-1)^(x+y) of the first row; it alternates along y
+    const bool ring_phi = has_t && !own_y;                 // the side columns' phi is not staged
+
+    // prologue: x(ta - 1) on the own rows, slice ta in flight
+    P4 xprev[NY];
+    if (has_t) {
+        const int tm = ta == 0 ? Nt - 1 : ta - 1;
+        const Site<float>* src = xk + (int64_t)tm * LL + row0 * L + gx;
+#pragma unroll
+        for (int j = 0; j < NY; ++j) {
+            xprev[j] = P4{};
+            if (HMC_IN(tm >= 0 && tm < Nt && row0 + j < L && gx >= 0 && gx < L, kBndStripGlobal))
+                xprev[j] = ldg_p4(src + j * L);
+        }
+    }
+    const int nsl = tb - ta + 1;   // staged slices x(ta) .. x(tb)
+    if (tid == 0) issue(0, ta);
+
+    u64 acc = 0;   // (sum re^2, sum im^2) of t_ on the own output sites
+    float phk[NY][3];   // phi of the own rows at the slice of the last t_ (the next y needs it; its slot is refilled)
+    for (int m = 0; m < nsl; ++m) {
+        const int slot = m & 1;
+        const int tn_slice = ta + m >= Nt ? ta + m - Nt : ta + m;   // slice of t_ computed now
+        float phr[NY][3];   // phi of the side columns (ring threads only)
+        if (ring_phi) {
+            const float* pp = phi + (int64_t)tn_slice * LL + row0 * L + gx;
+#pragma unroll
+            for (int j = 0; j < NY; ++j) {
+                phr[j][0] = __ldg(pp + j * L);
+                phr[j][1] = __ldg(pp + V + j * L);
+                phr[j][2] = __ldg(pp + 2 * V + j * L);
+            }
+        }
+        const bool ok = (test_timeout && m == 0) ? mbar_wait(bar0 + 16, 0, wait_limit)
+                                                 : mbar_wait(bar0 + 8 * slot, (m >> 1) & 1, wait_limit);
+        if (__syncthreads_or(!ok)) {
+            // drain the copy in flight into this slot before leaving (bounded as well)
+            if (tid == 0) {
+                if (!mbar_wait(bar0 + 8 * slot, (m >> 1) & 1, wait_limit)) atomicOr(err, 2);
+                atomicOr(err, 1);
+            }
+            __syncthreads();
+            return;
+        }
+        if (tid == 0 && m + 1 < nsl) {
+            fence_proxy_async();
+            issue(slot ^ 1, ta + m + 1 >= Nt ? ta + m + 1 - Nt : ta + m + 1);
+        }
+        const ulonglong2* xb = reinterpret_cast<const ulonglong2*>(sbase + slot * S::SLOT);
+        const float* phs = reinterpret_cast<const float*>(sbase + slot * S::SLOT + S::OFF_PHI);
+        ulonglong2* tn = tr + slot * S::TS;                 // t_(ta + m)
+        const ulonglong2* tc = tr + (slot ^ 1) * S::TS;    // t_(ta + m - 1)
+        // y(t) needs phi(t) of its rows, kept from the previous t_ step
+        float phc[NY][3];
+#pragma unroll
+        for (int j = 0; j < NY; ++j)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) phc[j][a] = phk[j][a];
+        // t_(tn_slice) = D^dagger x on the own rows, into shared memory
+        if (has_t) {
+            const u64 ts = tn_slice == 0 ? pk2(-1.f, -1.f) : pk2(1.f, 1.f);   // b(t - 1)
+            const ulonglong2 *xc_r = xb + gc, *xl_r = xb + gl, *xr_r = xb + gr;
+            P4 up = lds_site(xc_r, rup * rc_ + oc, S::SLOT / 16 - gc);
+            P4 cen = lds_site(xc_r, row0 * rc_ + oc, S::SLOT / 16 - gc);
+#pragma unroll
+            for (int j = 0; j < NY; ++j) {
+                const int rd = j + 1 < NY ? row0 + j + 1 : rdn;
+                const P4 dn = lds_site(xc_r, rd * rc_ + oc, S::SLOT / 16 - gc);
+                const P4 lf = lds_site(xl_r, (row0 + j) * rl + ol, S::SLOT / 16 - gl);
+                const P4 rt = lds_site(xr_r, (row0 + j) * rr + orr, S::SLOT / 16 - gr);
+                float p1, p2, p3;
+                if (own_y) {
+                    const float* q = phs + (row0 + j) * 16 + (tcol - 1);
+                    p1 = q[0];
+                    p2 = q[L * 16];
+                    p3 = q[2 * L * 16];
+                } else {
+                    p1 = phr[j][0];
+                    p2 = phr[j][1];
+                    p3 = phr[j][2];
+                }
+                phk[j][0] = p1;
+                phk[j][1] = p2;
+                phk[j][2] = p3;
+                const P4 o = site_op_p(cf, cen, lf, rt, up, dn, xprev[j], ts, p1, p2, p3, (j & 1) ? -eta0 : eta0);
+                sts_p4(tn, L * TC, (row0 + j) * TC + tcol, o);
+                xprev[j] = cen;
+                up = cen;
+                cen = dn;
+            }
+        }
+        // y(t) = D t_ at t = tn_slice - 1 on the own rows
+        if (own_y && m >= 1) {
+            const int t = tn_slice == 0 ? Nt - 1 : tn_slice - 1;
+            const u64 ts = t == Nt - 1 ? pk2(-1.f, -1.f) : pk2(1.f, 1.f);   // b(t)
+            P4 up = lds_p4(tc, L * TC, rup * TC + tcol, S::TS);
+            P4 cen = lds_p4(tc, L * TC, row0 * TC + tcol, S::TS);
+            Site<float>* dst = yk + (int64_t)t * LL + row0 * L + gx;
+#pragma unroll
+            for (int j = 0; j < NY; ++j) {
+                const int rd = j + 1 < NY ? row0 + j + 1 : rdn;
+                const P4 dn = lds_p4(tc, L * TC, rd * TC + tcol, S::TS);
+                const P4 lf = lds_p4(tc, L * TC, (row0 + j) * TC + tcol - 1, S::TS);
+                const P4 rt = lds_p4(tc, L * TC, (row0 + j) * TC + tcol + 1, S::TS);
+                const P4 nx = lds_p4(tn, L * TC, (row0 + j) * TC + tcol, S::TS);   // own t_(t + 1), written above
+                const P4 o = site_op_p(cf, cen, lf, rt, up, dn, nx, ts, phc[j][0], phc[j][1], phc[j][2],
+                                       (j & 1) ? -eta0 : eta0);
+                if (HMC_IN(t >= 0 && t < Nt && row0 + j < L && gx >= 0 && gx < L, kBndStripGlobal)) stg_p4(dst + j * L, o);
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) acc = fma2(cen.c[qq], cen.c[qq], acc);
+                up = cen;
+                cen = dn;
+            }
+        }
+    }
+    if (part) {
+        float a0, a1;
+        upk2(acc, a0, a1);
+        const double tot = block_sum((double)a0 + (double)a1, red);
+        if (tid == 0) part[(int64_t)k * (nch * nstrip) + c * nstrip + sx] = tot;
+    }
+}
+
+#ifndef STRIP_NY80
+#define STRIP_NY80 4
+#endif
+
+bool strip_supported(const Lat& lat) {
+    return lat.L % 16 == 0 && lat.L >= 16 && lat.L <= 80;
+}
+
+// Time chunk C: the number of chunks makes ceil(blocks / resident blocks) waves; each block stages
+// C + 1 slices and computes C + 1 slices of t_ for C of y, so minimise waves x (C + 1.5).
+static void strip_chunks(int Nt, int pipelines, int resident, int* C_out, int* nch_out) {
+    double best = 1e30;
+    int bC = Nt, bn = 1;
+    for (int C = 4; C <= Nt; ++C) {
+        const int nch = (Nt + C - 1) / C;
+        if (C > 4 && (Nt + C - 2) / (C - 1) == nch) continue;   // same chunk count with a smaller C
+        const int64_t blocks = (int64_t)nch * pipelines;
+        const double waves = (double)((blocks + resident - 1) / resident);
+        const double cost = waves * (C + 1.5);
+        if (cost < best) { best = cost; bC = C; bn = nch; }
+    }
+    if (Nt < 4) { bC = Nt; bn = 1; }
+    *C_out = bC;
+    *nch_out = bn;
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no link against
+// the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_fn(hmc_ctx* ctx, int* rc) {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        err = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+        if (err == cudaSuccess && q == cudaDriverEntryPointSuccess) fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    *rc = fn ? HMC_OK : fail(ctx, HMC_ERR_CUDA, "apply_A: cuTensorMapEncodeTiled unavailable");
+    return fn;
+}
+
+static int encode(hmc_ctx* ctx, EncodeTiledFn fn, CUtensorMap* m, const void* base, const cuuint64_t* dim,
+                  const cuuint64_t* stride, const cuuint32_t* box, CUtensorMapSwizzle swz) {
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dim, stride, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ctx, HMC_ERR_CUDA, "apply_A: tensor map rejected (" + std::to_string((int)r) + ")");
+    return HMC_OK;
+}
+
+// The three tensor maps of a launch on x (all right-hand sides) and phi.
+static int strip_maps(hmc_ctx* ctx, const Lat& lat, int nrhs, const float* phi, const void* x, StripMaps* m) {
+    int rc;
+    EncodeTiledFn fn = encode_fn(ctx, &rc);
+    if (!fn) return rc;
+    const cuuint64_t L = (cuuint64_t)lat.L;
+    const cuuint64_t xdim[4] = {8, L, L, (cuuint64_t)lat.Nt * (cuuint64_t)nrhs};
+    const cuuint64_t xstr[3] = {32, 32 * L, 32 * L * L};
+    const cuuint32_t bmain[4] = {8, 16, (cuuint32_t)L, 1}, bhalo[4] = {8, 2, (cuuint32_t)L, 1};
+    const cuuint64_t pdim[4] = {L, L, (cuuint64_t)lat.Nt, 3};
+    const cuuint64_t pstr[3] = {4 * L, 4 * L * L, 4 * (cuuint64_t)lat.V};
+    const cuuint32_t bphi[4] = {16, (cuuint32_t)L, 1, 3};
+    if ((rc = encode(ctx, fn, &m->xmain, x, xdim, xstr, bmain, CU_TENSOR_MAP_SWIZZLE_32B))) return rc;
+    if ((rc = encode(ctx, fn, &m->xhalo, x, xdim, xstr, bhalo, CU_TENSOR_MAP_SWIZZLE_32B))) return rc;
+    return encode(ctx, fn, &m->phi, phi, pdim, pstr, bphi, CU_TENSOR_MAP_SWIZZLE_NONE);
+}
+
+template <int L, int NY>
+static int go_strip(hmc_ctx* ctx, const Lat& lat, const float* phi, const Site<float>* x, Site<float>* y, int nrhs,
+                    double* part, const CgScalars* cgs, int* nblk_out) {
+    using S = StripShape<L, NY>;
+    static PerDevice attr;
+    uint64_t bit;
+    if (attr.pending(&bit)) {
+        HMC_CUDA(ctx, cudaFuncSetAttribute(k_apply_A_strip<L, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)S::smem));
+        attr.mark(bit);
+    }
+    const int per_sm_smem = 228 * 1024;
+    int bps = (int)(per_sm_smem / (S::smem + 1024));
+    if (bps > 2048 / S::NTHR) bps = 2048 / S::NTHR;
+    if (bps < 1) bps = 1;
+    const int pipes = nrhs * (L / 16);
+    int C, nch;
+    strip_chunks(lat.Nt, pipes, ctx->num_sms * bps, &C, &nch);
+    const int64_t nblk = (int64_t)nch * (L / 16);
+    if (part && nblk * nrhs > ctx->part_cap) return fail(ctx, HMC_ERR_ARG, "apply_A: reduction buffer too small");
+    StripMaps maps;
+    int rc;
+    if ((rc = strip_maps(ctx, lat, nrhs, phi, x, &maps))) return rc;
+    const int wl = ctx->p.wait_spin_limit > 0 ? ctx->p.wait_spin_limit : (1 << 20);
+    k_apply_A_strip<L, NY><<<(unsigned)(nch * pipes), S::NTHR, S::smem, ctx->stream>>>(
+        maps, lat, make_coef_p(ctx->p), nch, C, phi, x, y, part, cgs, ctx->d_flags, wl, ctx->p.test_wait_timeout);
+    HMC_LAUNCH(ctx, "k_apply_A_strip");
+    if (nblk_out) *nblk_out = (int)nblk;
+    return HMC_OK;
+}
+
+unsigned int bounds_take_strip() { return bounds_take_tu(); }
+
+int launch_apply_A_strip(hmc_ctx* ctx, const Lat& lat, const float* phi, const float2* x, float2* y, int nrhs,
+                         double* part, int* nblk_out, const CgScalars* cgs) {
+    const Site<float>* xs = reinterpret_cast<const Site<float>*>(x);
+    Site<float>* ys = reinterpret_cast<Site<float>*>(y);
+    switch (lat.L) {
+        case 16: return go_strip<16, 1>(ctx, lat, phi, xs, ys, nrhs, part, cgs, nblk_out);
+        case 32: return go_strip<32, 2>(ctx, lat, phi, xs, ys, nrhs, part, cgs, nblk_out);
+        case 48: return go_strip<48, 3>(ctx, lat, phi, xs, ys, nrhs, part, cgs, nblk_out);
+        case 64: return go_strip<64, 4>(ctx, lat, phi, xs, ys, nrhs, part, cgs, nblk_out);
+        case 80: return go_strip<80, STRIP_NY80>(ctx, lat, phi, xs, ys, nrhs, part, cgs, nblk_out);
+        default: return fail(ctx, HMC_ERR_STATE, "apply_A: no strip kernel for this L");
+    }
+}
+
+}  // namespace hmc

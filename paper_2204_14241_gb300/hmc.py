@@ -16,7 +16,8 @@ import os
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libhmc.so")
+# HMC_LIBRARY selects another build of the same library (the -DHMC_BOUNDS variant)
+LIB_PATH = os.environ.get("HMC_LIBRARY", os.path.join(HERE, "libhmc.so"))
 
 HMC_OK, HMC_ERR_ARG, HMC_ERR_NOCONV, HMC_ERR_NONFINITE, HMC_ERR_TIMEOUT, HMC_ERR_CUDA, HMC_ERR_STATE = range(7)
 FP64, FP32 = 0, 1
@@ -27,7 +28,8 @@ METRIC_MOMENTUM, METRIC_VELOCITY, METRIC_KINETIC, METRIC_ACCUM, METRIC_MNORM = r
 # every function declared in include/hmc.h
 EXPORTS = ("hmc_init", "hmc_destroy", "hmc_last_error", "hmc_counters", "apply_M", "apply_MdagM",
            "apply_MdagM_static", "apply_precond", "green_estimate",
-           "cg_solve", "force", "metric_apply", "trajectory", "philox_raw", "philox_normal")
+           "cg_solve", "force", "metric_apply", "trajectory", "hmc_trajectory_stats", "philox_raw", "philox_normal",
+           "hmc_fma_peak", "hmc_bounds_status")
 
 
 class HmcError(RuntimeError):
@@ -41,7 +43,8 @@ class Params(ctypes.Structure):
                 ("t_h", ctypes.c_double * 2), ("t_v", ctypes.c_double * 2), ("mu", ctypes.c_double * 2),
                 ("g", ctypes.c_double), ("r", ctypes.c_double), ("u", ctypes.c_double), ("c", ctypes.c_double),
                 ("solver_mode", ctypes.c_int), ("nrhs_max", ctypes.c_int), ("cg_tol", ctypes.c_double),
-                ("cg_maxit", ctypes.c_int), ("initial_guess", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("cg_maxit", ctypes.c_int), ("initial_guess", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("wait_spin_limit", ctypes.c_int), ("test_wait_timeout", ctypes.c_int)]
 
 
 class Chain(ctypes.Structure):
@@ -63,6 +66,21 @@ class TrajIn(ctypes.Structure):
                 ("precond", ctypes.c_int), ("noise", ctypes.c_int),
                 ("chi", ctypes.POINTER(ctypes.c_void_p)), ("z", ctypes.POINTER(ctypes.c_void_p)),
                 ("u", ctypes.POINTER(ctypes.c_double)), ("seed", ctypes.c_uint64), ("counter", ctypes.c_uint64)]
+
+
+MAX_SOLVES = 256
+
+
+class TrajStats(ctypes.Structure):
+    _fields_ = [("n_solves", ctypes.c_int), ("reliable_updates", ctypes.c_int),
+                ("iterations", ctypes.c_int * MAX_SOLVES), ("true_resid", ctypes.c_double * MAX_SOLVES),
+                ("phase_ms", ctypes.c_double * 4)]
+
+    def as_dict(self):
+        n = min(self.n_solves, MAX_SOLVES)
+        return {"n_solves": self.n_solves, "reliable_updates": self.reliable_updates,
+                "iterations": list(self.iterations[:n]), "true_resid": list(self.true_resid[:n]),
+                "phase_ms": dict(zip(("solve", "force", "metric", "other"), self.phase_ms))}
 
 
 class TrajOut(ctypes.Structure):
@@ -101,8 +119,11 @@ def lib():
         "metric_apply": [_P, _I, _I, _P, _P, _P, ctypes.POINTER(ctypes.c_double)],
         "green_estimate": [_P, _I, _P, _P, _I, _P, _I, ctypes.POINTER(CgStats)],
         "trajectory": [_P, ctypes.POINTER(TrajIn), ctypes.POINTER(TrajOut)],
+        "hmc_trajectory_stats": [_P, _I, ctypes.POINTER(TrajStats)],
         "philox_raw": [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int64, _P],
         "philox_normal": [_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, _I, _P],
+        "hmc_fma_peak": [_I, ctypes.POINTER(ctypes.c_double)],
+        "hmc_bounds_status": [ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_int)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -114,6 +135,27 @@ def lib():
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def bounds_status():
+    """(word, enabled) of the bounds build's index checks (word 0 and enabled False otherwise)."""
+    lib_ = lib()
+    w, e = ctypes.c_uint(), ctypes.c_int()
+    rc = lib_.hmc_bounds_status(ctypes.byref(w), ctypes.byref(e))
+    if rc:
+        raise HmcError(rc, lib_.hmc_last_error(None).decode())
+    return w.value, bool(e.value)
+
+
+def fma_peak(prec=FP64, device=None):
+    """Measured FMA throughput (flop/s) of the CUDA cores in FP64 (or FP32) on `device`."""
+    lib_ = lib()
+    v = ctypes.c_double()
+    with torch.cuda.device(torch.device(device or "cuda")):
+        rc = lib_.hmc_fma_peak(prec, ctypes.byref(v))
+    if rc:
+        raise HmcError(rc, lib_.hmc_last_error(None).decode())
+    return v.value
 
 
 def apply_MdagM_static(params, L, Nt, phi, x, out, norms=False, stream=None):
@@ -154,7 +196,7 @@ class Context:
 
     def __init__(self, L, Nt, dtau=0.1, t_h=(1.0, 0.5), t_v=(0.5, 1.0), mu=(-0.5, -0.5), g=1.0, r=0.5,
                  u=1.0, c=3.0, solver="mixed", nrhs_max=1, cg_tol=1e-10, cg_maxit=100000, chains=None,
-                 stream=None, device=None, initial_guess=0, autotune=0):
+                 stream=None, device=None, initial_guess=0, autotune=0, wait_spin_limit=0, test_wait_timeout=0):
         self.lib = lib()
         self.device = torch.device(device or "cuda")
         p = Params()
@@ -167,6 +209,8 @@ class Context:
         p.nrhs_max, p.cg_tol, p.cg_maxit = nrhs_max, cg_tol, cg_maxit
         p.initial_guess = int(initial_guess)
         p.autotune = int(autotune)
+        p.wait_spin_limit = int(wait_spin_limit)
+        p.test_wait_timeout = int(test_wait_timeout)
         self.params = p
         if chains is None:
             chains = [(L, Nt, r)]
@@ -339,6 +383,14 @@ class Context:
         return {"status": rc, "dH": list(dH), "accepted": [bool(a) for a in acc],
                 "energies": [list(en[6 * c:6 * c + 6]) for c in range(nc)],
                 "cg_iterations": list(its), "max_true_resid": list(res), "jump2": list(j2)}
+
+    def trajectory_stats(self, chain=0):
+        """Per-solve iterations and residuals and per-phase GPU times of the chain's last trajectory."""
+        st = TrajStats()
+        rc = self.lib.hmc_trajectory_stats(self.h, chain, ctypes.byref(st))
+        if rc:
+            raise HmcError(rc, self.lib.hmc_last_error(None).decode())
+        return st.as_dict()
 
     def philox_raw(self, key, ctr, nblocks):
         out = torch.empty(4 * nblocks, dtype=torch.int64, device=self.device)

@@ -12,7 +12,14 @@ and Section "Online metric estimation"), driving libhmc trajectories on the GPU.
 * Trajectory length (Eq. ESJD): for each candidate n, run proposals with n_leap = n and average
   (phi' - phi)^T M (phi' - phi) * alpha (the library reports the proposal's M-norm jump,
   accepted or not); n_max is the maximiser. Production runs draw n_leap ~ U{1 .. n_max}.
-* Metric (Eq. covest): sigma-hat <- mean over a batch of samples of |F phi|^2.
+* Metric (Eq. covest): sigma-hat <- mean over a batch of samples of |F phi|^2, or (centered)
+  the batch covariance mean |F phi|^2 - |F phi-bar|^2 about the batch mean phi-bar. Reading:
+  Sigma_true = <phi phi^T> is the covariance of a target whose mean vanishes by O(3) symmetry;
+  a warm-up batch of an ordered chain keeps its condensate, which the uncentered moment books on
+  the zero mode as a fluctuation of variance V |phi-bar|^2; the centered estimate equals
+  Eq. (covest) when the batch mean vanishes.
+* A proposal that fails (non-finite energy, solver failure) counts as alpha = 0; when alpha(eps)
+  is 0 the inequality is vacuous and eps shrinks.
 Every proposal is a full libhmc trajectory (heatbath, momentum, leapfrog, Metropolis), so the
 chain keeps moving while the statistics are gathered.
 
@@ -39,20 +46,26 @@ class Tuner:
         nz = self.noise(self.t) if self.noise else None
         if nz is None:
             o = self.ctx.trajectory([self.phi], [self.sigma], eps, n_leap, nrhs=self.nrhs,
-                                    precond=self.precond, seed=self.seed, counter=self.t)
+                                    precond=self.precond, seed=self.seed, counter=self.t, check=False)
         else:
             chi, z, u = nz
             o = self.ctx.trajectory([self.phi], [self.sigma], eps, n_leap, nrhs=self.nrhs,
-                                    precond=self.precond, chi=[chi], z=[z], u=[u])
+                                    precond=self.precond, chi=[chi], z=[z], u=[u], check=False)
         self.t += 1
         dH = o["dH"][0]
-        alpha = 1.0 if dH <= 0 else math.exp(-dH)
+        if o["status"] != 0 or not math.isfinite(dH):
+            alpha = 0.0   # the library restored phi
+        else:
+            alpha = 1.0 if dH <= 0 else math.exp(-dH)
         self.log.append((eps, n_leap, dH, o["accepted"][0]))
         return alpha, o["jump2"][0], dH, o["accepted"][0]
 
-    def tune_eps(self, eps, rounds, window, grow=1.2):
-        """Eq. (acc_ineq); returns the final eps and the history of (eps, a_eps, a_half)."""
+    def tune_eps(self, eps, rounds, window, grow=1.2, stop_after_turns=None):
+        """Eq. (acc_ineq); returns the final eps and the history of (eps, a_eps, a_half). With
+        stop_after_turns = n the rounds end once eps has changed direction n times (it then
+        oscillates around the largest step the inequality admits)."""
         hist = []
+        turns, last = 0, 0
         for _ in range(rounds):
             a1 = a2 = 0.0
             for _ in range(window):
@@ -60,7 +73,14 @@ class Tuner:
                 a2 += self.propose(0.5 * eps, 1)[0]
             a1, a2 = a1 / window, a2 / window
             hist.append((eps, a1, a2))
-            eps = eps * grow if a2 ** 2 <= 2.0 * a1 else eps / grow
+            up = a1 > 0.0 and a2 ** 2 <= 2.0 * a1
+            eps = eps * grow if up else eps / grow
+            d = 1 if up else -1
+            if last and d != last:
+                turns += 1
+            last = d
+            if stop_after_turns is not None and turns >= stop_after_turns:
+                break
         return eps, hist
 
     def tune_nmax(self, eps, candidates, per_candidate):
@@ -75,13 +95,39 @@ class Tuner:
         n_max = max(candidates, key=lambda n: esjd[n])
         return n_max, esjd
 
-    def estimate_sigma(self, eps, n_max, samples, jitter):
+    def estimate_sigma(self, eps, n_max, samples, jitter, centered=False):
         """Eq. (covest) over `samples` production updates (n_leap ~ U{1..n_max} via jitter(t))."""
-        acc = torch.zeros_like(self.sigma)
+        est = SigmaEstimator(self.ctx, self.phi, centered)
         for _ in range(samples):
             self.propose(eps, jitter(self.t, n_max))
-            self.ctx.metric(METRIC_ACCUM, self.sigma, self.phi, out=acc)
-        return acc / samples
+            est.add(self.phi)
+        return est.value()
+
+
+class SigmaEstimator:
+    """Running Eq. (covest): the library accumulates |F phi|^2 over the samples (METRIC_ACCUM);
+    with centered=True the batch mean phi-bar is kept as well and |F phi-bar|^2 is subtracted."""
+
+    def __init__(self, ctx, like, centered=False, chain=0):
+        self.ctx, self.centered, self.chain = ctx, centered, chain
+        self.acc = torch.zeros_like(like)
+        self.sum = torch.zeros_like(like) if centered else None
+        self.unused_sig = torch.ones_like(like)   # the accumulate op takes no metric
+        self.n = 0
+
+    def add(self, phi):
+        self.ctx.metric(METRIC_ACCUM, self.unused_sig, phi, out=self.acc, chain=self.chain)
+        if self.centered:
+            self.sum.add_(phi)
+        self.n += 1
+
+    def value(self):
+        m2 = self.acc / self.n
+        if not self.centered:
+            return m2
+        mean = self.sum / self.n
+        mm = self.ctx.metric(METRIC_ACCUM, self.unused_sig, mean, chain=self.chain)   # |F phi-bar|^2
+        return m2 - mm
 
 
 def uniform_jitter(seed):

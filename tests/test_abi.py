@@ -22,7 +22,7 @@ def header_struct_fields(name):
     body = m.group(1)
     fields = []
     for decl in body.split(";"):
-        decl = re.sub(r"\[\d+\]", "", decl).strip()
+        decl = re.sub(r"\[\w+\]", "", decl).strip()
         if not decl:
             continue
         parts = decl.split(",")
@@ -53,7 +53,8 @@ def test_library_exports_every_header_function(libpath):
 def test_binding_struct_layouts_match_header():
     from paper_2204_14241_gb300 import hmc
     for cname, pyt in [("hmc_params", hmc.Params), ("hmc_chain", hmc.Chain), ("hmc_cg_stats", hmc.CgStats),
-                       ("hmc_traj_in", hmc.TrajIn), ("hmc_traj_out", hmc.TrajOut)]:
+                       ("hmc_traj_in", hmc.TrajIn), ("hmc_traj_out", hmc.TrajOut),
+                       ("hmc_traj_stats", hmc.TrajStats)]:
         assert header_struct_fields(cname) == [f[0] for f in pyt._fields_], cname
 
 

@@ -603,3 +603,47 @@ def test_trajectory_stats_record():
     assert st["reliable_updates"] >= n_leap + 1
     ph = st["phase_ms"]
     assert all(v >= 0 for v in ph.values()) and ph["solve"] > 0 and ph["metric"] > 0
+
+
+@pytest.mark.parametrize("centered", [False, True])
+def test_sigma_estimate_matches_oracle(centered):
+    # Eq. (covest) accumulated by the library over a batch with a nonzero mean, as printed and
+    # about the batch mean (tuning.SigmaEstimator), against the oracle's estimates
+    from paper_2204_14241_gb300.tuning import SigmaEstimator
+    L, Nt = 6, 8
+    ctx = ctx_for(L, Nt)
+    mu = np.array([0.2, -0.1, 1.5])[:, None, None, None]
+    samples = [I.gaussian_field(950 + i, L, Nt) + mu for i in range(6)]
+    est = SigmaEstimator(ctx, dev(samples[0]), centered)
+    for s in samples:
+        est.add(dev(s))
+    got = I.to_paper_boson(est.value().cpu().numpy())
+    fn = ohmc.sigma_estimate_centered if centered else ohmc.sigma_estimate
+    ref = fn([I.to_paper_boson(s) for s in samples])
+    assert rel(got, ref) < 1e-12
+
+
+def test_device_wait_timeout_is_reported():
+    # The fused operator's device-side waits are bounded. With test_wait_timeout its first wait
+    # targets a barrier that nothing arms: the launch gives up after wait_spin_limit polls, drains
+    # its copy in flight and returns, and the call reports HMC_ERR_TIMEOUT; the context stays usable.
+    from paper_2204_14241_gb300.hmc import Context, HmcError, HMC_ERR_TIMEOUT
+    L, Nt = 16, 8
+    ctx = Context(L, Nt, solver="mixed", nrhs_max=1, cg_tol=1e-10, wait_spin_limit=64, test_wait_timeout=1,
+                  **COUPLINGS)
+    phi = dev(I.gaussian_field(1, L, Nt), torch.float32)
+    x = dev(I.fermion_noise(2, 1, L, Nt), torch.complex64)
+    with pytest.raises(HmcError) as e:
+        ctx.apply_MdagM(phi, x, norms=True)
+    assert e.value.code == HMC_ERR_TIMEOUT
+    with pytest.raises(HmcError) as e:
+        ctx.cg_solve(dev(I.gaussian_field(1, L, Nt)), dev(I.fermion_noise(2, 1, L, Nt)), precond=False)
+    assert e.value.code == HMC_ERR_TIMEOUT
+    y = ctx.apply_M(phi, x)   # no device-side waits on this path
+    P = oparams(L, Nt)
+    ref = fermion.apply_D(P, I.to_paper_boson(phi.double().cpu().numpy()), to_paper_vecs(x)[0])
+    assert rel(to_paper_vecs(y)[0], ref) < 1e-5
+    ok = ctx_for(L, Nt, "mixed", nrhs=1)
+    y2, n2 = ok.apply_MdagM(phi, x, norms=True)
+    assert rel(to_paper_vecs(y2)[0], fermion.apply_A(P, I.to_paper_boson(phi.double().cpu().numpy()),
+                                                       to_paper_vecs(x)[0])) < 1e-5
