@@ -58,7 +58,7 @@ WORKLOAD_BASE = (f"L={L}x{L}, Nt={NT} (dtau=0.1), 2 bands x 2 spins, {NRHS} pseu
                  f"degree-{GUESS} chronological initial guess; start: ordered field (amplitude {AMP} on one "
                  f"component + free-boson fluctuations), {N_THERM} thermalisation trajectories at eps={EPS0}, "
                  f"sigma-hat from Eq. (covest){' about the batch mean' if SIGMA_CENTERED else ''} over the last "
-                 f"{N_COVEST}, eps by Eq. (acc_ineq)")
+                 f"{N_COVEST}, eps by Eq. (acc_ineq) then backed off until a {NLEAP}-step trajectory is stable")
 # DRAM bytes (read + write) of one launch of the roofline kernel, the plain fused A on 8 RHS at
 # 80x80x160, from one ncu capture of `bench.py --profile-matvec 3`; None until that kernel has
 # been captured.
@@ -290,7 +290,10 @@ def run_ours(args):
     sig = est.value()
     sigma_ratio = (sig / sig_free)
     tuner = Tuner(ctx, phi, sig, nrhs=NRHS, precond=PRECOND, seed=seed + 1)
-    eps, eps_hist = tuner.tune_eps(EPS0, TUNE_ROUNDS, TUNE_WINDOW, grow=TUNE_GROW, stop_after_turns=TUNE_TURNS)
+    eps_single, eps_hist = tuner.tune_eps(EPS0, TUNE_ROUNDS, TUNE_WINDOW, grow=TUNE_GROW,
+                                          stop_after_turns=TUNE_TURNS)
+    # Eq. (acc_ineq) judges single steps; back off until a 40-step trajectory integrates stably
+    eps, eps_tries = tuner.stabilize_eps(eps_single, NLEAP, shrink=TUNE_GROW)
     warm = []
     for w in range(args.warmup):
         o = ctx.trajectory([phi], [sig], eps, NLEAP, nrhs=NRHS, precond=PRECOND, seed=seed, counter=500 + w,
@@ -411,7 +414,8 @@ def run_ours(args):
                         "sigma_hat_over_free_spectrum": {"median": float(sr.median().item()),
                                                           "mean": float(sr.mean().item()),
                                                           "max": float(sr.max().item())},
-                        "eps_tuning": [list(h) for h in eps_hist],
+                        "eps_tuning": [list(h) for h in eps_hist], "eps_single_step": eps_single,
+                        "eps_stability_tries": [list(t) for t in eps_tries],
                         "warmup_dH": [o["dH"][0] for o in warm], "warmup_status": [o["status"] for o in warm],
                         "untimed_warmup_seconds": t_warm},
                 "fp64_fma_peak_tflops": fp64_peak,
@@ -473,6 +477,22 @@ def run_profile_trajectory(args):
     ctx.close()
 
 
+def run_profile_force(args):
+    """One force evaluation of the workload (solve + force kernel), for an ncu capture of the FP64
+    force kernel and of the FP64 operator passes of the solve's reliable updates."""
+    import torch
+    from paper_2204_14241_gb300.hmc import Context
+    from paper_2204_14241_gb300 import inputs as I
+    phi_np, _ = synthetic_inputs(chain_seed(args.seed, 0))
+    phi = torch.from_numpy(phi_np).cuda()
+    pf = torch.from_numpy(I.fermion_noise(4, NRHS, L, NT)).cuda()
+    ctx = Context(L, NT, solver="mixed", nrhs_max=NRHS, cg_tol=TOL, cg_maxit=MAXIT, **COUPLINGS)
+    F, spf, sb, st = ctx.force(phi, pf, include_boson=True, precond=PRECOND)
+    torch.cuda.synchronize()
+    ctx.close()
+    print(json.dumps({"profile_force": 1, "S_pf": spf, **st}))
+
+
 def run_profile_matvec(args):
     """Only the dominant kernel: N launches of the fused A = D D^dagger (complex64, NRHS) on the
     benchmark's lattice, for an ncu capture of the last one."""
@@ -491,6 +511,74 @@ def run_profile_matvec(args):
     print(json.dumps({"profile_matvec": args.profile_matvec}))
 
 
+# ---- the batched configuration: 64 uneven chains ---------------------------------------------------
+B_NCHAINS, B_NRHS, B_EPS, B_NLEAP, B_GUESS = 64, 2, 0.02, 10, 3
+# ordered start: the uniform amplitude minimising S_B - 2 log det(D D^dagger) for two right-hand
+# sides is 1.5-1.7 across r in [0.2, 1] on these lattices
+B_AMP = 1.6
+
+
+def batched_chains():
+    """Chain i: L = {12, 16, 20, 24}[i mod 4], Nt = {24, 32, 48}[(i div 4) mod 3], r ~ U[0.2, 1]."""
+    from paper_2204_14241_gb300 import inputs as I
+    out = []
+    for i in range(B_NCHAINS):
+        L = (12, 16, 20, 24)[i % 4]
+        Nt = (24, 32, 48)[(i // 4) % 3]
+        out.append((L, Nt, 0.2 + 0.8 * I.uniform(900 + i)))
+    return out
+
+
+def run_batched_bench(args):
+    """64 independent chains of uneven lattices with 2 RHS each, every force solve of all chains in
+    one persistent launch; value = chain-trajectories per second. The same chains through the
+    serial path (one chain after another, same solver) are timed for comparison."""
+    import torch
+    from paper_2204_14241_gb300.hmc import Context
+    from paper_2204_14241_gb300 import inputs as I
+    chains = batched_chains()
+    dt = COUPLINGS["dtau"]
+    phis, sigs = [], []
+    for i, (L, Nt, r) in enumerate(chains):
+        phis.append(torch.from_numpy(I.ordered_field(5000 + i, L, Nt, r, kt(), 1.0 / np.sqrt(dt), B_AMP)).cuda())
+        sigs.append(torch.from_numpy(np.broadcast_to(I.spectrum(L, Nt, r, kt())[None] / dt, (3, Nt, L, L)).copy()).cuda())
+    kw = dict(solver="mixed", nrhs_max=B_NRHS, cg_tol=TOL, cg_maxit=MAXIT, chains=chains, initial_guess=B_GUESS,
+              **COUPLINGS)
+    res = {}
+    for mode, steps in (("batched", args.steps), ("serial", max(1, min(args.steps, 2)))):
+        ctx = Context(12, 24, batch_chains=1 if mode == "batched" else 0, **kw)
+        ph = [p.clone() for p in phis]
+        for w in range(args.warmup):
+            ctx.trajectory(ph, sigs, B_EPS, B_NLEAP, nrhs=B_NRHS, precond=False, seed=args.seed, counter=w, check=False)
+        torch.cuda.synchronize()
+        st = ctx.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = ctx.launches()
+        e0.record(st)
+        outs = [ctx.trajectory(ph, sigs, B_EPS, B_NLEAP, nrhs=B_NRHS, precond=False, seed=args.seed,
+                               counter=100 + k, check=False) for k in range(steps)]
+        e1.record(st)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1000.0
+        res[mode] = {"chain_traj_per_s": B_NCHAINS * steps / sec, "ms_per_step": 1000.0 * sec / steps, "steps": steps,
+                     "launches_per_step": (ctx.launches() - l0) / steps,
+                     "acceptance_rate": float(np.mean([a for o in outs for a in o["accepted"]])),
+                     "cg_iters_per_solve": float(np.mean([i for o in outs for i in o["cg_iterations"]])) / (B_NLEAP + 1),
+                     "status": sorted(set(o["status"] for o in outs))}
+        ctx.close()
+    line = {"metric": "chain trajectories/s, 64 uneven chains (batched configuration)",
+            "value": res["batched"]["chain_traj_per_s"], "unit": "chain-traj/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"{B_NCHAINS} chains, L in {{12,16,20,24}} x Nt in {{24,32,48}}, r ~ U[0.2,1], "
+                                   f"{B_NRHS} RHS, Yukawa lambda={LAMBDA}, eps={B_EPS}, n_leap={B_NLEAP}, ordered start "
+                                   f"(amplitude {B_AMP}), free-boson sigma-hat, complex64 CG with FP64 reliable "
+                                   f"updates to {TOL}, degree-{B_GUESS} chronological start",
+                       "total_sites": int(sum(L * L * Nt for L, Nt, _ in chains))},
+            "batched": res["batched"], "serial": res["serial"],
+            "speedup_vs_serial": res["batched"]["chain_traj_per_s"] / res["serial"]["chain_traj_per_s"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -506,10 +594,18 @@ def main():
                     help="run only two trajectories of the workload, the second inside an NVTX range")
     ap.add_argument("--profile-matvec", type=int, default=0,
                     help="run only this many launches of the fused A kernel (the roofline kernel)")
+    ap.add_argument("--profile-force", action="store_true",
+                    help="run only one force evaluation of the workload (for a capture of the FP64 kernels)")
+    ap.add_argument("--config", choices=["largest", "batched64"], default="largest",
+                    help="largest: the 80x80x160 chain (default); batched64: 64 uneven chains in batched launches")
     args = ap.parse_args()
     global CLOCK_LOG_DIR
     CLOCK_LOG_DIR = args.clock_log
-    if args.profile_trajectory:
+    if args.config == "batched64":
+        run_batched_bench(args)
+    elif args.profile_force:
+        run_profile_force(args)
+    elif args.profile_trajectory:
         run_profile_trajectory(args)
     elif args.profile_matvec:
         run_profile_matvec(args)

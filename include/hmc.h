@@ -87,7 +87,12 @@ typedef struct {
     int wait_spin_limit;   /* polls of a device-side wait before it gives up (0: 1 << 20); a wait
                               that gives up makes the call return HMC_ERR_TIMEOUT */
     int test_wait_timeout; /* nonzero (tests only): the first device-side wait of every fused-A
-                              launch targets a barrier that is never armed, so it always gives up */
+                              launch (and the first grid barrier of a batched solve) targets a
+                              barrier that nothing completes, so it always gives up */
+    int batch_chains;   /* nonzero: trajectory() advances all chains together and every force
+                           evaluation solves all (chain, RHS) pairs in one persistent cooperative
+                           launch (mixed solver mode only; CG without the preconditioner; grid
+                           barriers bounded by wait_spin_limit microseconds, default 2 s) */
 } hmc_params;
 
 /* Per-chain lattice (batched chains of uneven sizes). Coupling constants other than r

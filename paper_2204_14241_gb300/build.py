@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhmc.so")
-SOURCES = ["stencil.cu", "cg.cu", "fft.cu", "fft_ct.cu", "hmc.cu", "peak.cu", "strip.cu"]
+SOURCES = ["stencil.cu", "cg.cu", "fft.cu", "fft_ct.cu", "hmc.cu", "peak.cu", "strip.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

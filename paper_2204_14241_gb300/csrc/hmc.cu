@@ -191,6 +191,10 @@ static void free_all(hmc_ctx* ctx) {
                   ctx->d_part, ctx->d_red, ctx->d_cg, ctx->d_u32, ctx->d_flags};
     for (void* p : ps)
         if (p) cudaFree(p);
+    batch_free(ctx);
+    void* bs[] = {ctx->batch_phi32, ctx->d_energy, ctx->batch.bar, ctx->batch.iters, ctx->batch.ch};
+    for (void* b : bs)
+        if (b) cudaFree(b);
     for (cudaEvent_t e : ctx->events) cudaEventDestroy(e);
     ctx->events.clear();
     if (ctx->h_cg) cudaFreeHost(ctx->h_cg);
@@ -257,7 +261,14 @@ int hmc_init(const hmc_params* p, int n_chains, const hmc_chain* chains, void* c
         d.lat.V = (int64_t)Nt * L * L;
         d.r = r;
         ctx->chains.push_back(d);
+        ctx->batch_off.push_back(ctx->vtot);
+        ctx->vtot += d.lat.V;
         if (d.lat.V > ctx->vmax) ctx->vmax = d.lat.V;
+    }
+    const bool batch = p->batch_chains != 0;
+    if (batch && p->solver_mode != HMC_SOLVER_MIXED) {
+        delete ctx;
+        return fail(nullptr, HMC_ERR_ARG, "hmc_init: batch_chains needs solver_mode HMC_SOLVER_MIXED");
     }
     ctx->tstats.assign(n_chains, hmc_traj_stats{});
     ctx->tstats_valid.assign(n_chains, 0);
@@ -271,8 +282,10 @@ int hmc_init(const hmc_params* p, int n_chains, const hmc_chain* chains, void* c
         delete ctx;
         return rc;
     }
-    const int64_t nf = (int64_t)ctx->kmax * 4 * ctx->vmax;   // complex entries per workspace vector
-    const int64_t nb = 3 * ctx->vmax;
+    // the batched path keeps every chain's fermion vectors and momenta live at once
+    const int64_t vw = batch ? ctx->vtot : ctx->vmax;
+    const int64_t nf = (int64_t)ctx->kmax * 4 * vw;   // complex entries per workspace vector
+    const int64_t nb = 3 * ctx->vmax, nbw = 3 * vw;
     ctx->part_cap = 4 * (int64_t)ctx->kmax * 512;
     const int64_t need_a = (int64_t)ctx->kmax * (ctx->vmax / 16 + 1024);
     const int64_t need_m = 3 * ctx->vmax / 256 + 1024;
@@ -286,8 +299,12 @@ int hmc_init(const hmc_params* p, int n_chains, const hmc_chain* chains, void* c
         (rc = dalloc(ctx, &ctx->d_chi, nf)) || (rc = dalloc(ctx, &ctx->d_x32, mixed ? nf : 1)) ||
         (rc = dalloc(ctx, &ctx->d_r32, mixed ? nf : 1)) || (rc = dalloc(ctx, &ctx->d_p32, mixed ? nf : 1)) ||
         (rc = dalloc(ctx, &ctx->d_q32, mixed ? nf : 1)) || (rc = dalloc(ctx, &ctx->d_z32, mixed ? nf : 1)) ||
-        (rc = dalloc(ctx, &ctx->d_phi32, nb)) || (rc = dalloc(ctx, &ctx->d_phi_save, nb)) ||
-        (rc = dalloc(ctx, &ctx->d_pi, nb)) || (rc = dalloc(ctx, &ctx->d_F, nb)) || (rc = dalloc(ctx, &ctx->d_vel, nb)) ||
+        (rc = dalloc(ctx, &ctx->d_phi32, nb)) || (rc = dalloc(ctx, &ctx->d_phi_save, nbw)) ||
+        (rc = dalloc(ctx, &ctx->d_pi, nbw)) || (rc = dalloc(ctx, &ctx->d_F, nbw)) || (rc = dalloc(ctx, &ctx->d_vel, nbw)) ||
+        (batch && ((rc = dalloc(ctx, &ctx->batch_phi32, 3 * ctx->vtot)) ||
+                   (rc = dalloc(ctx, &ctx->d_energy, 7 * (int64_t)n_chains)) ||
+                   (rc = dalloc(ctx, &ctx->batch.bar, 2)) || (rc = dalloc(ctx, &ctx->batch.iters, 4)) ||
+                   (rc = dalloc(ctx, &ctx->batch.ch, n_chains)))) ||
         (rc = dalloc(ctx, &ctx->d_z, nb)) || (rc = dalloc(ctx, &ctx->d_fft, nb)) ||
         (rc = dalloc(ctx, &ctx->d_part, ctx->part_cap)) || (rc = dalloc(ctx, &ctx->d_red, 64)) ||
         (rc = dalloc(ctx, &ctx->d_cg, ctx->kmax)) || (rc = dalloc(ctx, &ctx->d_u32, 4)) ||
@@ -699,6 +716,206 @@ extern "C" int hmc_trajectory_stats(const hmc_ctx* ctx, int chain, hmc_traj_stat
     return HMC_OK;
 }
 
+// One HMC update of every chain together (hmc_params.batch_chains): the same steps as run_chain,
+// with the per-chain work issued back to back without host synchronisation and every force solve
+// of all chains in one persistent launch (batched_cg). Concatenated layouts: fermion vectors
+// [chain][k][V_c][4] at item offset K off_c, boson fields [chain][3][V_c] at 3 off_c. The host
+// synchronises once, for the energies and the Metropolis decisions.
+static int run_batched(hmc_ctx* ctx, const hmc_traj_in* in, hmc_traj_out* out) {
+    const int nc = (int)ctx->chains.size();
+    const int K = in->nrhs;
+    cudaStream_t sm = ctx->stream;
+    int rc;
+    PhaseTimer tm(ctx);
+    if ((rc = tm.mark(kPhaseOther))) return rc;
+    for (int c = 0; c < nc; ++c) {
+        ctx->tstats[c] = hmc_traj_stats{};
+        ctx->tstats_valid[c] = 0;
+    }
+    auto fvec = [&](double2* base, int c) { return base + (int64_t)K * 4 * ctx->batch_off[c]; };
+    auto bvec = [&](double* base, int c) { return base + 3 * ctx->batch_off[c]; };
+    std::vector<const double*> phis(nc);
+    double* E = ctx->d_energy;   // [6 c + j]: kinetic, S_B, S_PF at start and end; [6 nc + c]: uniform
+    // heatbath, momenta, initial energies
+    for (int c = 0; c < nc; ++c) {
+        const Lat& lat = ctx->chains[c].lat;
+        const int64_t nb = 3 * lat.V;
+        double* phi = (double*)in->phi[c];
+        phis[c] = phi;
+        HMC_CUDA(ctx, cudaMemcpyAsync(bvec(ctx->d_phi_save, c), phi, nb * sizeof(double), cudaMemcpyDeviceToDevice, sm));
+        const double2* chi;
+        const double* z;
+        if (in->noise == HMC_NOISE_EXPLICIT) {
+            chi = (const double2*)in->chi[c];
+            z = (const double*)in->z[c];
+            HMC_CUDA(ctx, cudaMemcpyAsync(E + 6 * nc + c, in->u + c, sizeof(double), cudaMemcpyHostToDevice, sm));
+        } else {
+            const uint64_t key = in->seed + 0x9E3779B97F4A7C15ull * (uint64_t)c;
+            if ((rc = gen_normal(ctx, key, in->counter, 0, (int64_t)K * 4 * lat.V, 1, (double*)ctx->d_chi))) return rc;
+            if ((rc = gen_normal(ctx, key, in->counter, 1ull << 48, nb, 0, ctx->d_z))) return rc;
+            k_philox_uniform<<<1, 1, 0, sm>>>(key, in->counter, 2ull << 48, E + 6 * nc + c);
+            HMC_LAUNCH(ctx, "k_philox_uniform");
+            chi = ctx->d_chi;
+            z = ctx->d_z;
+        }
+        if ((rc = launch_apply_D<double>(ctx, lat, phi, chi, fvec(ctx->d_pf, c), 0, K))) return rc;
+        k_norm2<<<1024, 256, 0, sm>>>((const double*)chi, (int64_t)K * 8 * lat.V, ctx->d_part);
+        HMC_LAUNCH(ctx, "k_norm2");
+        if ((rc = reduce_rows(ctx, ctx->d_part, 1, 1024, E + 6 * c + 2))) return rc;
+        const double* sig = (const double*)in->sigma_hat[c];
+        if ((rc = metric_op(ctx, lat, HMC_METRIC_MOMENTUM, sig, z, bvec(ctx->d_pi, c), 0.0, nullptr))) return rc;
+        if ((rc = metric_op(ctx, lat, HMC_METRIC_KINETIC, sig, bvec(ctx->d_pi, c), nullptr, 0.0, E + 6 * c))) return rc;
+        int nbb = 0;
+        if ((rc = launch_boson(ctx, lat, ctx->chains[c].r, phi, nullptr, ctx->d_part, &nbb))) return rc;
+        if ((rc = reduce_rows(ctx, ctx->d_part, 1, nbb, E + 6 * c + 1))) return rc;
+    }
+    // leapfrog with the chronological start over the concatenated solutions
+    const int mode = ctx->p.initial_guess;
+    double2* hist[kMaxGuess + 1] = {ctx->d_X};
+    for (int j = 1; j <= mode; ++j) hist[j] = ctx->d_Xhist[j - 1];
+    int nsol = 0, n_ru = 0;
+    const int64_t nall = (int64_t)K * 4 * ctx->vtot;
+    std::vector<int> its(nc);
+    std::vector<double> wres(nc);
+    std::vector<int> tot_it(nc, 0);
+    std::vector<double> worst(nc, 0.0);
+    auto do_force = [&](bool want) -> int {
+        const bool guess = mode && nsol >= 1;
+        const int np = guess ? std::min(nsol, mode + 1) : 0;
+        const int io = np < mode + 1 ? np : mode;
+        double2* xo = !guess ? hist[0] : hist[io];
+        if (guess) {
+            SolHist hs{};
+            double cb = np;
+            for (int j = 0; j < np; ++j) {
+                hs.h[j] = hist[j];
+                hs.c[j] = (j % 2 ? -cb : cb);
+                cb = cb * (np - j - 1) / (j + 2);
+            }
+            const unsigned ge = (unsigned)std::min<int64_t>((nall + 255) / 256, (int64_t)ctx->num_sms * 16);
+            switch (np) {
+                case 1: k_extrap<1><<<ge, 256, 0, sm>>>(hs, xo, nall); break;
+                case 2: k_extrap<2><<<ge, 256, 0, sm>>>(hs, xo, nall); break;
+                case 3: k_extrap<3><<<ge, 256, 0, sm>>>(hs, xo, nall); break;
+                case 4: k_extrap<4><<<ge, 256, 0, sm>>>(hs, xo, nall); break;
+                case 5: k_extrap<5><<<ge, 256, 0, sm>>>(hs, xo, nall); break;
+                default: k_extrap<6><<<ge, 256, 0, sm>>>(hs, xo, nall); break;
+            }
+            HMC_LAUNCH(ctx, "k_extrap");
+        }
+        int r2;
+        if ((r2 = tm.mark(kPhaseSolve))) return r2;
+        int nru = 0;
+        bool conv = false;
+        r2 = batched_cg(ctx, K, phis.data(), ctx->d_pf, xo, guess, ctx->p.cg_tol, ctx->p.cg_maxit, its.data(), &nru,
+                        wres.data(), &conv);
+        if (r2) return r2;
+        if ((r2 = tm.mark(kPhaseForce))) return r2;
+        for (int c = 0; c < nc; ++c) {
+            const ChainDesc& ch = ctx->chains[c];
+            int nb = 0;
+            if ((r2 = launch_force(ctx, ch.lat, ch.r, phis[c], fvec(xo, c), fvec(ctx->d_pf, c), K, bvec(ctx->d_F, c), 1,
+                                   ctx->d_part, &nb)))
+                return r2;
+            if (want) {
+                if ((r2 = reduce_rows(ctx, ctx->d_part, 1, nb, E + 6 * c + 5))) return r2;
+                if ((r2 = reduce_rows(ctx, ctx->d_part + nb, 1, nb, E + 6 * c + 4))) return r2;
+            }
+            hmc_traj_stats& ts = ctx->tstats[c];
+            if (ts.n_solves < HMC_MAX_SOLVES) {
+                ts.iterations[ts.n_solves] = its[c];
+                ts.true_resid[ts.n_solves] = wres[c];
+            }
+            ts.n_solves += 1;
+            ts.reliable_updates += nru;
+            tot_it[c] += its[c];
+            if (wres[c] > worst[c]) worst[c] = wres[c];
+        }
+        if ((r2 = tm.mark(kPhaseOther))) return r2;
+        if (guess) {
+            for (int j = io; j > 0; --j) hist[j] = hist[j - 1];
+            hist[0] = xo;
+        }
+        ++nsol;
+        n_ru += nru;
+        return HMC_OK;
+    };
+    const double eps = in->eps;
+    const int64_t nball = 3 * ctx->vtot;
+    const unsigned gball = (unsigned)((nball + 255) / 256);
+    rc = do_force(in->n_leap == 0);
+    if (!rc) {
+        k_axpy<<<gball, 256, 0, sm>>>(0.5 * eps, ctx->d_F, ctx->d_pi, nball);
+        HMC_LAUNCH(ctx, "k_axpy");
+        for (int i = 1; i <= in->n_leap && !rc; ++i) {
+            if ((rc = tm.mark(kPhaseMetric))) break;
+            for (int c = 0; c < nc && !rc; ++c)
+                rc = metric_op(ctx, ctx->chains[c].lat, HMC_METRIC_VELOCITY, (const double*)in->sigma_hat[c],
+                               bvec(ctx->d_pi, c), (double*)in->phi[c], eps, nullptr);
+            if (rc) break;
+            if ((rc = tm.mark(kPhaseOther))) break;
+            if ((rc = do_force(i == in->n_leap))) break;
+            k_axpy<<<gball, 256, 0, sm>>>(i < in->n_leap ? eps : 0.5 * eps, ctx->d_F, ctx->d_pi, nball);
+            HMC_LAUNCH(ctx, "k_axpy");
+        }
+    }
+    if (!rc) rc = tm.mark(kPhaseMetric);
+    for (int c = 0; c < nc && !rc; ++c) {
+        rc = metric_op(ctx, ctx->chains[c].lat, HMC_METRIC_KINETIC, (const double*)in->sigma_hat[c], bvec(ctx->d_pi, c),
+                       nullptr, 0.0, E + 6 * c + 3);
+        if (!rc && out && out->jump2) {
+            const Lat& lat = ctx->chains[c].lat;
+            const int64_t nb = 3 * lat.V;
+            k_sub<<<(unsigned)((nb + 255) / 256), 256, 0, sm>>>(phis[c], bvec(ctx->d_phi_save, c), ctx->d_vel, nb);
+            HMC_LAUNCH(ctx, "k_sub");
+            rc = metric_op(ctx, lat, HMC_METRIC_MNORM, (const double*)in->sigma_hat[c], ctx->d_vel, nullptr, 0.0,
+                           ctx->d_red + c % 64);
+            if (!rc) HMC_CUDA(ctx, cudaMemcpyAsync(out->jump2 + c, ctx->d_red + c % 64, sizeof(double),
+                                                   cudaMemcpyDeviceToHost, sm));
+        }
+    }
+    if (!rc) rc = tm.mark(kPhaseOther);
+    std::vector<double> he(7 * nc, 0.0);
+    if (!rc) {
+        HMC_CUDA(ctx, cudaMemcpyAsync(he.data(), E, 7 * nc * sizeof(double), cudaMemcpyDeviceToHost, sm));
+        HMC_CUDA(ctx, cudaStreamSynchronize(sm));
+    }
+    int first_err = rc;
+    for (int c = 0; c < nc; ++c) {
+        const Lat& lat = ctx->chains[c].lat;
+        const int64_t nb = 3 * lat.V;
+        double h = 0.0;
+        int acc = 0;
+        if (!rc) {
+            h = (he[6 * c + 3] + he[6 * c + 4] + he[6 * c + 5]) - (he[6 * c] + he[6 * c + 1] + he[6 * c + 2]);
+            if (!std::isfinite(h)) {
+                if (!first_err) first_err = fail(ctx, HMC_ERR_NONFINITE, "trajectory: non-finite energy change");
+            } else {
+                acc = he[6 * nc + c] < std::exp(-h) ? 1 : 0;
+            }
+        }
+        if (!acc)
+            HMC_CUDA(ctx, cudaMemcpyAsync((double*)in->phi[c], bvec(ctx->d_phi_save, c), nb * sizeof(double),
+                                          cudaMemcpyDeviceToDevice, sm));
+        if (out) {
+            if (out->dH) out->dH[c] = h;
+            if (out->accepted) out->accepted[c] = acc;
+            if (out->energies) for (int q = 0; q < 6; ++q) out->energies[6 * c + q] = rc ? 0.0 : he[6 * c + q];
+            if (out->cg_iterations) out->cg_iterations[c] = tot_it[c];
+            if (out->max_true_resid) out->max_true_resid[c] = worst[c];
+        }
+    }
+    if ((rc = tm.mark(kPhaseOther)) && !first_err) first_err = rc;
+    HMC_CUDA(ctx, cudaStreamSynchronize(sm));
+    double ms[4];
+    tm.collect(ms);
+    for (int c = 0; c < nc; ++c) {
+        for (int q = 0; q < 4; ++q) ctx->tstats[c].phase_ms[q] = ms[q];   // phases shared by all chains
+        ctx->tstats_valid[c] = first_err ? 0 : 1;
+    }
+    return first_err;
+}
+
 extern "C" int trajectory(hmc_ctx* ctx, const hmc_traj_in* in, hmc_traj_out* out) {
     if (!ctx || !in) return fail(ctx, HMC_ERR_ARG, "trajectory: null argument");
     int rc;
@@ -714,6 +931,7 @@ extern "C" int trajectory(hmc_ctx* ctx, const hmc_traj_in* in, hmc_traj_out* out
         if (in->noise == HMC_NOISE_EXPLICIT && (rc = check_ptrs(ctx, {in->chi[c], in->z[c]}))) return rc;
     }
     DevGuard g(ctx);
+    if (ctx->p.batch_chains) return run_batched(ctx, in, out);
     int first_err = HMC_OK;
     for (int c = 0; c < nc; ++c) {
         double e[6] = {0, 0, 0, 0, 0, 0}, dh = 0.0, worst = 0.0, j2 = 0.0;

@@ -41,6 +41,29 @@ struct ChainDesc {
     double r;
 };
 
+// Chain table of the batched solve (batch.cu): geometry, item offset of the chain's K
+// right-hand sides in the concatenated vectors, and its fields.
+struct BChainDev {
+    int L, Nt, LL;
+    float invL, invLL;
+    int64_t V;
+    int64_t off;
+    const double* phi64;
+    const float* phi32;
+};
+
+// Device state of the batched solve, built on first use for a right-hand-side count.
+struct BatchWork {
+    int K = 0, ntiles = 0, grid = 0;
+    void* tiles = nullptr;      // tile table
+    int* pair_t0 = nullptr;     // first tile of each (chain, RHS) pair
+    void* sc = nullptr;         // per-pair solver scalars
+    double* part = nullptr;     // per-tile partial sums
+    unsigned* bar = nullptr;    // grid barrier words
+    int* iters = nullptr;       // [0] iterations of the slowest pair, [1] reliable updates, [2] active pairs
+    BChainDev* ch = nullptr;    // chain table (n_chains entries)
+};
+
 // Per-RHS solver scalars, device resident (kernels read alpha/beta from here).
 struct CgScalars {
     double rr;        // <r, z> (or <r, r> without preconditioner) of the current iterate
@@ -75,6 +98,11 @@ struct hmc_ctx {
     std::vector<hmc::FftPlan> plans;
     std::vector<hmc::PcTables> pcs;
     std::vector<hmc::ATuned> atuned;   // tile shapes picked for the fused A kernel
+    hmc::BatchWork batch;                 // batched solve (hmc_params.batch_chains)
+    std::vector<int64_t> batch_off;       // site offset of each chain in the concatenated fields
+    int64_t vtot = 0;                     // sum of the chains' volumes
+    float* batch_phi32 = nullptr;         // FP32 copies of every chain's phi, concatenated
+    double* d_energy = nullptr;           // per chain: 6 energies and the Metropolis uniform
     std::vector<hmc_traj_stats> tstats;   // per chain: record of its last trajectory
     std::vector<int> tstats_valid;
     std::vector<cudaEvent_t> events;      // pool for the per-phase timing of trajectory()
@@ -229,6 +257,13 @@ int green_run(hmc_ctx* ctx, int chain, const double* phi, const double2* v, int 
 // bounds build: per-translation-unit device error words (0 in the normal build)
 unsigned int bounds_take_stencil();
 unsigned int bounds_take_strip();
+
+// batch.cu: all (chain, RHS) pairs of the context solve A X = b in one persistent launch (mixed
+// precision, no preconditioner). b, x: concatenated [chain][k][V][4] complex128 (x holds the start
+// when use_x0). Per chain: iterations of its slowest RHS and its worst final true residual.
+int batched_cg(hmc_ctx* ctx, int K, const double* const* phi, const double2* b, double2* x, bool use_x0, double tol,
+               int maxit, int* iterations, int* reliable_updates, double* worst_resid, bool* converged);
+void batch_free(hmc_ctx* ctx);
 
 // device error word: reads it (synchronising the stream) and returns HMC_ERR_TIMEOUT, clearing
 // it, if a bounded device-side wait gave up since the last check (hmc.cu)

@@ -63,9 +63,10 @@ class Tuner:
     def tune_eps(self, eps, rounds, window, grow=1.2, stop_after_turns=None):
         """Eq. (acc_ineq); returns the final eps and the history of (eps, a_eps, a_half). With
         stop_after_turns = n the rounds end once eps has changed direction n times (it then
-        oscillates around the largest step the inequality admits)."""
+        oscillates around the largest step the inequality admits) and the step returned is the
+        last one for which the inequality held."""
         hist = []
-        turns, last = 0, 0
+        turns, last, last_ok = 0, 0, None
         for _ in range(rounds):
             a1 = a2 = 0.0
             for _ in range(window):
@@ -74,14 +75,32 @@ class Tuner:
             a1, a2 = a1 / window, a2 / window
             hist.append((eps, a1, a2))
             up = a1 > 0.0 and a2 ** 2 <= 2.0 * a1
+            if up:
+                last_ok = eps
             eps = eps * grow if up else eps / grow
             d = 1 if up else -1
             if last and d != last:
                 turns += 1
             last = d
             if stop_after_turns is not None and turns >= stop_after_turns:
-                break
+                return (last_ok if last_ok is not None else eps), hist
         return eps, hist
+
+    def stabilize_eps(self, eps, n_leap, max_tries=8, shrink=1.5, max_abs_dH=1.0):
+        """Back eps off until a production-length trajectory (n_leap steps) integrates stably:
+        Eq. (acc_ineq) judges single steps, and a step that single steps tolerate can still drive
+        a long leapfrog trajectory unstable (non-finite energies or a solver failure). Each try is
+        one full update; eps is divided by `shrink` until a try ends with status 0 and
+        |dH| <= max_abs_dH. Returns (eps, list of (eps, dH, status))."""
+        tries = []
+        for _ in range(max_tries):
+            alpha, _, dH, _ = self.propose(eps, n_leap)   # alpha = 0 when the update failed
+            ok = math.isfinite(dH) and alpha > 0.0 and abs(dH) <= max_abs_dH
+            tries.append((eps, dH, ok))
+            if ok:
+                return eps, tries
+            eps /= shrink
+        return eps, tries
 
     def tune_nmax(self, eps, candidates, per_candidate):
         """Eq. (ESJD); returns n_max and {n: ESJD(n)}."""

@@ -647,3 +647,69 @@ def test_device_wait_timeout_is_reported():
     y2, n2 = ok.apply_MdagM(phi, x, norms=True)
     assert rel(to_paper_vecs(y2)[0], fermion.apply_A(P, I.to_paper_boson(phi.double().cpu().numpy()),
                                                        to_paper_vecs(x)[0])) < 1e-5
+
+
+def _uneven_chains(n=64):
+    chains = []
+    for i in range(n):
+        L = (12, 16, 20, 24)[i % 4]
+        Nt = (24, 32, 48)[(i // 4) % 3]
+        chains.append((L, Nt, 0.2 + 0.8 * I.uniform(900 + i)))
+    return chains
+
+
+@pytest.mark.parametrize("guess", [0, 3])
+def test_64_uneven_chains_batched_trajectory(guess):
+    # the batched configuration in its batched form: every force solve of the 64 chains (2 RHS each)
+    # is one persistent launch; chains checked against the oracle (PCG to 1e-13 there, 1e-12 here)
+    # and every chain against the serial path on the same explicit noise
+    from paper_2204_14241_gb300.hmc import Context
+    chains = _uneven_chains()
+    kw = dict(solver="mixed", nrhs_max=2, cg_tol=1e-12, chains=chains, initial_guess=guess, **COUPLINGS)
+    ctx_b = Context(12, 24, batch_chains=1, **kw)
+    ctx_s = Context(12, 24, **kw)
+    phis, sigs, chis, zs, us = [], [], [], [], []
+    for i, (L, Nt, r) in enumerate(chains):
+        phis.append(dev(I.gaussian_field(1000 + i, L, Nt) * 0.5))
+        sigs.append(dev(np.ones((3, Nt, L, L))))
+        chis.append(dev(I.fermion_noise(2000 + i, 2, L, Nt)))
+        zs.append(dev(I.gaussian_field(3000 + i, L, Nt)))
+        us.append(I.uniform(4000 + i))
+    phi_in = [p.clone() for p in phis]
+    phis_s = [p.clone() for p in phis]
+    out = ctx_b.trajectory(phis, sigs, 0.02, 2, nrhs=2, chi=chis, z=zs, u=us)
+    ref_s = ctx_s.trajectory(phis_s, sigs, 0.02, 2, nrhs=2, precond=False, chi=chis, z=zs, u=us)
+    assert out["status"] == 0 and max(out["max_true_resid"]) <= 1e-12
+    for i in range(64):
+        assert abs(out["dH"][i] - ref_s["dH"][i]) < 1e-8, (i, out["dH"][i], ref_s["dH"][i])
+        assert out["accepted"][i] == ref_s["accepted"][i]
+        assert rel(phis[i].cpu().numpy(), phis_s[i].cpu().numpy()) < 1e-9
+    for i in (0, 1, 6):
+        L, Nt, r = chains[i]
+        ref = ohmc.trajectory(oparams(L, Nt, r), I.to_paper_boson(phi_in[i].cpu().numpy()), np.ones((3, Nt, L, L)),
+                              [I.to_paper_fermion(chis[i].cpu().numpy()[k]) for k in range(2)],
+                              I.to_paper_boson(zs[i].cpu().numpy()), us[i], 0.02, 2, method="pcg", tol=1e-13)
+        assert abs(out["dH"][i] - ref["dH"]) < 1e-8, (i, out["dH"][i], ref["dH"])
+        assert out["accepted"][i] == ref["accept"]
+        assert rel(I.to_paper_boson(phis[i].cpu().numpy()), ref["phi"]) < 1e-9
+    st = ctx_b.trajectory_stats(5)
+    assert st["n_solves"] == 3 and sum(st["iterations"]) == out["cg_iterations"][5]
+
+
+def test_batched_grid_barrier_timeout():
+    # the batched solve's grid barriers are bounded: with test_wait_timeout its first barrier
+    # waits for one arrival more than there are blocks, gives up after wait_spin_limit
+    # microseconds, and the trajectory reports HMC_ERR_TIMEOUT with phi restored
+    from paper_2204_14241_gb300.hmc import Context, HMC_ERR_TIMEOUT
+    chains = _uneven_chains(4)
+    ctx = Context(12, 24, solver="mixed", nrhs_max=1, cg_tol=1e-10, chains=chains, batch_chains=1,
+                  test_wait_timeout=1, wait_spin_limit=20000, **COUPLINGS)
+    phis = [dev(I.gaussian_field(1100 + i, L, Nt) * 0.5) for i, (L, Nt, _) in enumerate(chains)]
+    phi_in = [p.clone() for p in phis]
+    sigs = [dev(np.ones((3, Nt, L, L))) for (L, Nt, _) in chains]
+    out = ctx.trajectory(phis, sigs, 0.02, 1, nrhs=1, seed=3, counter=0, check=False)
+    assert out["status"] == HMC_ERR_TIMEOUT
+    assert all(torch.equal(a, b) for a, b in zip(phis, phi_in))
+    ok = Context(12, 24, solver="mixed", nrhs_max=1, cg_tol=1e-10, chains=chains, batch_chains=1, **COUPLINGS)
+    o2 = ok.trajectory(phis, sigs, 0.02, 1, nrhs=1, seed=3, counter=0)
+    assert o2["status"] == 0 and all(np.isfinite(o2["dH"]))
