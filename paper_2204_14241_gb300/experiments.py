@@ -123,9 +123,11 @@ def main():
     ap.add_argument("--configs", type=int, default=3)
     ap.add_argument("--precision", action="store_true",
                     help="mixed vs FP64 on the 20 x 20 x 40 chain (100 trajectories) instead of the speedup sweep")
+    ap.add_argument("--tol", type=float, default=1e-10, help="solver tolerance of the precision report")
+    ap.add_argument("--trajectories", type=int, default=100)
     args = ap.parse_args()
     if args.precision:
-        r = precision_report()
+        r = precision_report(n_traj=args.trajectories, tol=args.tol)
         print(json.dumps({k: v for k, v in r.items() if k != "rows"}), flush=True)
         return
     Ls = (8, 16) if args.quick else (8, 12, 16, 20, 24, 32, 40)
