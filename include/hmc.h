@@ -147,9 +147,9 @@ int apply_MdagM(hmc_ctx* ctx, int chain, int prec, const void* phi, const void* 
  *   HMC_FP64 or HMC_FP32 (as for apply_MdagM); phi, x, y: device, layouts as for apply_MdagM,
  *   16-byte aligned, the byte range of y disjoint from those of x and phi; 1 <= nrhs <= 65535
  *   (<= 64 when norm2 is requested); cuda_stream: cudaStream_t or NULL for the default stream.
- * It always runs the generic fused kernel (the one apply_MdagM uses for FP64 and for lattices
- * without 16 x 16 tiles), never the complex64 16 x 16-tile kernel, so for complex64 with L a
- * multiple of 16 it is slower than apply_MdagM; the results agree to rounding.
+ * It always runs the generic fused kernel (the one apply_MdagM uses for FP64 and for L not a
+ * multiple of 16), never the complex64 strip kernel, so for complex64 with L a multiple of 16
+ * it is slower than apply_MdagM; the results agree to rounding.
  * Set-up: the first call on each device (with that device current) looks up the device
  * address of the scratch array (cudaGetSymbolAddress); make that first call before any
  * stream capture. Every call on a device shares the one array and overwrites it, and each

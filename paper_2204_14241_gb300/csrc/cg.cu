@@ -71,6 +71,29 @@ __global__ void __launch_bounds__(256) k_cg_xr(V16<R>* __restrict__ x, V16<R>* _
     if (threadIdx.x == 0) part[(int64_t)k * gridDim.x + blockIdx.x] = s;
 }
 
+// Fused complex64 update of plain CG: x += alpha p; r -= alpha q; p = r + beta p (beta known
+// before r: see k_cg_ab); partial ||r||^2. One pass over x, r, p, q.
+__global__ void __launch_bounds__(256) k_cg_xrp(float4* __restrict__ x, float4* __restrict__ r, float4* __restrict__ p,
+                                                const float4* __restrict__ q, int64_t n16, double* __restrict__ part,
+                                                const CgScalars* __restrict__ cgs) {
+    __shared__ double red[8];
+    const int k = blockIdx.y;
+    if (!cgs[k].active) return;
+    const float alpha = (float)cgs[k].alpha, beta = (float)cgs[k].beta;
+    const int64_t off = k * n16;
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 pv = p[off + i];
+        x[off + i] = v_axpy(alpha, pv, x[off + i]);
+        const float4 rn = v_axpy(-alpha, q[off + i], r[off + i]);
+        r[off + i] = rn;
+        p[off + i] = v_axpy(beta, pv, rn);
+        s += v_dot(rn, rn);
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) part[(int64_t)k * gridDim.x + blockIdx.x] = s;
+}
+
 __device__ __forceinline__ double row_sum(const double* part, int nblk, double* red) {
     double s = 0.0;
     for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += part[i];
@@ -90,10 +113,34 @@ __global__ void k_cg_alpha(CgScalars* cgs, const double* __restrict__ part, int 
     }
 }
 
-// r2 = ||r||^2, rz_new = <r, z> (= r2 without preconditioner), beta, convergence flags
+// Plain CG with beta ahead of the residual update: alpha = <r, r> / <p, A p> and
+//   ||r - alpha A p||^2 = ||r||^2 - 2 alpha Re<r, A p> + alpha^2 ||A p||^2 = alpha^2 ||A p||^2 - ||r||^2,
+// since <r, A p> = <p, A p> for a direction p = r + beta' p' conjugate to the previous one
+// (<p', A p> = 0) and alpha <p, A p> = ||r||^2. beta = that norm / ||r||^2 (0 if rounding makes it
+// negative, which restarts the direction). The residual norm itself comes from the update pass.
+__global__ void k_cg_ab(CgScalars* cgs, const double* __restrict__ part_pap, const double* __restrict__ part_qq,
+                        int nblk) {
+    __shared__ double red[8];
+    const int k = blockIdx.x;
+    if (!cgs[k].active) return;
+    const double pAp = row_sum(part_pap + (int64_t)k * nblk, nblk, red);
+    const double qq = row_sum(part_qq + (int64_t)k * nblk, nblk, red);
+    if (threadIdx.x == 0) {
+        CgScalars& c = cgs[k];
+        c.pAp = pAp;
+        const double alpha = (pAp > 0.0 && isfinite(pAp)) ? c.rr / pAp : 0.0;
+        const double rnext = alpha * alpha * qq - c.rr;
+        c.alpha = alpha;
+        c.beta = (c.rr > 0.0 && rnext > 0.0) ? rnext / c.rr : 0.0;
+        if (!isfinite(pAp) || !isfinite(qq)) c.nonfinite = 1;
+    }
+}
+
+// r2 = ||r||^2, rz_new = <r, z> (= r2 without preconditioner), beta (unless set_beta is 0: the
+// fused plain update took it from k_cg_ab), convergence flags
 __global__ void k_cg_beta(CgScalars* cgs, const double* __restrict__ part_r2,
                           const double* __restrict__ part_rz, int nblk, int nblk_rz, double tol2, double delta2,
-                          int mixed) {
+                          int mixed, int set_beta) {
     __shared__ double red[8];
     const int k = blockIdx.x;
     if (!cgs[k].active) return;
@@ -101,7 +148,7 @@ __global__ void k_cg_beta(CgScalars* cgs, const double* __restrict__ part_r2,
     const double rz = part_rz ? row_sum(part_rz + (int64_t)k * nblk_rz, nblk_rz, red) : r2;
     if (threadIdx.x == 0) {
         CgScalars& c = cgs[k];
-        c.beta = c.rr > 0.0 ? rz / c.rr : 0.0;
+        if (set_beta) c.beta = c.rr > 0.0 ? rz / c.rr : 0.0;
         c.rr = rz;
         c.r2 = r2;
         c.iters += 1;
@@ -319,6 +366,10 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
         return HMC_OK;
     };
     if ((rc = restart_dir())) return rc;
+    // plain complex64 CG on the strip operator: beta comes ahead of the residual update (k_cg_ab),
+    // so x, r and p are updated in one pass; the first direction is p = r
+    const bool fused = kMixed && !precond && strip_supported(lat);
+    if (fused) HMC_CUDA(ctx, cudaMemcpyAsync(pv, rv, nrhs * n * sizeof(C), cudaMemcpyDeviceToDevice, sm));
 
     // true-residual update for every active RHS
     int n_ru = 0;
@@ -351,13 +402,26 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
                 int nbr = 0, nbz = 0;
                 if ((rc = launch_pcg_xy_forward(ctx, lat, xv, rv, pv, qv, zv, nrhs, cgs, part, part2, &nbr, &nbz)))
                     return rc;
-                k_cg_beta<<<nrhs, 256, 0, sm>>>(cgs, part, part2, nbr, nbz, tol2, delta2, kMixed);
+                k_cg_beta<<<nrhs, 256, 0, sm>>>(cgs, part, part2, nbr, nbz, tol2, delta2, kMixed, 1);
                 HMC_LAUNCH(ctx, "k_cg_beta");
                 if ((rc = launch_pcg_xy_inverse(ctx, lat, zv, pv, pw, nrhs, cgs))) return rc;
                 { C* t = pv; pv = pw; pw = t; }
             }
         }
-        if (!xy) {
+        if (fused) {
+            if constexpr (kMixed) {
+                // q = A p with <p, A p> and ||A p||^2; alpha and beta; x, r, p; ||r||^2 and the flags
+                if ((rc = launch_apply_A_strip(ctx, lat, phiR, pv, qv, nrhs, part, &nb, cgs, part2))) return rc;
+                k_cg_ab<<<nrhs, 256, 0, sm>>>(cgs, part, part2, nb);
+                HMC_LAUNCH(ctx, "k_cg_ab");
+                k_cg_xrp<<<vgrid, 256, 0, sm>>>(reinterpret_cast<float4*>(xv), reinterpret_cast<float4*>(rv),
+                                                reinterpret_cast<float4*>(pv), reinterpret_cast<const float4*>(qv),
+                                                n16, part, cgs);
+                HMC_LAUNCH(ctx, "k_cg_xrp");
+                k_cg_beta<<<nrhs, 256, 0, sm>>>(cgs, part, nullptr, kRedBlocks, kRedBlocks, tol2, delta2, kMixed, 0);
+                HMC_LAUNCH(ctx, "k_cg_beta");
+            }
+        } else if (!xy) {
         if (kMixed && strip_supported(lat)) {
             // p = z + beta p as a streaming pass, then q = A p on the complex64 strip kernel (the
             // operator with the update folded in has no strip form: it would stage two vectors)
@@ -383,7 +447,7 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
                                               n16, part, cgs);
             HMC_LAUNCH(ctx, "k_cg_xr");
         }
-        k_cg_beta<<<nrhs, 256, 0, sm>>>(cgs, part, precond ? part2 : nullptr, nbr, nbz, tol2, delta2, kMixed);
+        k_cg_beta<<<nrhs, 256, 0, sm>>>(cgs, part, precond ? part2 : nullptr, nbr, nbz, tol2, delta2, kMixed, 1);
         HMC_LAUNCH(ctx, "k_cg_beta");
         }
         ++it;

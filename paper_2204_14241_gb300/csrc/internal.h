@@ -207,10 +207,11 @@ int launch_apply_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x,
                    int nrhs, double* part, int* nblk_out, const CgScalars* cgs = nullptr,
                    const cplx<R>* pold = nullptr, cplx<R>* pnew = nullptr);
 // strip.cu: the complex64 plain operator on full-height strips (L a multiple of 16 up to 80);
-// same contract as launch_apply_A without the direction update.
+// same contract as launch_apply_A without the direction update. part_q (may be null): partial
+// sums of ||A x||^2, laid out like part.
 bool strip_supported(const Lat& lat);
 int launch_apply_A_strip(hmc_ctx* ctx, const Lat& lat, const float* phi, const float2* x, float2* y, int nrhs,
-                         double* part, int* nblk_out, const CgScalars* cgs);
+                         double* part, int* nblk_out, const CgScalars* cgs, double* part_q = nullptr);
 // fermion (+ boson) force and the action pieces, see force() in hmc.h.
 int launch_force(hmc_ctx* ctx, const Lat& lat, double r, const double* phi, const double2* X,
                  const double2* pf, int nrhs, double* F, int include_boson, double* part,

@@ -1,20 +1,24 @@
 // Fused complex64 y = A x = D (D^dagger x) (Eq. linsys) on full-height strips, for L a multiple
 // of 16 up to 80.
 //
-// A block owns one strip of 16 columns x all L rows of one right-hand side and marches through a
-// chunk of time slices. Because the strip spans the whole periodic y extent there is no halo in
+// A pipeline is one strip of 16 columns x all L rows of one right-hand side, marched through a
+// range of time slices. Because the strip spans the whole periodic y extent there is no halo in
 // y; in x it stages two extra columns on each side (20 columns of x) and computes t_ = D^dagger x
-// on one extra column on each side (18 columns). 256 threads own a column of NY = L / 16
-// consecutive rows each (16 columns x 16 row segments); a ninth warp computes t_ on the two extra
-// columns. A thread walks down its column with a three-row window in registers, so each row's
-// y-neighbours cost one shared-memory site read instead of two: about 3.4 site reads of x and 3.4
-// of t_ per output site, against 5 and 5 for one site per thread; x(t-1) of its rows stays in
-// registers for the time hop.
+// on one extra column on each side (18 columns). 16 x NSEG threads own a column segment of
+// NY = L / NSEG consecutive rows each and walk down it with a three-row window in registers, so
+// each row's y-neighbours cost one shared-memory site read instead of two; x(t-1) of its rows
+// stays in registers for the time hop. 2 x NSEG side threads compute t_ on the two extra columns,
+// each on the rows s, s + NSEG, ... so that the eight threads of a quarter warp read distinct
+// bank groups.
 //
-// Per step t (x(t+1) landed in the three-slice cp.async ring): barrier; t_(t+1) = D^dagger x on
-// the thread's rows into registers; y(t) = D t_ from t_(t) in shared memory and t_(t+1) in
-// registers, stored to global; barrier; t_(t+1) into shared memory, x(t+4) issued into the
-// buffer that held x(t+1). The site arithmetic runs on packed (re, im) pairs with Blackwell's
+// The blocks of one time chunk run all strips and right-hand sides together, so a strip's halo
+// columns are read while its neighbour strip has the same slices in L2. (An even split of all
+// outputs over one block per SM, which ends the partial last wave, put neighbouring strips at
+// different slices and ran slower.)
+//
+// Per step t (x(t+1) landed in its TMA slot): barrier; t_(t+1) = D^dagger x on the thread's rows
+// into shared memory; y(t) = D t_ from t_(t) and the thread's own t_(t+1), stored with one
+// 32-byte store per site. The site arithmetic runs on packed (re, im) pairs with Blackwell's
 // two-wide FP32 instructions (add/mul/fma .f32x2).
 #include <cuda.h>
 
@@ -170,10 +174,11 @@ __device__ __forceinline__ P4 ldg_p4(const Site<float>* p) {
     s.c[0] = a.x; s.c[1] = a.y; s.c[2] = b.x; s.c[3] = b.y;
     return s;
 }
+// One 32-byte store per site (sites are 32-byte aligned).
 __device__ __forceinline__ void stg_p4(Site<float>* p, const P4& s) {
-    ulonglong2* q = reinterpret_cast<ulonglong2*>(p);
-    q[0] = make_ulonglong2(s.c[0], s.c[1]);
-    q[1] = make_ulonglong2(s.c[2], s.c[3]);
+    asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(s.c[0]), "l"(s.c[1]), "l"(s.c[2]),
+                 "l"(s.c[3])
+                 : "memory");
 }
 
 // ---- TMA and mbarrier primitives (inline PTX) ---------------------------------------------------
@@ -202,6 +207,12 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
         ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
         : "memory");
 }
+// Bulk-tensor prefetch of a box into L2 (no shared memory, no barrier).
+__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3) {
+    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+                 : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Tensor maps of one launch: x viewed as [slice = k * Nt + t][y][x][8 floats] (box: whole sites of
@@ -219,29 +230,28 @@ struct StripMaps {
 // m & 1 on that slot's mbarrier, issued by thread 0 one step ahead. t_ lives in two slices.
 // Step m: wait for slot m & 1; barrier (also the end of step m - 1); thread 0 issues slice m + 1
 // into the other slot (read in step m - 1; phi of the rows a thread needs for y is kept in its
-// registers from step m - 1); t_(ta + m) = D^dagger x on the own rows, written to the
-// t_ slice that y(ta + m - 2) read one step earlier; y(ta + m - 1) = D t_ from t_(ta + m - 1) and
+// registers from step m - 1); t_(ta + m) = D^dagger x on the thread's rows, written to the t_
+// slice that y(ta + m - 2) read one step earlier; y(ta + m - 1) = D t_ from t_(ta + m - 1) and
 // the thread's own t_(ta + m). A thread reads its own t_(ta + m) only, so one barrier per step.
 // Waits are bounded (wait_limit polls): on a timeout the block drains the copy in flight, sets
 // err[0] and returns. test_timeout makes the first wait target a barrier that is never armed.
-template <int L, int NY>
+// Slices prefetched into L2 ahead of the one loaded into the free slot: the two shared-memory
+// slots keep one slice (66 KB at L = 80) in flight per SM, too little to cover the DRAM latency.
+#ifndef STRIP_PREFETCH
+#define STRIP_PREFETCH 3
+#endif
+
+template <int L, int NY, bool QN>
 __global__ void __launch_bounds__(StripShape<L, NY>::NTHR, 1)
 k_apply_A_strip(const __grid_constant__ StripMaps maps, Lat lat, CoefP cf, int nch, int C,
                 const float* __restrict__ phi, const Site<float>* __restrict__ x, Site<float>* __restrict__ y,
-                double* __restrict__ part, const CgScalars* __restrict__ cgs, int* __restrict__ err, int wait_limit,
-                int test_timeout) {
+                double* __restrict__ part, double* __restrict__ part_q, const CgScalars* __restrict__ cgs,
+                int* __restrict__ err, int wait_limit, int test_timeout) {
     using S = StripShape<L, NY>;
-    constexpr int TC = S::TC;
+    constexpr int TC = S::TC, NSEG = S::NSEG;
     constexpr int nstrip = L / 16, LL = L * L;
-    const int P = gridDim.x / nch;
-    const int c = blockIdx.x / P, p = blockIdx.x - c * P;
-    const int k = p / nstrip, sx = p - k * nstrip;
-    if (cgs && !cgs[k].active) return;
     const int Nt = lat.Nt;
     const int64_t V = lat.V;
-    const int ta = c * C;
-    const int tb = min(ta + C, Nt);            // outputs y(ta .. tb-1); slices x(ta - 1 .. tb)
-    const int x0 = sx * 16;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sbase = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     ulonglong2* tr = reinterpret_cast<ulonglong2*>(sbase + 2 * S::SLOT);   // 2 slices x [2 planes][L rows][18 columns]
@@ -251,6 +261,7 @@ k_apply_A_strip(const __grid_constant__ StripMaps maps, Lat lat, CoefP cf, int n
     const int tid = threadIdx.x;
     const bool own_y = tid < S::NMAIN;
     const bool has_t = tid < S::NMAIN + S::NRING;
+    const bool side = has_t && !own_y;
     int tcol = 0, seg = 0;
     if (own_y) {
         tcol = 1 + (tid & 15);
@@ -260,6 +271,9 @@ k_apply_A_strip(const __grid_constant__ StripMaps maps, Lat lat, CoefP cf, int n
         tcol = (r & 1) ? TC - 1 : 0;
         seg = r >> 1;
     }
+    // row j of the thread: seg * NY + j (main), seg + NSEG * j (side)
+    const int rstep = own_y ? 1 : NSEG;
+    const int row0 = own_y ? seg * NY : seg;
     // staged x column of strip column j (j in [-2, 17]): its region (16-byte units from the slot),
     // the column within the region and the region's sites per row
     auto xcol_of = [&](int j, int& reg, int& col, int& rs) {
@@ -271,13 +285,14 @@ k_apply_A_strip(const __grid_constant__ StripMaps maps, Lat lat, CoefP cf, int n
     xcol_of(tcol - 1, gc, oc, rc_);
     xcol_of(tcol - 2, gl, ol, rl);
     xcol_of(tcol, gr, orr, rr);
-    int gx = x0 - 1 + tcol;
-    gx = gx < 0 ? gx + L : (gx >= L ? gx - L : gx);
-    const int row0 = seg * NY;
-    const int rup = row0 == 0 ? L - 1 : row0 - 1;          // row above the thread's column
-    const int rdn = row0 + NY == L ? 0 : row0 + NY;         // row below it
-    const Site<float>* xk = x + (int64_t)k * V;
-    Site<float>* yk = y + (int64_t)k * V;
+    constexpr int lim_slot = S::SLOT / 16;
+
+    const int P = gridDim.x / nch;
+    const int c = blockIdx.x / P, p = blockIdx.x - c * P;
+    const int k = p / nstrip, sx = p - k * nstrip;
+    const bool active = !cgs || cgs[k].active;   // a converged right-hand side is left as it is
+    const int ta = c * C;
+    const int tb = min(ta + C, Nt);            // outputs y(ta .. tb-1); slices x(ta - 1 .. tb)
 
     const uint32_t bar0 = smem_u32(&bars[0]);
     if (tid == 0) {
@@ -287,58 +302,76 @@ k_apply_A_strip(const __grid_constant__ StripMaps maps, Lat lat, CoefP cf, int n
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const int xl_col = x0 - 2 < 0 ? x0 - 2 + L : x0 - 2;
-    const int xr_col = x0 + 16 >= L ? x0 + 16 - L : x0 + 16;
     constexpr uint32_t kSlotBytes = (uint32_t)S::SLOT;
+    u64 acc = 0;   // (sum re^2, sum im^2) of t_ on the own output sites; with QN (sum |t_|^2, sum |y|^2)
+    const int x0 = sx * 16;
+    int gx = x0 - 1 + tcol;
+    gx = gx < 0 ? gx + L : (gx >= L ? gx - L : gx);
+    const Site<float>* xk = x + (int64_t)k * V;
+    Site<float>* yk = y + (int64_t)k * V;
+    // x columns x0 - 2, x0 - 1 and x0 + 16, x0 + 17 of the side boxes (thread 0 only)
+    auto side_cols = [&](int& xl, int& xr) {
+        xl = x0 - 2 < 0 ? x0 - 2 + L : x0 - 2;
+        xr = x0 + 16 >= L ? x0 + 16 - L : x0 + 16;
+    };
     auto issue = [&](int slot, int t) {   // thread 0 only
         const uint32_t bar = bar0 + 8 * slot;
         const uint32_t dst = smem_u32(sbase + slot * S::SLOT);
         const int sl = k * Nt + t;
+        int xl, xr;
+        side_cols(xl, xr);
         mbar_expect_tx(bar, kSlotBytes);
         tma_load_4d(dst, &maps.xmain, 0, x0, 0, sl, bar);
-        tma_load_4d(dst + S::OFF_XL, &maps.xhalo, 0, xl_col, 0, sl, bar);
-        tma_load_4d(dst + S::OFF_XR, &maps.xhalo, 0, xr_col, 0, sl, bar);
+        tma_load_4d(dst + S::OFF_XL, &maps.xhalo, 0, xl, 0, sl, bar);
+        tma_load_4d(dst + S::OFF_XR, &maps.xhalo, 0, xr, 0, sl, bar);
         tma_load_4d(dst + S::OFF_PHI, &maps.phi, x0, 0, t, 0, bar);
     };
-    const float eta0 = ((gx + row0) & 1) ? -1.f : 1.f;   // (-1)^(x+y) of the first row; it alternates along y
-    const bool ring_phi = has_t && !own_y;                 // the side columns' phi is not staged
+    auto prefetch = [&](int t) {   // thread 0 only: the boxes of slice t into L2
+        const int sl = k * Nt + t;
+        int xl, xr;
+        side_cols(xl, xr);
+        tma_prefetch_4d(&maps.xmain, 0, x0, 0, sl);
+        tma_prefetch_4d(&maps.xhalo, 0, xl, 0, sl);
+        tma_prefetch_4d(&maps.xhalo, 0, xr, 0, sl);
+        tma_prefetch_4d(&maps.phi, x0, 0, t, 0);
+    };
+    auto slice_of = [&](int m) { return ta + m >= Nt ? ta + m - Nt : ta + m; };
+    const float eta0 = ((gx + row0) & 1) ? -1.f : 1.f;   // (-1)^(x+y) of row 0 of the thread
 
-    // prologue: x(ta - 1) on the own rows, slice ta in flight
+    // x(ta - 1) of the thread's rows; phi of slice ta on the side columns (not staged)
     P4 xprev[NY];
-    if (has_t) {
+    float phk[NY][3];   // main: phi of the last t_ slice (the next y needs it); side: phi of the next t_ slice
+    if (has_t && active) {
         const int tm = ta == 0 ? Nt - 1 : ta - 1;
-        const Site<float>* src = xk + (int64_t)tm * LL + row0 * L + gx;
 #pragma unroll
         for (int j = 0; j < NY; ++j) {
+            const int row = row0 + j * rstep;
             xprev[j] = P4{};
-            if (HMC_IN(tm >= 0 && tm < Nt && row0 + j < L && gx >= 0 && gx < L, kBndStripGlobal))
-                xprev[j] = ldg_p4(src + j * L);
-        }
-    }
-    const int nsl = tb - ta + 1;   // staged slices x(ta) .. x(tb)
-    if (tid == 0) issue(0, ta);
-
-    u64 acc = 0;   // (sum re^2, sum im^2) of t_ on the own output sites
-    float phk[NY][3];   // phi of the own rows at the slice of the last t_ (the next y needs it; its slot is refilled)
-    for (int m = 0; m < nsl; ++m) {
-        const int slot = m & 1;
-        const int tn_slice = ta + m >= Nt ? ta + m - Nt : ta + m;   // slice of t_ computed now
-        float phr[NY][3];   // phi of the side columns (ring threads only)
-        if (ring_phi) {
-            const float* pp = phi + (int64_t)tn_slice * LL + row0 * L + gx;
-#pragma unroll
-            for (int j = 0; j < NY; ++j) {
-                phr[j][0] = __ldg(pp + j * L);
-                phr[j][1] = __ldg(pp + V + j * L);
-                phr[j][2] = __ldg(pp + 2 * V + j * L);
+            if (HMC_IN(tm >= 0 && tm < Nt && row < L && gx >= 0 && gx < L, kBndStripGlobal))
+                xprev[j] = ldg_p4(xk + (int64_t)tm * LL + row * L + gx);
+            if (side) {
+                const float* pp = phi + (int64_t)ta * LL + row * L + gx;
+                phk[j][0] = __ldg(pp);
+                phk[j][1] = __ldg(pp + V);
+                phk[j][2] = __ldg(pp + 2 * V);
             }
         }
+    }
+    const int nsl = active ? tb - ta + 1 : 0;   // staged slices x(ta) .. x(tb)
+    if (tid == 0 && nsl > 0) {
+        issue(0, ta);
+        for (int m = 1; m <= STRIP_PREFETCH && m < nsl; ++m) prefetch(slice_of(m));
+    }
+    for (int m = 0; m < nsl; ++m) {
+        const int slot = m & 1;
+        const uint32_t par = (uint32_t)((m >> 1) & 1);
+        const int tn_slice = ta + m >= Nt ? ta + m - Nt : ta + m;   // slice of t_ computed now
         const bool ok = (test_timeout && m == 0) ? mbar_wait(bar0 + 16, 0, wait_limit)
-                                                 : mbar_wait(bar0 + 8 * slot, (m >> 1) & 1, wait_limit);
+                                                  : mbar_wait(bar0 + 8 * slot, par, wait_limit);
         if (__syncthreads_or(!ok)) {
             // drain the copy in flight into this slot before leaving (bounded as well)
             if (tid == 0) {
-                if (!mbar_wait(bar0 + 8 * slot, (m >> 1) & 1, wait_limit)) atomicOr(err, 2);
+                if (!mbar_wait(bar0 + 8 * slot, par, wait_limit)) atomicOr(err, 2);
                 atomicOr(err, 1);
             }
             __syncthreads();
@@ -346,55 +379,77 @@ k_apply_A_strip(const __grid_constant__ StripMaps maps, Lat lat, CoefP cf, int n
         }
         if (tid == 0 && m + 1 < nsl) {
             fence_proxy_async();
-            issue(slot ^ 1, ta + m + 1 >= Nt ? ta + m + 1 - Nt : ta + m + 1);
+            issue(slot ^ 1, slice_of(m + 1));
+            if (m + 1 + STRIP_PREFETCH < nsl) prefetch(slice_of(m + 1 + STRIP_PREFETCH));
         }
         const ulonglong2* xb = reinterpret_cast<const ulonglong2*>(sbase + slot * S::SLOT);
         const float* phs = reinterpret_cast<const float*>(sbase + slot * S::SLOT + S::OFF_PHI);
-        ulonglong2* tn = tr + slot * S::TS;                 // t_(ta + m)
-        const ulonglong2* tc = tr + (slot ^ 1) * S::TS;    // t_(ta + m - 1)
+        ulonglong2* tn = tr + slot * S::TS;                 // t_(tn_slice)
+        const ulonglong2* tc = tr + (slot ^ 1) * S::TS;    // t_(tn_slice - 1)
+        const u64 ts = tn_slice == 0 ? pk2(-1.f, -1.f) : pk2(1.f, 1.f);   // b(t - 1) of D^dagger
+        const ulonglong2 *xc_r = xb + gc, *xl_r = xb + gl, *xr_r = xb + gr;
         // y(t) needs phi(t) of its rows, kept from the previous t_ step
         float phc[NY][3];
 #pragma unroll
         for (int j = 0; j < NY; ++j)
 #pragma unroll
             for (int a = 0; a < 3; ++a) phc[j][a] = phk[j][a];
-        // t_(tn_slice) = D^dagger x on the own rows, into shared memory
-        if (has_t) {
-            const u64 ts = tn_slice == 0 ? pk2(-1.f, -1.f) : pk2(1.f, 1.f);   // b(t - 1)
-            const ulonglong2 *xc_r = xb + gc, *xl_r = xb + gl, *xr_r = xb + gr;
-            P4 up = lds_site(xc_r, rup * rc_ + oc, S::SLOT / 16 - gc);
-            P4 cen = lds_site(xc_r, row0 * rc_ + oc, S::SLOT / 16 - gc);
+        if (own_y) {
+            // t_(tn_slice) = D^dagger x on the own rows, walking down the column
+            const int rup = row0 == 0 ? L - 1 : row0 - 1;
+            const int rdn = row0 + NY == L ? 0 : row0 + NY;
+            P4 up = lds_site(xc_r, rup * rc_ + oc, lim_slot - gc);
+            P4 cen = lds_site(xc_r, row0 * rc_ + oc, lim_slot - gc);
 #pragma unroll
             for (int j = 0; j < NY; ++j) {
                 const int rd = j + 1 < NY ? row0 + j + 1 : rdn;
-                const P4 dn = lds_site(xc_r, rd * rc_ + oc, S::SLOT / 16 - gc);
-                const P4 lf = lds_site(xl_r, (row0 + j) * rl + ol, S::SLOT / 16 - gl);
-                const P4 rt = lds_site(xr_r, (row0 + j) * rr + orr, S::SLOT / 16 - gr);
-                float p1, p2, p3;
-                if (own_y) {
-                    const float* q = phs + (row0 + j) * 16 + (tcol - 1);
-                    p1 = q[0];
-                    p2 = q[L * 16];
-                    p3 = q[2 * L * 16];
-                } else {
-                    p1 = phr[j][0];
-                    p2 = phr[j][1];
-                    p3 = phr[j][2];
-                }
+                const P4 dn = lds_site(xc_r, rd * rc_ + oc, lim_slot - gc);
+                const P4 lf = lds_site(xl_r, (row0 + j) * rl + ol, lim_slot - gl);
+                const P4 rt = lds_site(xr_r, (row0 + j) * rr + orr, lim_slot - gr);
+                const float* qp = phs + (row0 + j) * 16 + (tcol - 1);
+                const float p1 = qp[0], p2 = qp[L * 16], p3 = qp[2 * L * 16];
                 phk[j][0] = p1;
                 phk[j][1] = p2;
                 phk[j][2] = p3;
-                const P4 o = site_op_p(cf, cen, lf, rt, up, dn, xprev[j], ts, p1, p2, p3, (j & 1) ? -eta0 : eta0);
-                sts_p4(tn, L * TC, (row0 + j) * TC + tcol, o);
+                const P4 ov = site_op_p(cf, cen, lf, rt, up, dn, xprev[j], ts, p1, p2, p3, (j & 1) ? -eta0 : eta0);
+                sts_p4(tn, L * TC, (row0 + j) * TC + tcol, ov);
                 xprev[j] = cen;
                 up = cen;
                 cen = dn;
+            }
+        } else if (side) {
+            // t_ on a side column, rows seg + NSEG j; phi prefetched one step ahead
+#pragma unroll
+            for (int j = 0; j < NY; ++j) {
+                const int row = row0 + j * NSEG;
+                const int ru = row == 0 ? L - 1 : row - 1, rd = row == L - 1 ? 0 : row + 1;
+                const P4 cen = lds_site(xc_r, row * rc_ + oc, lim_slot - gc);
+                const P4 up = lds_site(xc_r, ru * rc_ + oc, lim_slot - gc);
+                const P4 dn = lds_site(xc_r, rd * rc_ + oc, lim_slot - gc);
+                const P4 lf = lds_site(xl_r, row * rl + ol, lim_slot - gl);
+                const P4 rt = lds_site(xr_r, row * rr + orr, lim_slot - gr);
+                const float eta = ((gx + row) & 1) ? -1.f : 1.f;
+                const P4 ov = site_op_p(cf, cen, lf, rt, up, dn, xprev[j], ts, phk[j][0], phk[j][1], phk[j][2], eta);
+                sts_p4(tn, L * TC, row * TC + tcol, ov);
+                xprev[j] = cen;
+            }
+            if (m + 1 < nsl) {
+                const int nx = tn_slice + 1 == Nt ? 0 : tn_slice + 1;
+#pragma unroll
+                for (int j = 0; j < NY; ++j) {
+                    const float* pp = phi + (int64_t)nx * LL + (row0 + j * NSEG) * L + gx;
+                    phk[j][0] = __ldg(pp);
+                    phk[j][1] = __ldg(pp + V);
+                    phk[j][2] = __ldg(pp + 2 * V);
+                }
             }
         }
         // y(t) = D t_ at t = tn_slice - 1 on the own rows
         if (own_y && m >= 1) {
             const int t = tn_slice == 0 ? Nt - 1 : tn_slice - 1;
-            const u64 ts = t == Nt - 1 ? pk2(-1.f, -1.f) : pk2(1.f, 1.f);   // b(t)
+            const u64 tsy = t == Nt - 1 ? pk2(-1.f, -1.f) : pk2(1.f, 1.f);   // b(t) of D
+            const int rup = row0 == 0 ? L - 1 : row0 - 1;
+            const int rdn = row0 + NY == L ? 0 : row0 + NY;
             P4 up = lds_p4(tc, L * TC, rup * TC + tcol, S::TS);
             P4 cen = lds_p4(tc, L * TC, row0 * TC + tcol, S::TS);
             Site<float>* dst = yk + (int64_t)t * LL + row0 * L + gx;
@@ -405,21 +460,41 @@ k_apply_A_strip(const __grid_constant__ StripMaps maps, Lat lat, CoefP cf, int n
                 const P4 lf = lds_p4(tc, L * TC, (row0 + j) * TC + tcol - 1, S::TS);
                 const P4 rt = lds_p4(tc, L * TC, (row0 + j) * TC + tcol + 1, S::TS);
                 const P4 nx = lds_p4(tn, L * TC, (row0 + j) * TC + tcol, S::TS);   // own t_(t + 1), written above
-                const P4 o = site_op_p(cf, cen, lf, rt, up, dn, nx, ts, phc[j][0], phc[j][1], phc[j][2],
-                                       (j & 1) ? -eta0 : eta0);
-                if (HMC_IN(t >= 0 && t < Nt && row0 + j < L && gx >= 0 && gx < L, kBndStripGlobal)) stg_p4(dst + j * L, o);
+                const P4 ov = site_op_p(cf, cen, lf, rt, up, dn, nx, tsy, phc[j][0], phc[j][1], phc[j][2],
+                                        (j & 1) ? -eta0 : eta0);
+                if (HMC_IN(t >= 0 && t < Nt && row0 + j < L && gx >= 0 && gx < L, kBndStripGlobal))
+                    stg_p4(dst + j * L, ov);
+                if constexpr (QN) {
+                    // acc = (sum |t_|^2, sum |y|^2): each site's two sums packed into one pair
+                    u64 st = mul2(cen.c[0], cen.c[0]), sy = mul2(ov.c[0], ov.c[0]);
 #pragma unroll
-                for (int qq = 0; qq < 4; ++qq) acc = fma2(cen.c[qq], cen.c[qq], acc);
+                    for (int qq = 1; qq < 4; ++qq) {
+                        st = fma2(cen.c[qq], cen.c[qq], st);
+                        sy = fma2(ov.c[qq], ov.c[qq], sy);
+                    }
+                    float t0, t1, y0, y1;
+                    upk2(st, t0, t1);
+                    upk2(sy, y0, y1);
+                    acc = add2(acc, pk2(t0 + t1, y0 + y1));
+                } else {
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) acc = fma2(cen.c[qq], cen.c[qq], acc);
+                }
                 up = cen;
                 cen = dn;
             }
         }
     }
+    float a0, a1;
+    upk2(acc, a0, a1);
+    const int64_t slot_out = (int64_t)k * (nch * nstrip) + c * nstrip + sx;
     if (part) {
-        float a0, a1;
-        upk2(acc, a0, a1);
-        const double tot = block_sum((double)a0 + (double)a1, red);
-        if (tid == 0) part[(int64_t)k * (nch * nstrip) + c * nstrip + sx] = tot;
+        const double tot = block_sum(QN ? (double)a0 : (double)a0 + (double)a1, red);
+        if (tid == 0) part[slot_out] = tot;
+    }
+    if (QN && part_q) {
+        const double tot = block_sum((double)a1, red);
+        if (tid == 0) part_q[slot_out] = tot;
     }
 }
 
@@ -497,12 +572,14 @@ static int strip_maps(hmc_ctx* ctx, const Lat& lat, int nrhs, const float* phi, 
 
 template <int L, int NY>
 static int go_strip(hmc_ctx* ctx, const Lat& lat, const float* phi, const Site<float>* x, Site<float>* y, int nrhs,
-                    double* part, const CgScalars* cgs, int* nblk_out) {
+                    double* part, double* part_q, const CgScalars* cgs, int* nblk_out) {
     using S = StripShape<L, NY>;
     static PerDevice attr;
     uint64_t bit;
     if (attr.pending(&bit)) {
-        HMC_CUDA(ctx, cudaFuncSetAttribute(k_apply_A_strip<L, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        HMC_CUDA(ctx, cudaFuncSetAttribute(k_apply_A_strip<L, NY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)S::smem));
+        HMC_CUDA(ctx, cudaFuncSetAttribute(k_apply_A_strip<L, NY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)S::smem));
         attr.mark(bit);
     }
@@ -514,13 +591,16 @@ static int go_strip(hmc_ctx* ctx, const Lat& lat, const float* phi, const Site<f
     int C, nch;
     strip_chunks(lat.Nt, pipes, ctx->num_sms * bps, &C, &nch);
     const int64_t nblk = (int64_t)nch * (L / 16);
-    if (part && nblk * nrhs > ctx->part_cap) return fail(ctx, HMC_ERR_ARG, "apply_A: reduction buffer too small");
+    const int64_t cap = part_q ? ctx->part_cap / 2 : ctx->part_cap;   // part_q lives in the second half
+    if ((part || part_q) && nblk * nrhs > cap) return fail(ctx, HMC_ERR_ARG, "apply_A: reduction buffer too small");
     StripMaps maps;
     int rc;
     if ((rc = strip_maps(ctx, lat, nrhs, phi, x, &maps))) return rc;
     const int wl = ctx->p.wait_spin_limit > 0 ? ctx->p.wait_spin_limit : (1 << 20);
-    k_apply_A_strip<L, NY><<<(unsigned)(nch * pipes), S::NTHR, S::smem, ctx->stream>>>(
-        maps, lat, make_coef_p(ctx->p), nch, C, phi, x, y, part, cgs, ctx->d_flags, wl, ctx->p.test_wait_timeout);
+    auto kern = part_q ? k_apply_A_strip<L, NY, true> : k_apply_A_strip<L, NY, false>;
+    kern<<<(unsigned)(nch * pipes), S::NTHR, S::smem, ctx->stream>>>(maps, lat, make_coef_p(ctx->p), nch, C, phi, x, y,
+                                                                     part, part_q, cgs, ctx->d_flags, wl,
+                                                                     ctx->p.test_wait_timeout);
     HMC_LAUNCH(ctx, "k_apply_A_strip");
     if (nblk_out) *nblk_out = (int)nblk;
     return HMC_OK;
@@ -529,15 +609,15 @@ static int go_strip(hmc_ctx* ctx, const Lat& lat, const float* phi, const Site<f
 unsigned int bounds_take_strip() { return bounds_take_tu(); }
 
 int launch_apply_A_strip(hmc_ctx* ctx, const Lat& lat, const float* phi, const float2* x, float2* y, int nrhs,
-                         double* part, int* nblk_out, const CgScalars* cgs) {
+                         double* part, int* nblk_out, const CgScalars* cgs, double* part_q) {
     const Site<float>* xs = reinterpret_cast<const Site<float>*>(x);
     Site<float>* ys = reinterpret_cast<Site<float>*>(y);
     switch (lat.L) {
-        case 16: return go_strip<16, 1>(ctx, lat, phi, xs, ys, nrhs, part, cgs, nblk_out);
-        case 32: return go_strip<32, 2>(ctx, lat, phi, xs, ys, nrhs, part, cgs, nblk_out);
-        case 48: return go_strip<48, 3>(ctx, lat, phi, xs, ys, nrhs, part, cgs, nblk_out);
-        case 64: return go_strip<64, 4>(ctx, lat, phi, xs, ys, nrhs, part, cgs, nblk_out);
-        case 80: return go_strip<80, STRIP_NY80>(ctx, lat, phi, xs, ys, nrhs, part, cgs, nblk_out);
+        case 16: return go_strip<16, 1>(ctx, lat, phi, xs, ys, nrhs, part, part_q, cgs, nblk_out);
+        case 32: return go_strip<32, 2>(ctx, lat, phi, xs, ys, nrhs, part, part_q, cgs, nblk_out);
+        case 48: return go_strip<48, 3>(ctx, lat, phi, xs, ys, nrhs, part, part_q, cgs, nblk_out);
+        case 64: return go_strip<64, 4>(ctx, lat, phi, xs, ys, nrhs, part, part_q, cgs, nblk_out);
+        case 80: return go_strip<80, STRIP_NY80>(ctx, lat, phi, xs, ys, nrhs, part, part_q, cgs, nblk_out);
         default: return fail(ctx, HMC_ERR_STATE, "apply_A: no strip kernel for this L");
     }
 }

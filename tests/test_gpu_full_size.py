@@ -1,8 +1,8 @@
 """The largest configuration, 80 x 80 x 160 (dtau = 0.1, Yukawa coupling 1), against the FP64
 oracle: the force at one field and a two-step trajectory, one pseudofermion right-hand side each,
-through the benchmark's kernels (complex64 16 x 16-tile operator, fused (x, y) and in-place tau
-preconditioner passes, FP64 reliable updates; the trajectory with the degree-4 chronological
-start). The oracle's values are stored in tests/golden/full_size_80x80x160.json, written by
+through the benchmark's kernels (complex64 strip operator, FP64 reliable updates; plain CG with
+the fused x, r, p update as the benchmark runs it, and PCG with the fused (x, y) and in-place tau
+preconditioner passes; the trajectory with the degree-4 chronological start). The oracle's values are stored in tests/golden/full_size_80x80x160.json, written by
 tests/golden/make_full_size.py from the oracle alone (its preconditioned CG takes minutes per
 solve at this size); the inputs are regenerated here from the same seeds.
 
@@ -40,12 +40,13 @@ def context(guess):
     return Context(G.L, G.NT, solver="mixed", nrhs_max=1, cg_tol=1e-12, initial_guess=guess, **G.COUPLINGS)
 
 
-def test_full_size_force_matches_oracle():
+@pytest.mark.parametrize("precond", [True, False])
+def test_full_size_force_matches_oracle(precond):
     g = golden()
     phi, sig, pf, chi, z, idx = G.inputs()
     assert list(map(int, idx)) == g["indices"]
     ctx = context(0)
-    F, spf, sb, st = ctx.force(dev(phi), dev(pf), include_boson=True, precond=True)
+    F, spf, sb, st = ctx.force(dev(phi), dev(pf), include_boson=True, precond=precond)
     assert st["converged"] and st["true_rel_resid"] <= 1e-12
     got = F.cpu().numpy().ravel()[idx]
     want = np.asarray(g["force"]["F_samples"])
@@ -54,13 +55,14 @@ def test_full_size_force_matches_oracle():
     ctx.close()
 
 
-def test_full_size_trajectory_matches_oracle():
+@pytest.mark.parametrize("precond", [True, False])
+def test_full_size_trajectory_matches_oracle(precond):
     g = golden()
     t = g["trajectory"]
     phi0, sig, pf, chi, z, idx = G.inputs()
     ctx = context(4)
     phi = dev(phi0)
-    out = ctx.trajectory([phi], [dev(sig)], G.EPS, G.NLEAP, nrhs=1, precond=True, chi=[dev(chi)], z=[dev(z)],
+    out = ctx.trajectory([phi], [dev(sig)], G.EPS, G.NLEAP, nrhs=1, precond=precond, chi=[dev(chi)], z=[dev(z)],
                          u=[G.U])
     assert out["status"] == 0 and out["max_true_resid"][0] <= 1e-12
     assert abs(out["dH"][0] - t["dH"]) < 1e-8, (out["dH"][0], t["dH"])

@@ -94,10 +94,10 @@ def test_apply_A_fused(L, Nt, prec):
 
 
 @pytest.mark.parametrize("L,Nt", [(16, 9), (32, 6), (48, 5)])
-def test_apply_A_fp32_16x16_tiles(L, Nt):
-    # L a multiple of 16: the plain FP32 operator runs on 16 x 16 tiles with asynchronous
-    # staging; one tile wrapping onto itself (L = 16), several tiles, time chunks of 4 slices
-    # with a ragged last chunk (Nt = 9: 4 + 4 + 1, Nt = 6: 4 + 2, Nt = 5: 4 + 1)
+def test_apply_A_fp32_strips(L, Nt):
+    # L a multiple of 16: the plain FP32 operator runs on full-height strips of 16 columns with
+    # TMA staging; one strip wrapping onto itself (L = 16), several strips, time chunks with a
+    # ragged last chunk
     ctx = ctx_for(L, Nt, nrhs=3)
     P = oparams(L, Nt)
     phi = dev(I.gaussian_field(30 + L, L, Nt), torch.float32)
@@ -141,8 +141,11 @@ def test_preconditioner_fp32_xy_pass(L, Nt):
 
 @pytest.mark.parametrize("mode", ["fp64", "mixed"])
 @pytest.mark.parametrize("precond", [False, True])
-@pytest.mark.parametrize("L,Nt", [(6, 7), (12, 24), (20, 12)])
+@pytest.mark.parametrize("L,Nt", [(6, 7), (12, 24), (20, 12), (16, 9), (32, 6)])
 def test_cg_solve(mode, precond, L, Nt):
+    # L = 16, 32 in mixed mode without preconditioner: the complex64 strip operator with the fused
+    # x, r, p update (beta ahead of the residual); with it, the strip operator after the p update
+    # and the (x, y) preconditioner passes
     tol = 1e-10
     ctx = ctx_for(L, Nt, mode, tol=tol)
     P = oparams(L, Nt)
@@ -538,12 +541,14 @@ def test_green_estimator_free_limit():
     assert rel(I.to_paper_fermion(est.cpu().numpy()), ref) < 1e-9
 
 
-def test_trajectory_bench_kernel_set_16x16x16():
-    # The benchmark's kernel set on a lattice small enough for the oracle: L = 16 (16 x 16-tile
-    # complex64 operator, fused (x, y) preconditioner passes, in-place tau pass at Nt = 16), 8
-    # right-hand sides, degree-4 chronological start, mixed-precision PCG, Yukawa coupling 1, an
-    # ordered field (uniform 2.8 along component 3 plus free-boson fluctuations) and the
-    # free-boson sigma-hat. Oracle: PCG from a zero start to 1e-13 on every solve.
+@pytest.mark.parametrize("precond", [False, True])
+def test_trajectory_bench_kernel_set_16x16x16(precond):
+    # The benchmark's kernel set on a lattice small enough for the oracle: L = 16 (complex64 strip
+    # operator; plain CG with the fused x, r, p update as the benchmark runs it, or PCG with the
+    # fused (x, y) preconditioner passes and the in-place tau pass at Nt = 16), 8 right-hand sides,
+    # degree-4 chronological start, mixed precision, Yukawa coupling 1, an ordered field (uniform
+    # 2.8 along component 3 plus free-boson fluctuations) and the free-boson sigma-hat. Oracle:
+    # PCG from a zero start to 1e-13 on every solve.
     L, Nt, K, eps, n_leap = 16, 16, 8, 0.02, 4
     kt = 2.0 / (9 * 0.01)
     ctx = ctx_for(L, Nt, "mixed", nrhs=K, tol=1e-12, guess=4)
@@ -554,7 +559,8 @@ def test_trajectory_bench_kernel_set_16x16x16():
     z = I.gaussian_field(42, L, Nt)
     u = 0.45
     phi = dev(phi0)
-    out = ctx.trajectory([phi], [dev(sig)], eps, n_leap, nrhs=K, precond=True, chi=[dev(chi)], z=[dev(z)], u=[u])
+    out = ctx.trajectory([phi], [dev(sig)], eps, n_leap, nrhs=K, precond=precond, chi=[dev(chi)], z=[dev(z)],
+                         u=[u])
     ref = ohmc.trajectory(P, I.to_paper_boson(phi0), I.to_paper_boson(sig),
                           [I.to_paper_fermion(chi[k]) for k in range(K)], I.to_paper_boson(z), u, eps, n_leap,
                           method="pcg", tol=1e-13)
