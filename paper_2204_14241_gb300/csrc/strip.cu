@@ -16,10 +16,10 @@
 // outputs over one block per SM, which ends the partial last wave, put neighbouring strips at
 // different slices and ran slower.)
 //
-// Per step t (x(t+1) landed in its TMA slot): barrier; t_(t+1) = D^dagger x on the thread's rows
-// into shared memory; y(t) = D t_ from t_(t) and the thread's own t_(t+1), stored with one
-// 32-byte store per site. The site arithmetic runs on packed (re, im) pairs with Blackwell's
-// two-wide FP32 instructions (add/mul/fma .f32x2).
+// Per step t (x(t+1) landed in its TMA slot): barrier; then row by row, t_(t+1) = D^dagger x on
+// the row into shared memory and y(t) = D t_ from t_(t) and the row's t_(t+1) still in registers,
+// stored with one 32-byte store per site. The site arithmetic runs on packed (re, im) pairs with
+// Blackwell's two-wide FP32 instructions (add/mul/fma .f32x2).
 #include <cuda.h>
 
 #include <cstring>
@@ -127,11 +127,10 @@ template <int L, int NY> struct StripShape {
     static constexpr int NRING = 2 * NSEG;            // threads for the two side columns of t_
     static constexpr int NTHR = (NMAIN + NRING + 31) / 32 * 32;
     static constexpr int TC = 18;                     // columns of t_ computed
-    // one staging slot (bytes): x of the 16 own columns [row][16 sites][32 B], of the two columns
-    // left of the strip [row][2][32 B] and of the two right of it [row][2][32 B], each site's two
-    // 16-byte halves swapped where bit 2 of the site index is set (the TMA 32-byte swizzle, which
-    // makes a quarter warp's reads of one half of eight consecutive sites hit eight distinct bank
-    // groups); phi of the own columns [component][row][16]. Regions are multiples of 1024 bytes.
+    // one staging slot (bytes): x of the 16 own columns [row][16 sites][32 B] (TMA 128-byte
+    // swizzle), of the two columns left of the strip [row][2][32 B] and of the two right of it
+    // [row][2][32 B] (64-byte swizzle); phi of the own columns [component][row][16]. Regions are
+    // multiples of 1024 bytes.
     static constexpr int XMAIN = L * 16 * 32;
     static constexpr int XHALO = L * 2 * 32;
     static constexpr int PHI = 3 * L * 16 * 4;
@@ -143,12 +142,16 @@ template <int L, int NY> struct StripShape {
     static_assert(XMAIN % 1024 == 0 && XHALO % 1024 == 0 && PHI % 1024 == 0, "swizzled TMA regions 1024-byte aligned");
 };
 
-// Site `site` of a swizzled site-major region (16-byte units from `region`): its halves sit at
-// 2 site + s and 2 site + 1 - s, s = bit 2 of the site index.
-__device__ __forceinline__ P4 lds_site(const ulonglong2* region, int site, int lim) {
+// Site `site` of a swizzled site-major region (16-byte units from `region`): unit u = 2 site + h
+// of half h sits at u ^ ((u >> 3) & mask), the TMA swizzle of the region's box: mask 7 for the
+// 128-byte swizzle of the 16 own columns (box rows of 4 sites), 3 for the 64-byte swizzle of the
+// two side columns (box rows of 2 sites). A quarter warp's reads of one half of eight consecutive
+// sites of a row, or of one side column on four consecutive rows of each side, hit eight distinct
+// bank groups.
+__device__ __forceinline__ P4 lds_site(const ulonglong2* region, int site, int lim, int mask) {
     if (!HMC_IN(site >= 0 && 2 * site + 1 < lim, kBndStripShared)) return P4{};
-    const int sw = (site >> 2) & 1;
-    const ulonglong2 a = region[2 * site + sw], b = region[2 * site + 1 - sw];
+    const int u = (2 * site) ^ ((site >> 2) & mask);
+    const ulonglong2 a = region[u], b = region[u ^ 1];
     P4 r;
     r.c[0] = a.x; r.c[1] = a.y; r.c[2] = b.x; r.c[3] = b.y;
     return r;
@@ -215,9 +218,12 @@ __device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int c0, 
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Tensor maps of one launch: x viewed as [slice = k * Nt + t][y][x][8 floats] (box: whole sites of
-// 16 or 2 columns x all rows, 32-byte swizzle), phi as [component][t][y][x] (box: 16 columns x all
-// rows x 3 components).
+// Tensor maps of one launch: x viewed as [slice = k * Nt + t][y][x / 4][32 floats] for the own
+// columns (box: 4 units of 4 sites x all rows, 128-byte swizzle) and as [slice][y][x / 2][16
+// floats] for the side columns (box: 1 unit of 2 sites x all rows, 64-byte swizzle), phi as
+// [component][t][y][x] (box: 16 columns x all rows x 3 components). Box rows of 128 and 64 bytes
+// take a quarter and a half of the copy requests of whole-site (32-byte) rows, which the copy
+// engine, not DRAM, was limited by.
 struct StripMaps {
     CUtensorMap xmain, xhalo, phi;
 };
@@ -230,9 +236,10 @@ struct StripMaps {
 // m & 1 on that slot's mbarrier, issued by thread 0 one step ahead. t_ lives in two slices.
 // Step m: wait for slot m & 1; barrier (also the end of step m - 1); thread 0 issues slice m + 1
 // into the other slot (read in step m - 1; phi of the rows a thread needs for y is kept in its
-// registers from step m - 1); t_(ta + m) = D^dagger x on the thread's rows, written to the t_
-// slice that y(ta + m - 2) read one step earlier; y(ta + m - 1) = D t_ from t_(ta + m - 1) and
-// the thread's own t_(ta + m). A thread reads its own t_(ta + m) only, so one barrier per step.
+// registers from step m - 1); on each of its rows a thread writes t_(ta + m) = D^dagger x to the
+// t_ slice that y(ta + m - 2) read one step earlier and computes y(ta + m - 1) = D t_ from
+// t_(ta + m - 1) and the row's t_(ta + m) in registers. Nothing of t_(ta + m) is read before the
+// next barrier, so one barrier per step.
 // Waits are bounded (wait_limit polls): on a timeout the block drains the copy in flight, sets
 // err[0] and returns. test_timeout makes the first wait target a barrier that is never armed.
 // Slices prefetched into L2 ahead of the one loaded into the free slot: the two shared-memory
@@ -285,6 +292,7 @@ k_apply_A_strip(const __grid_constant__ StripMaps maps, Lat lat, CoefP cf, int n
     xcol_of(tcol - 1, gc, oc, rc_);
     xcol_of(tcol - 2, gl, ol, rl);
     xcol_of(tcol, gr, orr, rr);
+    const int mc = gc == 0 ? 7 : 3, ml = gl == 0 ? 7 : 3, mr = gr == 0 ? 7 : 3;   // swizzle of each region
     constexpr int lim_slot = S::SLOT / 16;
 
     const int P = gridDim.x / nch;
@@ -321,18 +329,18 @@ k_apply_A_strip(const __grid_constant__ StripMaps maps, Lat lat, CoefP cf, int n
         int xl, xr;
         side_cols(xl, xr);
         mbar_expect_tx(bar, kSlotBytes);
-        tma_load_4d(dst, &maps.xmain, 0, x0, 0, sl, bar);
-        tma_load_4d(dst + S::OFF_XL, &maps.xhalo, 0, xl, 0, sl, bar);
-        tma_load_4d(dst + S::OFF_XR, &maps.xhalo, 0, xr, 0, sl, bar);
+        tma_load_4d(dst, &maps.xmain, 0, x0 / 4, 0, sl, bar);
+        tma_load_4d(dst + S::OFF_XL, &maps.xhalo, 0, xl / 2, 0, sl, bar);
+        tma_load_4d(dst + S::OFF_XR, &maps.xhalo, 0, xr / 2, 0, sl, bar);
         tma_load_4d(dst + S::OFF_PHI, &maps.phi, x0, 0, t, 0, bar);
     };
     auto prefetch = [&](int t) {   // thread 0 only: the boxes of slice t into L2
         const int sl = k * Nt + t;
         int xl, xr;
         side_cols(xl, xr);
-        tma_prefetch_4d(&maps.xmain, 0, x0, 0, sl);
-        tma_prefetch_4d(&maps.xhalo, 0, xl, 0, sl);
-        tma_prefetch_4d(&maps.xhalo, 0, xr, 0, sl);
+        tma_prefetch_4d(&maps.xmain, 0, x0 / 4, 0, sl);
+        tma_prefetch_4d(&maps.xhalo, 0, xl / 2, 0, sl);
+        tma_prefetch_4d(&maps.xhalo, 0, xr / 2, 0, sl);
         tma_prefetch_4d(&maps.phi, x0, 0, t, 0);
     };
     auto slice_of = [&](int m) { return ta + m >= Nt ? ta + m - Nt : ta + m; };
@@ -388,34 +396,71 @@ k_apply_A_strip(const __grid_constant__ StripMaps maps, Lat lat, CoefP cf, int n
         const ulonglong2* tc = tr + (slot ^ 1) * S::TS;    // t_(tn_slice - 1)
         const u64 ts = tn_slice == 0 ? pk2(-1.f, -1.f) : pk2(1.f, 1.f);   // b(t - 1) of D^dagger
         const ulonglong2 *xc_r = xb + gc, *xl_r = xb + gl, *xr_r = xb + gr;
-        // y(t) needs phi(t) of its rows, kept from the previous t_ step
-        float phc[NY][3];
-#pragma unroll
-        for (int j = 0; j < NY; ++j)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) phc[j][a] = phk[j][a];
         if (own_y) {
-            // t_(tn_slice) = D^dagger x on the own rows, walking down the column
+            // Row by row down the column: t_(tn_slice) = D^dagger x on row j (into shared memory for
+            // the neighbours), then y(t) = D t_ on row j at t = tn_slice - 1 from t_(t) of the
+            // previous step and this row's t_(t + 1), still in registers; phi(t) of the row is kept
+            // from the previous step.
             const int rup = row0 == 0 ? L - 1 : row0 - 1;
             const int rdn = row0 + NY == L ? 0 : row0 + NY;
-            P4 up = lds_site(xc_r, rup * rc_ + oc, lim_slot - gc);
-            P4 cen = lds_site(xc_r, row0 * rc_ + oc, lim_slot - gc);
+            const bool do_y = m >= 1;
+            const int t = tn_slice == 0 ? Nt - 1 : tn_slice - 1;
+            const u64 tsy = t == Nt - 1 ? pk2(-1.f, -1.f) : pk2(1.f, 1.f);   // b(t) of D
+            Site<float>* dst = yk + (int64_t)t * LL + row0 * L + gx;
+            P4 up = lds_site(xc_r, rup * rc_ + oc, lim_slot - gc, mc);
+            P4 cen = lds_site(xc_r, row0 * rc_ + oc, lim_slot - gc, mc);
+            P4 tup, tcen;
+            if (do_y) {
+                tup = lds_p4(tc, L * TC, rup * TC + tcol, S::TS);
+                tcen = lds_p4(tc, L * TC, row0 * TC + tcol, S::TS);
+            }
 #pragma unroll
             for (int j = 0; j < NY; ++j) {
                 const int rd = j + 1 < NY ? row0 + j + 1 : rdn;
-                const P4 dn = lds_site(xc_r, rd * rc_ + oc, lim_slot - gc);
-                const P4 lf = lds_site(xl_r, (row0 + j) * rl + ol, lim_slot - gl);
-                const P4 rt = lds_site(xr_r, (row0 + j) * rr + orr, lim_slot - gr);
-                const float* qp = phs + (row0 + j) * 16 + (tcol - 1);
-                const float p1 = qp[0], p2 = qp[L * 16], p3 = qp[2 * L * 16];
-                phk[j][0] = p1;
-                phk[j][1] = p2;
-                phk[j][2] = p3;
-                const P4 ov = site_op_p(cf, cen, lf, rt, up, dn, xprev[j], ts, p1, p2, p3, (j & 1) ? -eta0 : eta0);
-                sts_p4(tn, L * TC, (row0 + j) * TC + tcol, ov);
-                xprev[j] = cen;
-                up = cen;
-                cen = dn;
+                const float eta = (j & 1) ? -eta0 : eta0;
+                P4 tnew;
+                {
+                    const P4 dn = lds_site(xc_r, rd * rc_ + oc, lim_slot - gc, mc);
+                    const P4 lf = lds_site(xl_r, (row0 + j) * rl + ol, lim_slot - gl, ml);
+                    const P4 rt = lds_site(xr_r, (row0 + j) * rr + orr, lim_slot - gr, mr);
+                    const float* qp = phs + (row0 + j) * 16 + (tcol - 1);
+                    const float p1 = qp[0], p2 = qp[L * 16], p3 = qp[2 * L * 16];
+                    tnew = site_op_p(cf, cen, lf, rt, up, dn, xprev[j], ts, p1, p2, p3, eta);
+                    sts_p4(tn, L * TC, (row0 + j) * TC + tcol, tnew);
+                    xprev[j] = cen;
+                    up = cen;
+                    cen = dn;
+                    if (do_y) {
+                        const P4 tdn = lds_p4(tc, L * TC, rd * TC + tcol, S::TS);
+                        const P4 tlf = lds_p4(tc, L * TC, (row0 + j) * TC + tcol - 1, S::TS);
+                        const P4 trt = lds_p4(tc, L * TC, (row0 + j) * TC + tcol + 1, S::TS);
+                        const P4 ov = site_op_p(cf, tcen, tlf, trt, tup, tdn, tnew, tsy, phk[j][0], phk[j][1],
+                                                phk[j][2], eta);
+                        if (HMC_IN(t >= 0 && t < Nt && row0 + j < L && gx >= 0 && gx < L, kBndStripGlobal))
+                            stg_p4(dst + j * L, ov);
+                        if constexpr (QN) {
+                            // acc = (sum |t_|^2, sum |y|^2): each site's two sums packed into one pair
+                            u64 st = mul2(tcen.c[0], tcen.c[0]), sy = mul2(ov.c[0], ov.c[0]);
+#pragma unroll
+                            for (int qq = 1; qq < 4; ++qq) {
+                                st = fma2(tcen.c[qq], tcen.c[qq], st);
+                                sy = fma2(ov.c[qq], ov.c[qq], sy);
+                            }
+                            float t0, t1, y0, y1;
+                            upk2(st, t0, t1);
+                            upk2(sy, y0, y1);
+                            acc = add2(acc, pk2(t0 + t1, y0 + y1));
+                        } else {
+#pragma unroll
+                            for (int qq = 0; qq < 4; ++qq) acc = fma2(tcen.c[qq], tcen.c[qq], acc);
+                        }
+                        tup = tcen;
+                        tcen = tdn;
+                    }
+                    phk[j][0] = p1;
+                    phk[j][1] = p2;
+                    phk[j][2] = p3;
+                }
             }
         } else if (side) {
             // t_ on a side column, rows seg + NSEG j; phi prefetched one step ahead
@@ -423,11 +468,11 @@ k_apply_A_strip(const __grid_constant__ StripMaps maps, Lat lat, CoefP cf, int n
             for (int j = 0; j < NY; ++j) {
                 const int row = row0 + j * NSEG;
                 const int ru = row == 0 ? L - 1 : row - 1, rd = row == L - 1 ? 0 : row + 1;
-                const P4 cen = lds_site(xc_r, row * rc_ + oc, lim_slot - gc);
-                const P4 up = lds_site(xc_r, ru * rc_ + oc, lim_slot - gc);
-                const P4 dn = lds_site(xc_r, rd * rc_ + oc, lim_slot - gc);
-                const P4 lf = lds_site(xl_r, row * rl + ol, lim_slot - gl);
-                const P4 rt = lds_site(xr_r, row * rr + orr, lim_slot - gr);
+                const P4 cen = lds_site(xc_r, row * rc_ + oc, lim_slot - gc, mc);
+                const P4 up = lds_site(xc_r, ru * rc_ + oc, lim_slot - gc, mc);
+                const P4 dn = lds_site(xc_r, rd * rc_ + oc, lim_slot - gc, mc);
+                const P4 lf = lds_site(xl_r, row * rl + ol, lim_slot - gl, ml);
+                const P4 rt = lds_site(xr_r, row * rr + orr, lim_slot - gr, mr);
                 const float eta = ((gx + row) & 1) ? -1.f : 1.f;
                 const P4 ov = site_op_p(cf, cen, lf, rt, up, dn, xprev[j], ts, phk[j][0], phk[j][1], phk[j][2], eta);
                 sts_p4(tn, L * TC, row * TC + tcol, ov);
@@ -442,46 +487,6 @@ k_apply_A_strip(const __grid_constant__ StripMaps maps, Lat lat, CoefP cf, int n
                     phk[j][1] = __ldg(pp + V);
                     phk[j][2] = __ldg(pp + 2 * V);
                 }
-            }
-        }
-        // y(t) = D t_ at t = tn_slice - 1 on the own rows
-        if (own_y && m >= 1) {
-            const int t = tn_slice == 0 ? Nt - 1 : tn_slice - 1;
-            const u64 tsy = t == Nt - 1 ? pk2(-1.f, -1.f) : pk2(1.f, 1.f);   // b(t) of D
-            const int rup = row0 == 0 ? L - 1 : row0 - 1;
-            const int rdn = row0 + NY == L ? 0 : row0 + NY;
-            P4 up = lds_p4(tc, L * TC, rup * TC + tcol, S::TS);
-            P4 cen = lds_p4(tc, L * TC, row0 * TC + tcol, S::TS);
-            Site<float>* dst = yk + (int64_t)t * LL + row0 * L + gx;
-#pragma unroll
-            for (int j = 0; j < NY; ++j) {
-                const int rd = j + 1 < NY ? row0 + j + 1 : rdn;
-                const P4 dn = lds_p4(tc, L * TC, rd * TC + tcol, S::TS);
-                const P4 lf = lds_p4(tc, L * TC, (row0 + j) * TC + tcol - 1, S::TS);
-                const P4 rt = lds_p4(tc, L * TC, (row0 + j) * TC + tcol + 1, S::TS);
-                const P4 nx = lds_p4(tn, L * TC, (row0 + j) * TC + tcol, S::TS);   // own t_(t + 1), written above
-                const P4 ov = site_op_p(cf, cen, lf, rt, up, dn, nx, tsy, phc[j][0], phc[j][1], phc[j][2],
-                                        (j & 1) ? -eta0 : eta0);
-                if (HMC_IN(t >= 0 && t < Nt && row0 + j < L && gx >= 0 && gx < L, kBndStripGlobal))
-                    stg_p4(dst + j * L, ov);
-                if constexpr (QN) {
-                    // acc = (sum |t_|^2, sum |y|^2): each site's two sums packed into one pair
-                    u64 st = mul2(cen.c[0], cen.c[0]), sy = mul2(ov.c[0], ov.c[0]);
-#pragma unroll
-                    for (int qq = 1; qq < 4; ++qq) {
-                        st = fma2(cen.c[qq], cen.c[qq], st);
-                        sy = fma2(ov.c[qq], ov.c[qq], sy);
-                    }
-                    float t0, t1, y0, y1;
-                    upk2(st, t0, t1);
-                    upk2(sy, y0, y1);
-                    acc = add2(acc, pk2(t0 + t1, y0 + y1));
-                } else {
-#pragma unroll
-                    for (int qq = 0; qq < 4; ++qq) acc = fma2(cen.c[qq], cen.c[qq], acc);
-                }
-                up = cen;
-                cen = dn;
             }
         }
     }
@@ -559,14 +564,16 @@ static int strip_maps(hmc_ctx* ctx, const Lat& lat, int nrhs, const float* phi, 
     EncodeTiledFn fn = encode_fn(ctx, &rc);
     if (!fn) return rc;
     const cuuint64_t L = (cuuint64_t)lat.L;
-    const cuuint64_t xdim[4] = {8, L, L, (cuuint64_t)lat.Nt * (cuuint64_t)nrhs};
-    const cuuint64_t xstr[3] = {32, 32 * L, 32 * L * L};
-    const cuuint32_t bmain[4] = {8, 16, (cuuint32_t)L, 1}, bhalo[4] = {8, 2, (cuuint32_t)L, 1};
+    const cuuint64_t hdim[4] = {16, L / 2, L, (cuuint64_t)lat.Nt * (cuuint64_t)nrhs};   // 2 sites per unit
+    const cuuint64_t hstr[3] = {64, 32 * L, 32 * L * L};
+    const cuuint64_t wdim[4] = {32, L / 4, L, (cuuint64_t)lat.Nt * (cuuint64_t)nrhs};   // 4 sites per unit
+    const cuuint64_t wstr[3] = {128, 32 * L, 32 * L * L};
+    const cuuint32_t bmain[4] = {32, 4, (cuuint32_t)L, 1}, bhalo[4] = {16, 1, (cuuint32_t)L, 1};
     const cuuint64_t pdim[4] = {L, L, (cuuint64_t)lat.Nt, 3};
     const cuuint64_t pstr[3] = {4 * L, 4 * L * L, 4 * (cuuint64_t)lat.V};
     const cuuint32_t bphi[4] = {16, (cuuint32_t)L, 1, 3};
-    if ((rc = encode(ctx, fn, &m->xmain, x, xdim, xstr, bmain, CU_TENSOR_MAP_SWIZZLE_32B))) return rc;
-    if ((rc = encode(ctx, fn, &m->xhalo, x, xdim, xstr, bhalo, CU_TENSOR_MAP_SWIZZLE_32B))) return rc;
+    if ((rc = encode(ctx, fn, &m->xmain, x, wdim, wstr, bmain, CU_TENSOR_MAP_SWIZZLE_128B))) return rc;
+    if ((rc = encode(ctx, fn, &m->xhalo, x, hdim, hstr, bhalo, CU_TENSOR_MAP_SWIZZLE_64B))) return rc;
     return encode(ctx, fn, &m->phi, phi, pdim, pstr, bphi, CU_TENSOR_MAP_SWIZZLE_NONE);
 }
 
