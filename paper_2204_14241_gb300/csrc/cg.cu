@@ -71,21 +71,29 @@ __global__ void __launch_bounds__(256) k_cg_xr(V16<R>* __restrict__ x, V16<R>* _
     if (threadIdx.x == 0) part[(int64_t)k * gridDim.x + blockIdx.x] = s;
 }
 
-// Fused complex64 update of plain CG: x += alpha p; r -= alpha q; p = r + beta p (beta known
-// before r: see k_cg_ab); partial ||r||^2. One pass over x, r, p, q.
+// Fused complex64 update of plain CG: r -= alpha q; p = r + beta p (beta known before r: see
+// k_cg_ab); partial ||r||^2; and x += alpha p every other iteration. An iteration with
+// defer set (and beta > 0) leaves x alone and k_cg_beta records carry = alpha / beta; the next one
+// adds both terms, recovering the previous direction from the vectors it reads anyway:
+// p_prev = (p - r) / beta_prev, so x += alpha p + carry (p - r). One pass over r, p, q, and over x
+// on the iterations that update it.
+__device__ __forceinline__ float4 v_sub(float4 a, float4 b) {
+    return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
 __global__ void __launch_bounds__(256) k_cg_xrp(float4* __restrict__ x, float4* __restrict__ r, float4* __restrict__ p,
                                                 const float4* __restrict__ q, int64_t n16, double* __restrict__ part,
-                                                const CgScalars* __restrict__ cgs) {
+                                                const CgScalars* __restrict__ cgs, int defer) {
     __shared__ double red[8];
     const int k = blockIdx.y;
     if (!cgs[k].active) return;
-    const float alpha = (float)cgs[k].alpha, beta = (float)cgs[k].beta;
+    const float alpha = (float)cgs[k].alpha, beta = (float)cgs[k].beta, carry = (float)cgs[k].carry;
+    const bool skip_x = defer && cgs[k].beta > 0.0;
     const int64_t off = k * n16;
     double s = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x) {
-        const float4 pv = p[off + i];
-        x[off + i] = v_axpy(alpha, pv, x[off + i]);
-        const float4 rn = v_axpy(-alpha, q[off + i], r[off + i]);
+        const float4 pv = p[off + i], rv = r[off + i];
+        if (!skip_x) x[off + i] = v_axpy(carry, v_sub(pv, rv), v_axpy(alpha, pv, x[off + i]));
+        const float4 rn = v_axpy(-alpha, q[off + i], rv);
         r[off + i] = rn;
         p[off + i] = v_axpy(beta, pv, rn);
         s += v_dot(rn, rn);
@@ -137,10 +145,11 @@ __global__ void k_cg_ab(CgScalars* cgs, const double* __restrict__ part_pap, con
 }
 
 // r2 = ||r||^2, rz_new = <r, z> (= r2 without preconditioner), beta (unless set_beta is 0: the
-// fused plain update took it from k_cg_ab), convergence flags
+// fused plain update took it from k_cg_ab, and defer says whether that update left x for the next
+// iteration, see k_cg_xrp), convergence flags
 __global__ void k_cg_beta(CgScalars* cgs, const double* __restrict__ part_r2,
                           const double* __restrict__ part_rz, int nblk, int nblk_rz, double tol2, double delta2,
-                          int mixed, int set_beta) {
+                          int mixed, int set_beta, int defer) {
     __shared__ double red[8];
     const int k = blockIdx.x;
     if (!cgs[k].active) return;
@@ -149,6 +158,7 @@ __global__ void k_cg_beta(CgScalars* cgs, const double* __restrict__ part_r2,
     if (threadIdx.x == 0) {
         CgScalars& c = cgs[k];
         if (set_beta) c.beta = c.rr > 0.0 ? rz / c.rr : 0.0;
+        else c.carry = (defer && c.beta > 0.0) ? c.alpha / c.beta : 0.0;
         c.rr = rz;
         c.r2 = r2;
         c.iters += 1;
@@ -402,7 +412,7 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
                 int nbr = 0, nbz = 0;
                 if ((rc = launch_pcg_xy_forward(ctx, lat, xv, rv, pv, qv, zv, nrhs, cgs, part, part2, &nbr, &nbz)))
                     return rc;
-                k_cg_beta<<<nrhs, 256, 0, sm>>>(cgs, part, part2, nbr, nbz, tol2, delta2, kMixed, 1);
+                k_cg_beta<<<nrhs, 256, 0, sm>>>(cgs, part, part2, nbr, nbz, tol2, delta2, kMixed, 1, 0);
                 HMC_LAUNCH(ctx, "k_cg_beta");
                 if ((rc = launch_pcg_xy_inverse(ctx, lat, zv, pv, pw, nrhs, cgs))) return rc;
                 { C* t = pv; pv = pw; pw = t; }
@@ -414,11 +424,15 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
                 if ((rc = launch_apply_A_strip(ctx, lat, phiR, pv, qv, nrhs, part, &nb, cgs, part2))) return rc;
                 k_cg_ab<<<nrhs, 256, 0, sm>>>(cgs, part, part2, nb);
                 HMC_LAUNCH(ctx, "k_cg_ab");
+                // x is updated on odd iterations only (see k_cg_xrp); never deferred across the host's
+                // checks, where a reliable update may fold x in, nor past maxit
+                const int defer = (it % 2 == 0) && ((it + 1) % check_every != 0) && (it + 1 < maxit);
                 k_cg_xrp<<<vgrid, 256, 0, sm>>>(reinterpret_cast<float4*>(xv), reinterpret_cast<float4*>(rv),
                                                 reinterpret_cast<float4*>(pv), reinterpret_cast<const float4*>(qv),
-                                                n16, part, cgs);
+                                                n16, part, cgs, defer);
                 HMC_LAUNCH(ctx, "k_cg_xrp");
-                k_cg_beta<<<nrhs, 256, 0, sm>>>(cgs, part, nullptr, kRedBlocks, kRedBlocks, tol2, delta2, kMixed, 0);
+                k_cg_beta<<<nrhs, 256, 0, sm>>>(cgs, part, nullptr, kRedBlocks, kRedBlocks, tol2, delta2, kMixed, 0,
+                                                defer);
                 HMC_LAUNCH(ctx, "k_cg_beta");
             }
         } else if (!xy) {
@@ -447,7 +461,8 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
                                               n16, part, cgs);
             HMC_LAUNCH(ctx, "k_cg_xr");
         }
-        k_cg_beta<<<nrhs, 256, 0, sm>>>(cgs, part, precond ? part2 : nullptr, nbr, nbz, tol2, delta2, kMixed, 1);
+        k_cg_beta<<<nrhs, 256, 0, sm>>>(cgs, part, precond ? part2 : nullptr, nbr, nbz, tol2, delta2, kMixed, 1,
+                                        0);
         HMC_LAUNCH(ctx, "k_cg_beta");
         }
         ++it;

@@ -75,6 +75,7 @@ struct CgScalars {
     double r2_max;    // largest ||r||^2 since the last reliable update
     double b2;        // <b, b>
     double r2true;    // ||b - A x||^2 at the last true-residual evaluation
+    double carry;     // fused plain CG: alpha / beta of an iteration whose x update was deferred
     int active;       // 1 while this RHS iterates
     int iters;
     int need_ru;      // set when a true-residual (reliable) update is due
