@@ -31,6 +31,17 @@ struct PcTables {
 };
 
 // Tile shape chosen for the fused A kernel per (L, Nt, nrhs, precision).
+// Block schedule of the strip operator for one (lattice, nrhs, resident blocks): right-hand side
+// k runs in nch[k] time chunks of its Nt slices; blocks are launched right-hand side by right-hand
+// side in the order `order`, chunk by chunk, the strips of a chunk together.
+struct StripSched {
+    int L = 0, Nt = 0, nrhs = 0, slots = 0;   // key: lattice, right-hand sides, resident blocks
+    int maxch = 0;                             // largest chunk count (partial-sum stride / strips)
+    int nblk = 0;                              // blocks of the launch
+    unsigned char order[64];
+    unsigned char nch[64];
+};
+
 struct ATuned {
     int L, Nt, nrhs, prec;
     int TX, TY, C;
@@ -99,6 +110,7 @@ struct hmc_ctx {
     std::vector<hmc::FftPlan> plans;
     std::vector<hmc::PcTables> pcs;
     std::vector<hmc::ATuned> atuned;   // tile shapes picked for the fused A kernel
+    std::vector<hmc::StripSched> strip_sched;   // block schedules of the strip operator
     hmc::BatchWork batch;                 // batched solve (hmc_params.batch_chains)
     std::vector<int64_t> batch_off;       // site offset of each chain in the concatenated fields
     int64_t vtot = 0;                     // sum of the chains' volumes

@@ -11,10 +11,9 @@
 // each on the rows s, s + NSEG, ... so that the eight threads of a quarter warp read distinct
 // bank groups.
 //
-// The blocks of one time chunk run all strips and right-hand sides together, so a strip's halo
-// columns are read while its neighbour strip has the same slices in L2. (An even split of all
-// outputs over one block per SM, which ends the partial last wave, put neighbouring strips at
-// different slices and ran slower.)
+// The blocks of one time chunk of a right-hand side run all its strips together, so a strip's
+// halo columns are read while its neighbour strip has the same slices in L2. (An even split of all
+// outputs over one block per SM put neighbouring strips at different slices and ran slower.)
 //
 // Per step t (x(t+1) landed in its TMA slot): barrier; then row by row, t_(t+1) = D^dagger x on
 // the row into shared memory and y(t) = D t_ from t_(t) and the row's t_(t+1) still in registers,
@@ -23,7 +22,10 @@
 #include <cuda.h>
 
 #include <cstring>
+#include <functional>
 #include <mutex>
+#include <queue>
+#include <vector>
 
 #include "internal.h"
 
@@ -228,9 +230,10 @@ struct StripMaps {
     CUtensorMap xmain, xhalo, phi;
 };
 
-// Grid: nch time chunks of C slices x P = nrhs * (L / 16) pipelines, block = c * P + p with
-// p = k * (L / 16) + strip. part (if not null): part[k * nblk + c * (L / 16) + strip], nblk =
-// nch * (L / 16), the partial sums of ||D^dagger x_k||^2 over the block's output sites.
+// Grid: the blocks of StripSched sch (right-hand side k in sch.nch[k] time chunks, all strips of a
+// chunk consecutive). part (if not null): part[k * nblk + c * (L / 16) + strip], nblk =
+// sch.maxch * (L / 16), the partial sums of ||D^dagger x_k||^2 over the block's output sites (of
+// ||A x_k||^2 in part_q with QN).
 //
 // Staging: two slots; slice x(ta + m) (and phi(ta + m) of the own columns) arrives by TMA in slot
 // m & 1 on that slot's mbarrier, issued by thread 0 one step ahead. t_ lives in two slices.
@@ -250,7 +253,7 @@ struct StripMaps {
 
 template <int L, int NY, bool QN>
 __global__ void __launch_bounds__(StripShape<L, NY>::NTHR, 1)
-k_apply_A_strip(const __grid_constant__ StripMaps maps, Lat lat, CoefP cf, int nch, int C,
+k_apply_A_strip(const __grid_constant__ StripMaps maps, Lat lat, CoefP cf, const __grid_constant__ StripSched sch,
                 const float* __restrict__ phi, const Site<float>* __restrict__ x, Site<float>* __restrict__ y,
                 double* __restrict__ part, double* __restrict__ part_q, const CgScalars* __restrict__ cgs,
                 int* __restrict__ err, int wait_limit, int test_timeout) {
@@ -295,12 +298,18 @@ k_apply_A_strip(const __grid_constant__ StripMaps maps, Lat lat, CoefP cf, int n
     const int mc = gc == 0 ? 7 : 3, ml = gl == 0 ? 7 : 3, mr = gr == 0 ? 7 : 3;   // swizzle of each region
     constexpr int lim_slot = S::SLOT / 16;
 
-    const int P = gridDim.x / nch;
-    const int c = blockIdx.x / P, p = blockIdx.x - c * P;
-    const int k = p / nstrip, sx = p - k * nstrip;
+    // this block's right-hand side k, time chunk c of nchk and strip sx (see StripSched)
+    int b = blockIdx.x, k = 0, nchk = 1;
+    for (int i = 0; i < sch.nrhs; ++i) {
+        k = sch.order[i];
+        nchk = sch.nch[k];
+        if (b < nchk * nstrip) break;
+        b -= nchk * nstrip;
+    }
+    const int c = b / nstrip, sx = b - c * nstrip;
     const bool active = !cgs || cgs[k].active;   // a converged right-hand side is left as it is
-    const int ta = c * C;
-    const int tb = min(ta + C, Nt);            // outputs y(ta .. tb-1); slices x(ta - 1 .. tb)
+    const int ta = (int)((int64_t)c * Nt / nchk);
+    const int tb = (int)((int64_t)(c + 1) * Nt / nchk);   // outputs y(ta .. tb-1); slices x(ta - 1 .. tb)
 
     const uint32_t bar0 = smem_u32(&bars[0]);
     if (tid == 0) {
@@ -492,14 +501,20 @@ k_apply_A_strip(const __grid_constant__ StripMaps maps, Lat lat, CoefP cf, int n
     }
     float a0, a1;
     upk2(acc, a0, a1);
-    const int64_t slot_out = (int64_t)k * (nch * nstrip) + c * nstrip + sx;
+    // partial sums: slot c * nstrip + sx of right-hand side k's maxch * nstrip; the last chunk's
+    // blocks zero the slots of the chunks their right-hand side does not have
+    const int64_t stride = (int64_t)sch.maxch * nstrip, slot_out = (int64_t)k * stride + c * nstrip + sx;
     if (part) {
         const double tot = block_sum(QN ? (double)a0 : (double)a0 + (double)a1, red);
         if (tid == 0) part[slot_out] = tot;
+        if (c == nchk - 1)
+            for (int cc = nchk + tid; cc < sch.maxch; cc += blockDim.x) part[(int64_t)k * stride + cc * nstrip + sx] = 0.0;
     }
     if (QN && part_q) {
         const double tot = block_sum((double)a1, red);
         if (tid == 0) part_q[slot_out] = tot;
+        if (c == nchk - 1)
+            for (int cc = nchk + tid; cc < sch.maxch; cc += blockDim.x) part_q[(int64_t)k * stride + cc * nstrip + sx] = 0.0;
     }
 }
 
@@ -511,22 +526,65 @@ bool strip_supported(const Lat& lat) {
     return lat.L % 16 == 0 && lat.L >= 16 && lat.L <= 80;
 }
 
-// Time chunk C: the number of chunks makes ceil(blocks / resident blocks) waves; each block stages
-// C + 1 slices and computes C + 1 slices of t_ for C of y, so minimise waves x (C + 1.5).
-static void strip_chunks(int Nt, int pipelines, int resident, int* C_out, int* nch_out) {
-    double best = 1e30;
-    int bC = Nt, bn = 1;
-    for (int C = 4; C <= Nt; ++C) {
-        const int nch = (Nt + C - 1) / C;
-        if (C > 4 && (Nt + C - 2) / (C - 1) == nch) continue;   // same chunk count with a smaller C
-        const int64_t blocks = (int64_t)nch * pipelines;
-        const double waves = (double)((blocks + resident - 1) / resident);
-        const double cost = waves * (C + 1.5);
-        if (cost < best) { best = cost; bC = C; bn = nch; }
+// Block schedule. A block stages C + 1 slices and computes C + 1 slices of t_ for C outputs, so it
+// costs about C + 1.5 slice steps. Right-hand side k is cut into nch[k] equal time chunks, n or
+// n + 1 of them; the right-hand sides with the longer chunks are launched first, so that blocks
+// dealt to the SMs in launch order pair a long first block with a short second one instead of
+// leaving SMs idle in a partial last wave (280 blocks on 152 SMs at 80x80x160 with 8 RHS cost 2 x
+// 24.5 steps; 4 RHS in 7 chunks and 4 in 8 cost 46). The strips of one (k, chunk) are consecutive
+// in the launch, so neighbouring strips read each other's halo columns from L2. The split is the
+// one whose simulated greedy dealing over the resident block slots ends first.
+static void strip_schedule(int Nt, int nrhs, int nstrip, int slots, StripSched* out) {
+    double best = 1e300;
+    int best_n = 1, best_m = 0;
+    std::vector<double> cost;
+    // chunk counts that fill at most 8 waves of the resident slots (more only adds block overhead)
+    int64_t nmax = (int64_t)8 * slots / ((int64_t)nrhs * nstrip);
+    if (nmax < 1) nmax = 1;
+    if (nmax > Nt) nmax = Nt;
+    for (int n = 1; n <= (int)nmax; ++n) {
+        for (int m = 0; m <= nrhs; ++m) {
+            if (m > 0 && n + 1 > Nt) break;
+            cost.clear();
+            for (int i = 0; i < nrhs; ++i) {
+                const int nc = i < nrhs - m ? n : n + 1;
+                for (int c = 0; c < nc; ++c) {
+                    const double len = (double)((int64_t)(c + 1) * Nt / nc - (int64_t)c * Nt / nc) + 1.5;
+                    for (int sx = 0; sx < nstrip; ++sx) cost.push_back(len);
+                }
+            }
+            std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
+            for (int i = 0; i < slots; ++i) free_at.push(0.0);
+            double end = 0.0;
+            for (double c : cost) {
+                const double t = free_at.top() + c;
+                free_at.pop();
+                free_at.push(t);
+                if (t > end) end = t;
+            }
+            if (end < best - 1e-9) { best = end; best_n = n; best_m = m; }
+        }
     }
-    if (Nt < 4) { bC = Nt; bn = 1; }
-    *C_out = bC;
-    *nch_out = bn;
+    out->maxch = best_m > 0 ? best_n + 1 : best_n;
+    out->nblk = 0;
+    for (int i = 0; i < nrhs; ++i) {
+        out->order[i] = (unsigned char)i;
+        out->nch[i] = (unsigned char)(i < nrhs - best_m ? best_n : best_n + 1);
+        out->nblk += out->nch[i] * nstrip;
+    }
+}
+
+static const StripSched* strip_sched(hmc_ctx* ctx, const Lat& lat, int nrhs, int slots) {
+    for (const StripSched& s : ctx->strip_sched)
+        if (s.L == lat.L && s.Nt == lat.Nt && s.nrhs == nrhs && s.slots == slots) return &s;
+    StripSched s;
+    s.L = lat.L;
+    s.Nt = lat.Nt;
+    s.nrhs = nrhs;
+    s.slots = slots;
+    strip_schedule(lat.Nt, nrhs, lat.L / 16, slots, &s);
+    ctx->strip_sched.push_back(s);
+    return &ctx->strip_sched.back();
 }
 
 // cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no link against
@@ -594,10 +652,9 @@ static int go_strip(hmc_ctx* ctx, const Lat& lat, const float* phi, const Site<f
     int bps = (int)(per_sm_smem / (S::smem + 1024));
     if (bps > 2048 / S::NTHR) bps = 2048 / S::NTHR;
     if (bps < 1) bps = 1;
-    const int pipes = nrhs * (L / 16);
-    int C, nch;
-    strip_chunks(lat.Nt, pipes, ctx->num_sms * bps, &C, &nch);
-    const int64_t nblk = (int64_t)nch * (L / 16);
+    if (nrhs > 64) return fail(ctx, HMC_ERR_ARG, "apply_A: at most 64 right-hand sides per launch");
+    const StripSched* sch = strip_sched(ctx, lat, nrhs, ctx->num_sms * bps);
+    const int64_t nblk = (int64_t)sch->maxch * (L / 16);   // partial sums per right-hand side
     const int64_t cap = part_q ? ctx->part_cap / 2 : ctx->part_cap;   // part_q lives in the second half
     if ((part || part_q) && nblk * nrhs > cap) return fail(ctx, HMC_ERR_ARG, "apply_A: reduction buffer too small");
     StripMaps maps;
@@ -605,9 +662,8 @@ static int go_strip(hmc_ctx* ctx, const Lat& lat, const float* phi, const Site<f
     if ((rc = strip_maps(ctx, lat, nrhs, phi, x, &maps))) return rc;
     const int wl = ctx->p.wait_spin_limit > 0 ? ctx->p.wait_spin_limit : (1 << 20);
     auto kern = part_q ? k_apply_A_strip<L, NY, true> : k_apply_A_strip<L, NY, false>;
-    kern<<<(unsigned)(nch * pipes), S::NTHR, S::smem, ctx->stream>>>(maps, lat, make_coef_p(ctx->p), nch, C, phi, x, y,
-                                                                     part, part_q, cgs, ctx->d_flags, wl,
-                                                                     ctx->p.test_wait_timeout);
+    kern<<<(unsigned)sch->nblk, S::NTHR, S::smem, ctx->stream>>>(maps, lat, make_coef_p(ctx->p), *sch, phi, x, y, part,
+                                                                 part_q, cgs, ctx->d_flags, wl, ctx->p.test_wait_timeout);
     HMC_LAUNCH(ctx, "k_apply_A_strip");
     if (nblk_out) *nblk_out = (int)nblk;
     return HMC_OK;
