@@ -532,8 +532,9 @@ def batched_chains():
 
 def run_batched_bench(args):
     """64 independent chains of uneven lattices with 2 RHS each, every force solve of all chains in
-    one persistent launch; value = chain-trajectories per second. The same chains through the
-    serial path (one chain after another, same solver) are timed for comparison."""
+    one persistent launch and the leapfrog replayed as a CUDA graph; value = chain-trajectories per
+    second. The same chains with the leapfrog's kernels launched one by one, and through the serial
+    path (one chain after another, same solver), are timed for comparison."""
     import torch
     from paper_2204_14241_gb300.hmc import Context
     from paper_2204_14241_gb300 import inputs as I
@@ -546,8 +547,9 @@ def run_batched_bench(args):
     kw = dict(solver="mixed", nrhs_max=B_NRHS, cg_tol=TOL, cg_maxit=MAXIT, chains=chains, initial_guess=B_GUESS,
               **COUPLINGS)
     res = {}
-    for mode, steps in (("batched", args.steps), ("serial", max(1, min(args.steps, 2)))):
-        ctx = Context(12, 24, batch_chains=1 if mode == "batched" else 0, **kw)
+    for mode, steps in (("batched", args.steps), ("batched_direct", args.steps), ("serial", max(1, min(args.steps, 2)))):
+        ctx = Context(12, 24, batch_chains=0 if mode == "serial" else 1, batch_graph=1 if mode == "batched" else 0,
+                      **kw)
         ph = [p.clone() for p in phis]
         for w in range(args.warmup):
             ctx.trajectory(ph, sigs, B_EPS, B_NLEAP, nrhs=B_NRHS, precond=False, seed=args.seed, counter=w, check=False)
@@ -575,8 +577,9 @@ def run_batched_bench(args):
                                    f"(amplitude {B_AMP}), free-boson sigma-hat, complex64 CG with FP64 reliable "
                                    f"updates to {TOL}, degree-{B_GUESS} chronological start",
                        "total_sites": int(sum(L * L * Nt for L, Nt, _ in chains))},
-            "batched": res["batched"], "serial": res["serial"],
-            "speedup_vs_serial": res["batched"]["chain_traj_per_s"] / res["serial"]["chain_traj_per_s"]}
+            "batched": res["batched"], "batched_direct": res["batched_direct"], "serial": res["serial"],
+            "speedup_vs_serial": res["batched"]["chain_traj_per_s"] / res["serial"]["chain_traj_per_s"],
+            "graph_speedup": res["batched"]["chain_traj_per_s"] / res["batched_direct"]["chain_traj_per_s"]}
     print(json.dumps(line), flush=True)
 
 

@@ -93,6 +93,12 @@ typedef struct {
                            evaluation solves all (chain, RHS) pairs in one persistent cooperative
                            launch (mixed solver mode only; CG without the preconditioner; grid
                            barriers bounded by wait_spin_limit microseconds, default 2 s) */
+    int batch_graph;    /* with batch_chains: the leapfrog part of a trajectory (every force
+                           evaluation, kick and drift of all chains) runs as one CUDA graph,
+                           captured on first use and replayed while n_leap, eps, the chains'
+                           phi and sigma-hat buffers, nrhs and the solver settings stay the same;
+                           its GPU time is then reported under the solve phase of
+                           hmc_trajectory_stats (the per-phase split is not measured inside it) */
 } hmc_params;
 
 /* Per-chain lattice (batched chains of uneven sizes). Coupling constants other than r

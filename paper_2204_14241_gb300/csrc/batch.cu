@@ -482,16 +482,60 @@ __global__ void k_phi_to32_b(const double* __restrict__ a, float* __restrict__ b
 // ---- host ----------------------------------------------------------------------------------------
 void batch_free(hmc_ctx* ctx) {
     BatchWork& w = ctx->batch;
-    void* ps[] = {w.tiles, w.pair_t0, w.sc, w.part};
+    void* ps[] = {w.tiles, w.pair_t0, w.sc, w.part, w.hist, w.hist_ru};
     for (void* p : ps)
         if (p) cudaFree(p);
-    w.tiles = nullptr; w.pair_t0 = nullptr; w.sc = nullptr; w.part = nullptr;
+    w.tiles = nullptr; w.pair_t0 = nullptr; w.sc = nullptr; w.part = nullptr; w.hist = nullptr; w.hist_ru = nullptr;
     w.K = 0;
+    w.kcap = 0;
 }
 
-int batch_setup(hmc_ctx* ctx, int K) {
+// Statistics of one pair after a solve.
+struct BStat {
+    double r2true, b2;
+    int iters, flags;   // flags: 1 still active (not converged), 2 non-finite
+};
+
+// hist[slot][pair] from the solver scalars; hist_ru[slot] = reliable updates; hist_ru[HMC_MAX_SOLVES]
+// collects the failure flags of every solve of the trajectory (also those past the last slot).
+__global__ void k_batch_record(const BScal* __restrict__ sc, int npairs, const int* __restrict__ iters,
+                               BStat* __restrict__ hist, int* __restrict__ hist_ru, int slot) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npairs) return;
+    const BScal& s = sc[i];
+    const int f = (s.active ? 1 : 0) | (s.nonfinite ? 2 : 0);
+    if (f) atomicOr(hist_ru + HMC_MAX_SOLVES, f);
+    if (slot >= HMC_MAX_SOLVES) return;
+    hist[(int64_t)slot * npairs + i] = BStat{s.r2true, s.b2, s.iters, f};
+    if (i == 0) hist_ru[slot] = iters[1];
+}
+
+int batch_alloc(hmc_ctx* ctx) {
     BatchWork& w = ctx->batch;
-    if (w.K == K && w.tiles) return HMC_OK;
+    const int nc = (int)ctx->chains.size(), K = ctx->kmax;
+    int64_t nt = 0;
+    for (int c = 0; c < nc; ++c) nt += (ctx->chains[c].lat.V + kTile - 1) / kTile;
+    nt *= K;
+    if (nt > (int64_t)1 << 30) return fail(ctx, HMC_ERR_ARG, "hmc_init: too many batched tiles");
+    HMC_CUDA(ctx, cudaMalloc(&w.tiles, nt * sizeof(BTile)));
+    HMC_CUDA(ctx, cudaMalloc((void**)&w.pair_t0, ((size_t)nc * K + 1) * sizeof(int)));
+    HMC_CUDA(ctx, cudaMalloc(&w.sc, (size_t)nc * K * sizeof(BScal)));
+    HMC_CUDA(ctx, cudaMalloc((void**)&w.part, nt * 2 * sizeof(double)));
+    HMC_CUDA(ctx, cudaMalloc(&w.hist, (size_t)HMC_MAX_SOLVES * nc * K * sizeof(BStat)));
+    HMC_CUDA(ctx, cudaMalloc((void**)&w.hist_ru, (HMC_MAX_SOLVES + 1) * sizeof(int)));
+    w.kcap = K;
+    w.ntiles_cap = (int)nt;
+    w.K = 0;
+    w.hch.resize(nc);
+    return HMC_OK;
+}
+
+// Tile table for K right-hand sides (rebuilt only when K changes; synchronous copies into the
+// buffers batch_alloc made).
+static int batch_setup(hmc_ctx* ctx, int K) {
+    BatchWork& w = ctx->batch;
+    if (w.K == K) return HMC_OK;
+    if (K < 1 || K > w.kcap) return fail(ctx, HMC_ERR_ARG, "batched solve: nrhs must be in [1, nrhs_max]");
     const int nc = (int)ctx->chains.size();
     std::vector<BTile> tiles;
     std::vector<int> pt0;
@@ -503,11 +547,7 @@ int batch_setup(hmc_ctx* ctx, int K) {
         }
     }
     pt0.push_back((int)tiles.size());
-    batch_free(ctx);
-    HMC_CUDA(ctx, cudaMalloc(&w.tiles, tiles.size() * sizeof(BTile)));
-    HMC_CUDA(ctx, cudaMalloc((void**)&w.pair_t0, pt0.size() * sizeof(int)));
-    HMC_CUDA(ctx, cudaMalloc(&w.sc, (size_t)nc * K * sizeof(BScal)));
-    HMC_CUDA(ctx, cudaMalloc((void**)&w.part, tiles.size() * 2 * sizeof(double)));
+    HMC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // the tables may be in use by earlier work
     HMC_CUDA(ctx, cudaMemcpy(w.tiles, tiles.data(), tiles.size() * sizeof(BTile), cudaMemcpyHostToDevice));
     HMC_CUDA(ctx, cudaMemcpy(w.pair_t0, pt0.data(), pt0.size() * sizeof(int), cudaMemcpyHostToDevice));
     w.ntiles = (int)tiles.size();
@@ -519,14 +559,11 @@ int batch_setup(hmc_ctx* ctx, int K) {
     return HMC_OK;
 }
 
-int batched_cg(hmc_ctx* ctx, int K, const double* const* phi, const double2* b, double2* x, bool use_x0, double tol,
-               int maxit, int* iterations, int* reliable_updates, double* worst_resid, bool* converged) {
+int batched_begin(hmc_ctx* ctx, int K, const double* const* phi) {
     BatchWork& w = ctx->batch;
     int rc;
     if ((rc = batch_setup(ctx, K))) return rc;
     const int nc = (int)ctx->chains.size();
-    // chain table: phi pointers of this call, FP32 copies of phi
-    std::vector<BChainDev> hc(nc);
     for (int c = 0; c < nc; ++c) {
         const Lat& lat = ctx->chains[c].lat;
         BChainDev d{};
@@ -539,12 +576,23 @@ int batched_cg(hmc_ctx* ctx, int K, const double* const* phi, const double2* b, 
         d.off = ctx->batch_off[c] * K;
         d.phi64 = phi[c];
         d.phi32 = ctx->batch_phi32 + 3 * ctx->batch_off[c];
-        hc[c] = d;
-        k_phi_to32_b<<<(unsigned)((3 * lat.V + 255) / 256), 256, 0, ctx->stream>>>(phi[c], const_cast<float*>(d.phi32),
-                                                                                 3 * lat.V);
+        w.hch[c] = d;
+    }
+    HMC_CUDA(ctx, cudaMemcpyAsync(w.ch, w.hch.data(), nc * sizeof(BChainDev), cudaMemcpyHostToDevice, ctx->stream));
+    HMC_CUDA(ctx, cudaMemsetAsync(w.hist_ru + HMC_MAX_SOLVES, 0, sizeof(int), ctx->stream));
+    return HMC_OK;
+}
+
+int batched_solve(hmc_ctx* ctx, int K, const double2* b, double2* x, bool use_x0, double tol, int maxit, int slot) {
+    BatchWork& w = ctx->batch;
+    if (w.K != K) return fail(ctx, HMC_ERR_STATE, "batched solve: batched_begin was not called for this nrhs");
+    const int nc = (int)ctx->chains.size();
+    for (int c = 0; c < nc; ++c) {
+        const BChainDev& d = w.hch[c];
+        k_phi_to32_b<<<(unsigned)((3 * d.V + 255) / 256), 256, 0, ctx->stream>>>(d.phi64, const_cast<float*>(d.phi32),
+                                                                                 3 * d.V);
         HMC_LAUNCH(ctx, "k_phi_to32");
     }
-    HMC_CUDA(ctx, cudaMemcpyAsync(w.ch, hc.data(), nc * sizeof(BChainDev), cudaMemcpyHostToDevice, ctx->stream));
     BatchArgs a{};
     a.nchains = nc;
     a.K = K;
@@ -578,34 +626,56 @@ int batched_cg(hmc_ctx* ctx, int K, const double* const* phi, const double2* b, 
     a.timeout_ns = ctx->p.wait_spin_limit > 0 ? (long long)ctx->p.wait_spin_limit * 1000LL : 2000000000LL;
     HMC_CUDA(ctx, cudaMemsetAsync(w.bar, 0, 2 * sizeof(unsigned), ctx->stream));
     HMC_CUDA(ctx, cudaMemsetAsync(w.iters, 0, 4 * sizeof(int), ctx->stream));
-    void* args[] = {&a};
-    HMC_CUDA(ctx, cudaLaunchCooperativeKernel((const void*)k_batched_cg, w.grid, kBThreads, args, 0, ctx->stream));
+    // cooperative launch through the attribute form, which stream capture records as a
+    // cooperative kernel node
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)w.grid);
+    cfg.blockDim = dim3(kBThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    HMC_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_batched_cg, a));
     HMC_LAUNCH(ctx, "k_batched_cg");
-    // results
-    std::vector<BScal> hs(nc * K);
-    int hi[2];
-    HMC_CUDA(ctx, cudaMemcpyAsync(hs.data(), w.sc, hs.size() * sizeof(BScal), cudaMemcpyDeviceToHost, ctx->stream));
-    HMC_CUDA(ctx, cudaMemcpyAsync(hi, w.iters, 2 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    k_batch_record<<<(unsigned)((nc * K + 127) / 128), 128, 0, ctx->stream>>>(
+        reinterpret_cast<const BScal*>(w.sc), nc * K, w.iters, reinterpret_cast<BStat*>(w.hist), w.hist_ru, slot);
+    HMC_LAUNCH(ctx, "k_batch_record");
+    return HMC_OK;
+}
+
+int batched_collect(hmc_ctx* ctx, int K, int nsolves, int* iterations, double* worst_resid, int* reliable_updates) {
+    BatchWork& w = ctx->batch;
+    const int nc = (int)ctx->chains.size(), np = nc * K;
+    const int kept = std::min(nsolves, HMC_MAX_SOLVES);
+    std::vector<BStat> hs((size_t)kept * np);
+    std::vector<int> hr(HMC_MAX_SOLVES + 1);
+    if (kept > 0)
+        HMC_CUDA(ctx, cudaMemcpyAsync(hs.data(), w.hist, hs.size() * sizeof(BStat), cudaMemcpyDeviceToHost, ctx->stream));
+    HMC_CUDA(ctx, cudaMemcpyAsync(hr.data(), w.hist_ru, hr.size() * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    int rc;
     if ((rc = check_device_flags(ctx))) return rc;   // synchronises
-    bool conv = true, nonfinite = false;
-    for (int c = 0; c < nc; ++c) {
-        double wr = 0.0;
-        int it = 0;
-        for (int k = 0; k < K; ++k) {
-            const BScal& s = hs[c * K + k];
-            if (s.active) conv = false;
-            if (s.nonfinite) nonfinite = true;
-            const double rel = s.b2 > 0.0 ? std::sqrt(s.r2true / s.b2) : 0.0;
-            if (!(rel <= wr)) wr = rel;
-            if (s.iters > it) it = s.iters;
+    for (int j = 0; j < kept; ++j) {
+        for (int c = 0; c < nc; ++c) {
+            double wr = 0.0;
+            int it = 0;
+            for (int k = 0; k < K; ++k) {
+                const BStat& s = hs[(size_t)j * np + c * K + k];
+                const double rel = s.b2 > 0.0 ? std::sqrt(s.r2true / s.b2) : 0.0;
+                if (!(rel <= wr)) wr = rel;
+                if (s.iters > it) it = s.iters;
+            }
+            iterations[(size_t)j * nc + c] = it;
+            worst_resid[(size_t)j * nc + c] = wr;
         }
-        if (iterations) iterations[c] = it;
-        if (worst_resid) worst_resid[c] = wr;
+        reliable_updates[j] = hr[j];
     }
-    if (reliable_updates) *reliable_updates = hi[1];
-    if (converged) *converged = conv && !nonfinite;
-    if (nonfinite) return fail(ctx, HMC_ERR_NONFINITE, "batched solve: non-finite residual norm");
-    if (!conv) return fail(ctx, HMC_ERR_NOCONV, "batched solve: no convergence in " + std::to_string(maxit) + " iterations");
+    const int f = hr[HMC_MAX_SOLVES];
+    if (f & 2) return fail(ctx, HMC_ERR_NONFINITE, "batched solve: non-finite residual norm");
+    if (f & 1) return fail(ctx, HMC_ERR_NOCONV, "batched solve: no convergence in " + std::to_string(ctx->p.cg_maxit) +
+                                                   " iterations");
     return HMC_OK;
 }
 

@@ -191,6 +191,10 @@ static void free_all(hmc_ctx* ctx) {
                   ctx->d_part, ctx->d_red, ctx->d_cg, ctx->d_u32, ctx->d_flags};
     for (void* p : ps)
         if (p) cudaFree(p);
+    if (ctx->bgraph) cudaGraphExecDestroy(ctx->bgraph);
+    ctx->bgraph = nullptr;
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    ctx->cap_stream = nullptr;
     batch_free(ctx);
     void* bs[] = {ctx->batch_phi32, ctx->d_energy, ctx->batch.bar, ctx->batch.iters, ctx->batch.ch};
     for (void* b : bs)
@@ -308,7 +312,7 @@ int hmc_init(const hmc_params* p, int n_chains, const hmc_chain* chains, void* c
         (rc = dalloc(ctx, &ctx->d_z, nb)) || (rc = dalloc(ctx, &ctx->d_fft, nb)) ||
         (rc = dalloc(ctx, &ctx->d_part, ctx->part_cap)) || (rc = dalloc(ctx, &ctx->d_red, 64)) ||
         (rc = dalloc(ctx, &ctx->d_cg, ctx->kmax)) || (rc = dalloc(ctx, &ctx->d_u32, 4)) ||
-        (rc = dalloc(ctx, &ctx->d_flags, 16))) {
+        (rc = dalloc(ctx, &ctx->d_flags, 16)) || (batch && (rc = batch_alloc(ctx)))) {
         std::string m = ctx->err;
         free_all(ctx);
         delete ctx;
@@ -769,16 +773,17 @@ static int run_batched(hmc_ctx* ctx, const hmc_traj_in* in, hmc_traj_out* out) {
         if ((rc = launch_boson(ctx, lat, ctx->chains[c].r, phi, nullptr, ctx->d_part, &nbb))) return rc;
         if ((rc = reduce_rows(ctx, ctx->d_part, 1, nbb, E + 6 * c + 1))) return rc;
     }
-    // leapfrog with the chronological start over the concatenated solutions
+    // leapfrog with the chronological start over the concatenated solutions; every solve records
+    // its statistics on the device (slot = solve index) and nothing in it waits for the host, so
+    // with batch_graph the whole leapfrog is captured once and replayed as a CUDA graph
+    if ((rc = batched_begin(ctx, K, phis.data()))) return rc;
     const int mode = ctx->p.initial_guess;
     double2* hist[kMaxGuess + 1] = {ctx->d_X};
     for (int j = 1; j <= mode; ++j) hist[j] = ctx->d_Xhist[j - 1];
-    int nsol = 0, n_ru = 0;
+    int nsol = 0;
     const int64_t nall = (int64_t)K * 4 * ctx->vtot;
-    std::vector<int> its(nc);
-    std::vector<double> wres(nc);
-    std::vector<int> tot_it(nc, 0);
-    std::vector<double> worst(nc, 0.0);
+    bool capturing = false;
+    auto mark = [&](int phase) -> int { return capturing ? HMC_OK : tm.mark(phase); };
     auto do_force = [&](bool want) -> int {
         const bool guess = mode && nsol >= 1;
         const int np = guess ? std::min(nsol, mode + 1) : 0;
@@ -804,13 +809,9 @@ static int run_batched(hmc_ctx* ctx, const hmc_traj_in* in, hmc_traj_out* out) {
             HMC_LAUNCH(ctx, "k_extrap");
         }
         int r2;
-        if ((r2 = tm.mark(kPhaseSolve))) return r2;
-        int nru = 0;
-        bool conv = false;
-        r2 = batched_cg(ctx, K, phis.data(), ctx->d_pf, xo, guess, ctx->p.cg_tol, ctx->p.cg_maxit, its.data(), &nru,
-                        wres.data(), &conv);
-        if (r2) return r2;
-        if ((r2 = tm.mark(kPhaseForce))) return r2;
+        if ((r2 = mark(kPhaseSolve))) return r2;
+        if ((r2 = batched_solve(ctx, K, ctx->d_pf, xo, guess, ctx->p.cg_tol, ctx->p.cg_maxit, nsol))) return r2;
+        if ((r2 = mark(kPhaseForce))) return r2;
         for (int c = 0; c < nc; ++c) {
             const ChainDesc& ch = ctx->chains[c];
             int nb = 0;
@@ -821,43 +822,118 @@ static int run_batched(hmc_ctx* ctx, const hmc_traj_in* in, hmc_traj_out* out) {
                 if ((r2 = reduce_rows(ctx, ctx->d_part, 1, nb, E + 6 * c + 5))) return r2;
                 if ((r2 = reduce_rows(ctx, ctx->d_part + nb, 1, nb, E + 6 * c + 4))) return r2;
             }
-            hmc_traj_stats& ts = ctx->tstats[c];
-            if (ts.n_solves < HMC_MAX_SOLVES) {
-                ts.iterations[ts.n_solves] = its[c];
-                ts.true_resid[ts.n_solves] = wres[c];
-            }
-            ts.n_solves += 1;
-            ts.reliable_updates += nru;
-            tot_it[c] += its[c];
-            if (wres[c] > worst[c]) worst[c] = wres[c];
         }
-        if ((r2 = tm.mark(kPhaseOther))) return r2;
+        if ((r2 = mark(kPhaseOther))) return r2;
         if (guess) {
             for (int j = io; j > 0; --j) hist[j] = hist[j - 1];
             hist[0] = xo;
         }
         ++nsol;
-        n_ru += nru;
         return HMC_OK;
     };
     const double eps = in->eps;
     const int64_t nball = 3 * ctx->vtot;
     const unsigned gball = (unsigned)((nball + 255) / 256);
-    rc = do_force(in->n_leap == 0);
-    if (!rc) {
+    auto leapfrog = [&]() -> int {
+        int r2 = do_force(in->n_leap == 0);
+        if (r2) return r2;
         k_axpy<<<gball, 256, 0, sm>>>(0.5 * eps, ctx->d_F, ctx->d_pi, nball);
         HMC_LAUNCH(ctx, "k_axpy");
-        for (int i = 1; i <= in->n_leap && !rc; ++i) {
-            if ((rc = tm.mark(kPhaseMetric))) break;
-            for (int c = 0; c < nc && !rc; ++c)
-                rc = metric_op(ctx, ctx->chains[c].lat, HMC_METRIC_VELOCITY, (const double*)in->sigma_hat[c],
-                               bvec(ctx->d_pi, c), (double*)in->phi[c], eps, nullptr);
-            if (rc) break;
-            if ((rc = tm.mark(kPhaseOther))) break;
-            if ((rc = do_force(i == in->n_leap))) break;
+        for (int i = 1; i <= in->n_leap; ++i) {
+            if ((r2 = mark(kPhaseMetric))) return r2;
+            for (int c = 0; c < nc; ++c)
+                if ((r2 = metric_op(ctx, ctx->chains[c].lat, HMC_METRIC_VELOCITY, (const double*)in->sigma_hat[c],
+                                    bvec(ctx->d_pi, c), (double*)in->phi[c], eps, nullptr)))
+                    return r2;
+            if ((r2 = mark(kPhaseOther))) return r2;
+            if ((r2 = do_force(i == in->n_leap))) return r2;
             k_axpy<<<gball, 256, 0, sm>>>(i < in->n_leap ? eps : 0.5 * eps, ctx->d_F, ctx->d_pi, nball);
             HMC_LAUNCH(ctx, "k_axpy");
         }
+        return HMC_OK;
+    };
+    if (ctx->p.batch_graph) {
+        // the graph is valid for these settings and buffers (everything else it touches is the
+        // context's own workspace)
+        std::vector<unsigned long long> key;
+        auto bits = [](double v) { unsigned long long u; memcpy(&u, &v, 8); return u; };
+        key.push_back((unsigned long long)in->n_leap);
+        key.push_back(bits(eps));
+        key.push_back((unsigned long long)K);
+        key.push_back((unsigned long long)mode);
+        key.push_back(bits(ctx->p.cg_tol));
+        key.push_back((unsigned long long)ctx->p.cg_maxit);
+        key.push_back((unsigned long long)ctx->p.test_wait_timeout);
+        key.push_back((unsigned long long)ctx->p.wait_spin_limit);
+        for (int c = 0; c < nc; ++c) {
+            key.push_back((unsigned long long)(uintptr_t)in->phi[c]);
+            key.push_back((unsigned long long)(uintptr_t)in->sigma_hat[c]);
+        }
+        if (!ctx->bgraph || key != ctx->bgraph_key) {
+            if (ctx->bgraph) {
+                cudaGraphExecDestroy(ctx->bgraph);
+                ctx->bgraph = nullptr;
+            }
+            // capture on the context's own non-blocking stream (the legacy default stream, which a
+            // caller may have given hmc_init, cannot be captured); the graph runs on ctx->stream
+            if (!ctx->cap_stream) HMC_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+            cudaStream_t home = ctx->stream;
+            HMC_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+            const int64_t l0 = ctx->launches;
+            ctx->stream = sm = ctx->cap_stream;
+            capturing = true;
+            rc = leapfrog();
+            capturing = false;
+            ctx->stream = sm = home;
+            ctx->bgraph_kernels = ctx->launches - l0;   // counted again at every replay
+            ctx->launches = l0;
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &graph);
+            if (!rc && ec != cudaSuccess)
+                rc = fail(ctx, HMC_ERR_CUDA, std::string("trajectory: graph capture: ") + cudaGetErrorString(ec));
+            if (!rc) {
+                const cudaError_t ei = cudaGraphInstantiate(&ctx->bgraph, graph, 0);
+                if (ei != cudaSuccess) {
+                    ctx->bgraph = nullptr;
+                    rc = fail(ctx, HMC_ERR_CUDA, std::string("trajectory: graph instantiation: ") +
+                                                     cudaGetErrorString(ei));
+                }
+            }
+            if (graph) cudaGraphDestroy(graph);
+            if (rc) {
+                cudaGetLastError();
+                return rc;
+            }
+            ctx->bgraph_key = key;
+        } else {
+            nsol = in->n_leap + 1;   // what the captured leapfrog performs
+        }
+        if ((rc = tm.mark(kPhaseSolve))) return rc;
+        HMC_CUDA(ctx, cudaGraphLaunch(ctx->bgraph, sm));
+        ctx->launches += ctx->bgraph_kernels;
+        if ((rc = tm.mark(kPhaseOther))) return rc;
+    } else {
+        rc = leapfrog();
+    }
+    // statistics of every solve, read once
+    std::vector<int> its((size_t)std::max(nsol, 1) * nc, 0), nru(std::max(nsol, 1), 0);
+    std::vector<double> wres((size_t)std::max(nsol, 1) * nc, 0.0);
+    std::vector<int> tot_it(nc, 0);
+    std::vector<double> worst(nc, 0.0);
+    if (!rc) rc = batched_collect(ctx, K, nsol, its.data(), wres.data(), nru.data());
+    if (!rc) {
+        const int kept = std::min(nsol, HMC_MAX_SOLVES);
+        for (int j = 0; j < kept; ++j) {
+            for (int c = 0; c < nc; ++c) {
+                hmc_traj_stats& ts = ctx->tstats[c];
+                ts.iterations[j] = its[(size_t)j * nc + c];
+                ts.true_resid[j] = wres[(size_t)j * nc + c];
+                ts.reliable_updates += nru[j];
+                tot_it[c] += its[(size_t)j * nc + c];
+                worst[c] = std::max(worst[c], wres[(size_t)j * nc + c]);
+            }
+        }
+        for (int c = 0; c < nc; ++c) ctx->tstats[c].n_solves = nsol;
     }
     if (!rc) rc = tm.mark(kPhaseMetric);
     for (int c = 0; c < nc && !rc; ++c) {

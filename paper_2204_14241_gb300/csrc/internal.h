@@ -66,6 +66,7 @@ struct BChainDev {
 // Device state of the batched solve, built on first use for a right-hand-side count.
 struct BatchWork {
     int K = 0, ntiles = 0, grid = 0;
+    int kcap = 0, ntiles_cap = 0;   // capacities allocated at hmc_init (nrhs_max right-hand sides)
     void* tiles = nullptr;      // tile table
     int* pair_t0 = nullptr;     // first tile of each (chain, RHS) pair
     void* sc = nullptr;         // per-pair solver scalars
@@ -73,6 +74,9 @@ struct BatchWork {
     unsigned* bar = nullptr;    // grid barrier words
     int* iters = nullptr;       // [0] iterations of the slowest pair, [1] reliable updates, [2] active pairs
     BChainDev* ch = nullptr;    // chain table (n_chains entries)
+    void* hist = nullptr;       // per-solve statistics of every pair, HMC_MAX_SOLVES solves of a trajectory
+    int* hist_ru = nullptr;     // reliable updates of each solve
+    std::vector<BChainDev> hch; // host copy of the chain table of the current trajectory
 };
 
 // Per-RHS solver scalars, device resident (kernels read alpha/beta from here).
@@ -111,6 +115,10 @@ struct hmc_ctx {
     std::vector<hmc::PcTables> pcs;
     std::vector<hmc::ATuned> atuned;   // tile shapes picked for the fused A kernel
     std::vector<hmc::StripSched> strip_sched;   // block schedules of the strip operator
+    cudaGraphExec_t bgraph = nullptr;           // batched leapfrog graph (hmc_params.batch_graph)
+    std::vector<unsigned long long> bgraph_key; // what it was captured for
+    int64_t bgraph_kernels = 0;                 // kernel launches in it
+    cudaStream_t cap_stream = nullptr;          // private stream the graph is captured on
     hmc::BatchWork batch;                 // batched solve (hmc_params.batch_chains)
     std::vector<int64_t> batch_off;       // site offset of each chain in the concatenated fields
     int64_t vtot = 0;                     // sum of the chains' volumes
@@ -273,10 +281,18 @@ unsigned int bounds_take_stencil();
 unsigned int bounds_take_strip();
 
 // batch.cu: all (chain, RHS) pairs of the context solve A X = b in one persistent launch (mixed
-// precision, no preconditioner). b, x: concatenated [chain][k][V][4] complex128 (x holds the start
-// when use_x0). Per chain: iterations of its slowest RHS and its worst final true residual.
-int batched_cg(hmc_ctx* ctx, int K, const double* const* phi, const double2* b, double2* x, bool use_x0, double tol,
-               int maxit, int* iterations, int* reliable_updates, double* worst_resid, bool* converged);
+// precision, no preconditioner). b, x: concatenated [chain][k][V][4] complex128.
+// batch_alloc (hmc_init) allocates the workspace for nrhs_max; batched_begin builds the tile
+// table for K right-hand sides and uploads the chain table (phi pointers) of a trajectory;
+// batched_solve enqueues one solve of every pair from b into x (from x when use_x0) and records
+// its statistics in slot `slot` on the device, with no host synchronisation (so it can be
+// captured in a CUDA graph); batched_collect reads the statistics of solves [0, nsolves) back: per
+// solve and chain the iterations of its slowest pair and its worst true relative residual, per
+// solve the reliable updates.
+int batch_alloc(hmc_ctx* ctx);
+int batched_begin(hmc_ctx* ctx, int K, const double* const* phi);
+int batched_solve(hmc_ctx* ctx, int K, const double2* b, double2* x, bool use_x0, double tol, int maxit, int slot);
+int batched_collect(hmc_ctx* ctx, int K, int nsolves, int* iterations, double* worst_resid, int* reliable_updates);
 void batch_free(hmc_ctx* ctx);
 
 // device error word: reads it (synchronising the stream) and returns HMC_ERR_TIMEOUT, clearing

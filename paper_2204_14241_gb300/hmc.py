@@ -44,7 +44,8 @@ class Params(ctypes.Structure):
                 ("g", ctypes.c_double), ("r", ctypes.c_double), ("u", ctypes.c_double), ("c", ctypes.c_double),
                 ("solver_mode", ctypes.c_int), ("nrhs_max", ctypes.c_int), ("cg_tol", ctypes.c_double),
                 ("cg_maxit", ctypes.c_int), ("initial_guess", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("wait_spin_limit", ctypes.c_int), ("test_wait_timeout", ctypes.c_int), ("batch_chains", ctypes.c_int)]
+                ("wait_spin_limit", ctypes.c_int), ("test_wait_timeout", ctypes.c_int), ("batch_chains", ctypes.c_int),
+                ("batch_graph", ctypes.c_int)]
 
 
 class Chain(ctypes.Structure):
@@ -197,7 +198,7 @@ class Context:
     def __init__(self, L, Nt, dtau=0.1, t_h=(1.0, 0.5), t_v=(0.5, 1.0), mu=(-0.5, -0.5), g=1.0, r=0.5,
                  u=1.0, c=3.0, solver="mixed", nrhs_max=1, cg_tol=1e-10, cg_maxit=100000, chains=None,
                  stream=None, device=None, initial_guess=0, autotune=0, wait_spin_limit=0, test_wait_timeout=0,
-                 batch_chains=0):
+                 batch_chains=0, batch_graph=None):
         self.lib = lib()
         self.device = torch.device(device or "cuda")
         p = Params()
@@ -213,6 +214,8 @@ class Context:
         p.wait_spin_limit = int(wait_spin_limit)
         p.test_wait_timeout = int(test_wait_timeout)
         p.batch_chains = int(batch_chains)
+        # the batched form replays its leapfrog as a CUDA graph unless asked not to
+        p.batch_graph = int(bool(batch_chains) if batch_graph is None else batch_graph)
         self.params = p
         if chains is None:
             chains = [(L, Nt, r)]

@@ -702,6 +702,32 @@ def test_64_uneven_chains_batched_trajectory(guess):
     assert st["n_solves"] == 3 and sum(st["iterations"]) == out["cg_iterations"][5]
 
 
+def test_batched_graph_replay_matches_direct_launches():
+    # the batched leapfrog as a CUDA graph (captured on the first trajectory, replayed on the
+    # next, captured again when eps changes) gives bit for bit the trajectories of the same
+    # kernels launched one by one, with the same per-solve statistics
+    from paper_2204_14241_gb300.hmc import Context
+    chains = _uneven_chains(8)
+    kw = dict(solver="mixed", nrhs_max=2, cg_tol=1e-10, chains=chains, initial_guess=2, batch_chains=1, **COUPLINGS)
+    ctx_g = Context(12, 24, batch_graph=1, **kw)
+    ctx_d = Context(12, 24, batch_graph=0, **kw)
+    phis_g = [dev(I.gaussian_field(1200 + i, L, Nt) * 0.5) for i, (L, Nt, _) in enumerate(chains)]
+    phis_d = [p.clone() for p in phis_g]
+    sigs = [dev(np.ones((3, Nt, L, L))) for (L, Nt, _) in chains]
+    for t, eps in enumerate((0.02, 0.02, 0.02, 0.03)):
+        og = ctx_g.trajectory(phis_g, sigs, eps, 3, nrhs=2, seed=11, counter=t)
+        od = ctx_d.trajectory(phis_d, sigs, eps, 3, nrhs=2, seed=11, counter=t)
+        assert og["status"] == 0 and od["status"] == 0
+        assert og["dH"] == od["dH"] and og["accepted"] == od["accepted"]
+        assert og["cg_iterations"] == od["cg_iterations"]
+        assert all(torch.equal(a, b) for a, b in zip(phis_g, phis_d))
+        for c in (0, 5):
+            sg, sd = ctx_g.trajectory_stats(c), ctx_d.trajectory_stats(c)
+            assert sg["n_solves"] == sd["n_solves"] == 4
+            assert sg["iterations"] == sd["iterations"] and sg["true_resid"] == sd["true_resid"]
+            assert sg["reliable_updates"] == sd["reliable_updates"]
+
+
 def test_batched_grid_barrier_timeout():
     # the batched solve's grid barriers are bounded: with test_wait_timeout its first barrier
     # waits for one arrival more than there are blocks, gives up after wait_spin_limit
