@@ -99,6 +99,27 @@ __global__ void k_philox_uniform(uint64_t seed, uint64_t counter, uint64_t jbase
     out[0] = 1.0 - u1;   // [0, 1)
 }
 
+// Metropolis test (Eq. hmc Hamiltonian) in FP64 for n chains: e[6 c + j] holds kinetic, S_B, S_PF at
+// the start (j = 0, 1, 2) and at the end (j = 3, 4, 5); dH = H_end - H_start; the proposal is
+// accepted when u[c] < exp(-dH) (a non-finite dH is rejected). acc[c] = 1.0 or 0.0.
+__global__ void k_metropolis(const double* __restrict__ e, const double* __restrict__ u, double* __restrict__ dh,
+                             double* __restrict__ acc, int n) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const double* q = e + 6 * c;
+    const double h = (q[3] + q[4] + q[5]) - (q[0] + q[1] + q[2]);
+    dh[c] = h;
+    acc[c] = (isfinite(h) && u[c] < exp(-h)) ? 1.0 : 0.0;
+}
+
+// phi = saved phi where the proposal was rejected (*acc == 0)
+__global__ void k_restore_rejected(double* __restrict__ phi, const double* __restrict__ save, int64_t n,
+                                   const double* __restrict__ acc) {
+    if (*acc != 0.0) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        phi[i] = save[i];
+}
+
 // ---- small vector kernels ------------------------------------------------------------------
 __global__ void k_axpy(double a, const double* __restrict__ x, double* __restrict__ y, int64_t n) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -306,7 +327,7 @@ int hmc_init(const hmc_params* p, int n_chains, const hmc_chain* chains, void* c
         (rc = dalloc(ctx, &ctx->d_phi32, nb)) || (rc = dalloc(ctx, &ctx->d_phi_save, nbw)) ||
         (rc = dalloc(ctx, &ctx->d_pi, nbw)) || (rc = dalloc(ctx, &ctx->d_F, nbw)) || (rc = dalloc(ctx, &ctx->d_vel, nbw)) ||
         (batch && ((rc = dalloc(ctx, &ctx->batch_phi32, 3 * ctx->vtot)) ||
-                   (rc = dalloc(ctx, &ctx->d_energy, 7 * (int64_t)n_chains)) ||
+                   (rc = dalloc(ctx, &ctx->d_energy, 9 * (int64_t)n_chains)) ||
                    (rc = dalloc(ctx, &ctx->batch.bar, 2)) || (rc = dalloc(ctx, &ctx->batch.iters, 4)) ||
                    (rc = dalloc(ctx, &ctx->batch.ch, n_chains)))) ||
         (rc = dalloc(ctx, &ctx->d_z, nb)) || (rc = dalloc(ctx, &ctx->d_fft, nb)) ||
@@ -432,10 +453,11 @@ struct PhaseTimer {
 enum { kPhaseSolve = 0, kPhaseForce = 1, kPhaseMetric = 2, kPhaseOther = 3 };
 
 // F, S_pf and S_b at phi for the pseudofermions pf; X receives A^{-1} pf (starting from the
-// contents of X when use_x0).
+// contents of X when use_x0). S_pf and S_b go to the host (s_pf, s_b) or, with dev_e, stay on the
+// device as dev_e[0], dev_e[1].
 static int force_impl(hmc_ctx* ctx, int chain, const double* phi, const double2* pf, int nrhs, double* F,
                       int include_boson, int precond, double* s_pf, double* s_b, hmc_cg_stats* st,
-                      double2* X, bool use_x0, PhaseTimer* tm = nullptr) {
+                      double2* X, bool use_x0, PhaseTimer* tm = nullptr, double* dev_e = nullptr) {
     const ChainDesc& ch = ctx->chains[chain];
     int rc;
     if (tm && (rc = tm->mark(kPhaseSolve))) return rc;
@@ -444,6 +466,7 @@ static int force_impl(hmc_ctx* ctx, int chain, const double* phi, const double2*
     if (tm && (rc = tm->mark(kPhaseForce))) return rc;
     int nb = 0;
     if ((rc = launch_force(ctx, ch.lat, ch.r, phi, X, pf, nrhs, F, include_boson, ctx->d_part, &nb))) return rc;
+    if (dev_e) return reduce_rows(ctx, ctx->d_part, 2, nb, dev_e);
     if (!s_pf && !s_b) return HMC_OK;
     if ((rc = reduce_rows(ctx, ctx->d_part, 2, nb, ctx->d_red))) return rc;
     double v[2];
@@ -554,22 +577,22 @@ static int run_chain(hmc_ctx* ctx, int c, const hmc_traj_in* in, double out_e[6]
     HMC_CUDA(ctx, cudaMemcpyAsync(ctx->d_phi_save, phi, nb * sizeof(double), cudaMemcpyDeviceToDevice, sm));
 
     // noise
+    // the chain's energy record on the device: E[0..5] kinetic, S_B, S_PF at the start and at the
+    // end, E[6] the uniform draw, E[7] dH, E[8] the decision
+    double* E = ctx->d_red + 40;
     const double2* chi;
     const double* z;
-    double u;
     if (in->noise == HMC_NOISE_EXPLICIT) {
         chi = (const double2*)in->chi[c];
         z = (const double*)in->z[c];
-        u = in->u[c];
+        ctx->h_red[40] = in->u[c];
+        HMC_CUDA(ctx, cudaMemcpyAsync(E + 6, ctx->h_red + 40, sizeof(double), cudaMemcpyHostToDevice, sm));
     } else {
         const uint64_t key = in->seed + 0x9E3779B97F4A7C15ull * (uint64_t)c;
         if ((rc = gen_normal(ctx, key, in->counter, 0, (int64_t)K * 4 * lat.V, 1, (double*)ctx->d_chi))) return rc;
         if ((rc = gen_normal(ctx, key, in->counter, 1ull << 48, nb, 0, ctx->d_z))) return rc;
-        k_philox_uniform<<<1, 1, 0, sm>>>(key, in->counter, 2ull << 48, ctx->d_red + 32);
+        k_philox_uniform<<<1, 1, 0, sm>>>(key, in->counter, 2ull << 48, E + 6);
         HMC_LAUNCH(ctx, "k_philox_uniform");
-        HMC_CUDA(ctx, cudaMemcpyAsync(ctx->h_red + 32, ctx->d_red + 32, sizeof(double), cudaMemcpyDeviceToHost, sm));
-        HMC_CUDA(ctx, cudaStreamSynchronize(sm));
-        u = ctx->h_red[32];
         chi = ctx->d_chi;
         z = ctx->d_z;
     }
@@ -578,24 +601,22 @@ static int run_chain(hmc_ctx* ctx, int c, const hmc_traj_in* in, double out_e[6]
     if ((rc = launch_apply_D<double>(ctx, lat, phi, chi, ctx->d_pf, 0, K))) return rc;
     if ((rc = tm.mark(kPhaseMetric))) return rc;
     if ((rc = metric_op(ctx, lat, HMC_METRIC_MOMENTUM, sig, z, ctx->d_pi, 0.0, nullptr))) return rc;
-    if ((rc = metric_op(ctx, lat, HMC_METRIC_KINETIC, sig, ctx->d_pi, nullptr, 0.0, ctx->d_red))) return rc;
+    if ((rc = metric_op(ctx, lat, HMC_METRIC_KINETIC, sig, ctx->d_pi, nullptr, 0.0, E))) return rc;
     if ((rc = tm.mark(kPhaseOther))) return rc;
     int nbb = 0;
     if ((rc = launch_boson(ctx, lat, ch.r, phi, nullptr, ctx->d_part, &nbb))) return rc;
-    if ((rc = reduce_rows(ctx, ctx->d_part, 1, nbb, ctx->d_red + 1))) return rc;
+    if ((rc = reduce_rows(ctx, ctx->d_part, 1, nbb, E + 1))) return rc;
     {
         const unsigned g = 1024;
         k_norm2<<<g, 256, 0, sm>>>((const double*)chi, (int64_t)K * 8 * lat.V, ctx->d_part);
         HMC_LAUNCH(ctx, "k_norm2");
-        if ((rc = reduce_rows(ctx, ctx->d_part, 1, g, ctx->d_red + 2))) return rc;
+        if ((rc = reduce_rows(ctx, ctx->d_part, 1, g, E + 2))) return rc;
     }
-    double e0[3];
-    if ((rc = fetch_red(ctx, 3, e0))) return rc;
 
     // leapfrog: kick eps/2, (drift eps, kick eps) x n, last kick eps/2
     const double eps = in->eps;
     int tot_it = 0;
-    double wr = 0.0, s_pf = 0.0, s_b = 0.0;
+    double wr = 0.0;
     hmc_cg_stats st;
     // solution history (initial guesses): hist[0] the latest solution, hist[1] the one before, ...; the
     // start of the next solve is the extrapolation through the last min(nsol, mode + 1) of them,
@@ -631,8 +652,8 @@ static int run_chain(hmc_ctx* ctx, int c, const hmc_traj_in* in, double out_e[6]
             }
             HMC_LAUNCH(ctx, "k_extrap");
         }
-        int r2 = force_impl(ctx, c, phi, ctx->d_pf, K, ctx->d_F, 1, in->precond, want ? &s_pf : nullptr,
-                            want ? &s_b : nullptr, &st, xo, guess, &tm);
+        int r2 = force_impl(ctx, c, phi, ctx->d_pf, K, ctx->d_F, 1, in->precond, nullptr, nullptr, &st, xo, guess, &tm,
+                            want ? ctx->d_red + 56 : nullptr);   // S_PF, S_B at the end, swapped into E below
         if (!r2) r2 = tm.mark(kPhaseOther);
         if (ts.n_solves < HMC_MAX_SOLVES) {
             ts.iterations[ts.n_solves] = st.iterations;
@@ -663,16 +684,13 @@ static int run_chain(hmc_ctx* ctx, int c, const hmc_traj_in* in, double out_e[6]
         if (in->n_leap == 0 && !rc) rc = do_force(true);
     }
     if (!rc) rc = tm.mark(kPhaseMetric);
-    if (!rc) rc = metric_op(ctx, lat, HMC_METRIC_KINETIC, sig, ctx->d_pi, nullptr, 0.0, ctx->d_red);
+    if (!rc) rc = metric_op(ctx, lat, HMC_METRIC_KINETIC, sig, ctx->d_pi, nullptr, 0.0, E + 3);
     if (!rc) rc = tm.mark(kPhaseOther);
-    double k1 = 0.0;
-    if (!rc) rc = fetch_red(ctx, 1, &k1);
     if (!rc && jump2) {
         // squared M-norm of the proposed jump (Eq. ESJD), accepted or not
         k_sub<<<gb, 256, 0, sm>>>(phi, ctx->d_phi_save, ctx->d_vel, nb);
         HMC_LAUNCH(ctx, "k_sub");
-        rc = metric_op(ctx, lat, HMC_METRIC_MNORM, sig, ctx->d_vel, nullptr, 0.0, ctx->d_red);
-        if (!rc) rc = fetch_red(ctx, 1, jump2);
+        rc = metric_op(ctx, lat, HMC_METRIC_MNORM, sig, ctx->d_vel, nullptr, 0.0, ctx->d_red + 60);
     }
     *iters = tot_it;
     *worst = wr;
@@ -681,20 +699,23 @@ static int run_chain(hmc_ctx* ctx, int c, const hmc_traj_in* in, double out_e[6]
         cudaStreamSynchronize(sm);
         return rc;
     }
-    out_e[0] = e0[0]; out_e[1] = e0[1]; out_e[2] = e0[2];
-    out_e[3] = k1; out_e[4] = s_b; out_e[5] = s_pf;
-    const double h = (k1 + s_b + s_pf) - (e0[0] + e0[1] + e0[2]);
-    *dH = h;
-    if (!std::isfinite(h)) {
-        cudaMemcpyAsync(phi, ctx->d_phi_save, nb * sizeof(double), cudaMemcpyDeviceToDevice, sm);
-        cudaStreamSynchronize(sm);
-        *acc = 0;
-        return fail(ctx, HMC_ERR_NONFINITE, "trajectory: non-finite energy change");
-    }
-    *acc = u < std::exp(-h) ? 1 : 0;
-    if (!*acc) HMC_CUDA(ctx, cudaMemcpyAsync(phi, ctx->d_phi_save, nb * sizeof(double), cudaMemcpyDeviceToDevice, sm));
+    // the Metropolis test and the restore of a rejected proposal on the device
+    HMC_CUDA(ctx, cudaMemcpyAsync(E + 4, ctx->d_red + 57, sizeof(double), cudaMemcpyDeviceToDevice, sm));   // S_B
+    HMC_CUDA(ctx, cudaMemcpyAsync(E + 5, ctx->d_red + 56, sizeof(double), cudaMemcpyDeviceToDevice, sm));   // S_PF
+    k_metropolis<<<1, 32, 0, sm>>>(E, E + 6, E + 7, E + 8, 1);
+    HMC_LAUNCH(ctx, "k_metropolis");
+    k_restore_rejected<<<(unsigned)std::min<int64_t>(gb, (int64_t)ctx->num_sms * 8), 256, 0, sm>>>(phi, ctx->d_phi_save,
+                                                                                                   nb, E + 8);
+    HMC_LAUNCH(ctx, "k_restore_rejected");
     if ((rc = tm.mark(kPhaseOther))) return rc;
+    HMC_CUDA(ctx, cudaMemcpyAsync(ctx->h_red, E, 9 * sizeof(double), cudaMemcpyDeviceToHost, sm));
+    if (jump2) HMC_CUDA(ctx, cudaMemcpyAsync(ctx->h_red + 9, ctx->d_red + 60, sizeof(double), cudaMemcpyDeviceToHost, sm));
     HMC_CUDA(ctx, cudaStreamSynchronize(sm));
+    for (int q = 0; q < 6; ++q) out_e[q] = ctx->h_red[q];
+    *dH = ctx->h_red[7];
+    *acc = ctx->h_red[8] != 0.0 ? 1 : 0;
+    if (jump2) *jump2 = ctx->h_red[9];
+    if (!std::isfinite(*dH)) return fail(ctx, HMC_ERR_NONFINITE, "trajectory: non-finite energy change");
     tm.collect(ts.phase_ms);
     ctx->tstats_valid[c] = 1;
     return HMC_OK;
@@ -739,7 +760,9 @@ static int run_batched(hmc_ctx* ctx, const hmc_traj_in* in, hmc_traj_out* out) {
     auto fvec = [&](double2* base, int c) { return base + (int64_t)K * 4 * ctx->batch_off[c]; };
     auto bvec = [&](double* base, int c) { return base + 3 * ctx->batch_off[c]; };
     std::vector<const double*> phis(nc);
-    double* E = ctx->d_energy;   // [6 c + j]: kinetic, S_B, S_PF at start and end; [6 nc + c]: uniform
+    // [6 c + j]: kinetic, S_B, S_PF at start and end; [6 nc + c]: uniform draw; [7 nc + c]: dH;
+    // [8 nc + c]: the Metropolis decision
+    double* E = ctx->d_energy;
     // heatbath, momenta, initial energies
     for (int c = 0; c < nc; ++c) {
         const Lat& lat = ctx->chains[c].lat;
@@ -951,28 +974,33 @@ static int run_batched(hmc_ctx* ctx, const hmc_traj_in* in, hmc_traj_out* out) {
         }
     }
     if (!rc) rc = tm.mark(kPhaseOther);
-    std::vector<double> he(7 * nc, 0.0);
+    // the Metropolis test of every chain and the restore of rejected proposals on the device
     if (!rc) {
-        HMC_CUDA(ctx, cudaMemcpyAsync(he.data(), E, 7 * nc * sizeof(double), cudaMemcpyDeviceToHost, sm));
+        k_metropolis<<<(unsigned)((nc + 127) / 128), 128, 0, sm>>>(E, E + 6 * nc, E + 7 * nc, E + 8 * nc, nc);
+        HMC_LAUNCH(ctx, "k_metropolis");
+    }
+    for (int c = 0; c < nc; ++c) {
+        const int64_t nb = 3 * ctx->chains[c].lat.V;
+        if (!rc) {
+            k_restore_rejected<<<(unsigned)std::min<int64_t>((nb + 255) / 256, (int64_t)ctx->num_sms * 8), 256, 0, sm>>>(
+                (double*)in->phi[c], bvec(ctx->d_phi_save, c), nb, E + 8 * nc + c);
+            HMC_LAUNCH(ctx, "k_restore_rejected");
+        } else {
+            HMC_CUDA(ctx, cudaMemcpyAsync((double*)in->phi[c], bvec(ctx->d_phi_save, c), nb * sizeof(double),
+                                          cudaMemcpyDeviceToDevice, sm));
+        }
+    }
+    std::vector<double> he(9 * nc, 0.0);
+    if (!rc) {
+        HMC_CUDA(ctx, cudaMemcpyAsync(he.data(), E, 9 * nc * sizeof(double), cudaMemcpyDeviceToHost, sm));
         HMC_CUDA(ctx, cudaStreamSynchronize(sm));
     }
     int first_err = rc;
     for (int c = 0; c < nc; ++c) {
-        const Lat& lat = ctx->chains[c].lat;
-        const int64_t nb = 3 * lat.V;
-        double h = 0.0;
-        int acc = 0;
-        if (!rc) {
-            h = (he[6 * c + 3] + he[6 * c + 4] + he[6 * c + 5]) - (he[6 * c] + he[6 * c + 1] + he[6 * c + 2]);
-            if (!std::isfinite(h)) {
-                if (!first_err) first_err = fail(ctx, HMC_ERR_NONFINITE, "trajectory: non-finite energy change");
-            } else {
-                acc = he[6 * nc + c] < std::exp(-h) ? 1 : 0;
-            }
-        }
-        if (!acc)
-            HMC_CUDA(ctx, cudaMemcpyAsync((double*)in->phi[c], bvec(ctx->d_phi_save, c), nb * sizeof(double),
-                                          cudaMemcpyDeviceToDevice, sm));
+        const double h = rc ? 0.0 : he[7 * nc + c];
+        const int acc = (!rc && he[8 * nc + c] != 0.0) ? 1 : 0;
+        if (!rc && !std::isfinite(h) && !first_err)
+            first_err = fail(ctx, HMC_ERR_NONFINITE, "trajectory: non-finite energy change");
         if (out) {
             if (out->dH) out->dH[c] = h;
             if (out->accepted) out->accepted[c] = acc;
