@@ -169,12 +169,12 @@ __global__ void k_cg_beta(CgScalars* cgs, const double* __restrict__ part_r2,
 
 // Initial scalars: b2 = ||b||^2 from part_b2; r2 = r2_max = ||b - A x0||^2 from part_r2 (or
 // b2 for a zero start). A right-hand side is active unless b = 0 or x0 already meets tol.
-__global__ void k_cg_start(CgScalars* cgs, const double* __restrict__ part_b2, const double* __restrict__ part_r2,
-                           int nblk, double tol2) {
+__global__ void k_cg_start(CgScalars* cgs, const double* __restrict__ part_b2, int nblk_b2,
+                           const double* __restrict__ part_r2, int nblk_r2, double tol2) {
     __shared__ double red[8];
     const int k = blockIdx.x;
-    const double b2 = row_sum(part_b2 + (int64_t)k * nblk, nblk, red);
-    const double r2 = part_r2 ? row_sum(part_r2 + (int64_t)k * nblk, nblk, red) : b2;
+    const double b2 = row_sum(part_b2 + (int64_t)k * nblk_b2, nblk_b2, red);
+    const double r2 = part_r2 ? row_sum(part_r2 + (int64_t)k * nblk_r2, nblk_r2, red) : b2;
     if (threadIdx.x == 0) {
         CgScalars c = {};
         c.b2 = b2;
@@ -284,16 +284,18 @@ __global__ void k_phi_to32(const double* __restrict__ a, float* __restrict__ b, 
 }
 
 // ---- host driver ---------------------------------------------------------------------------
-// FP64 y = A x for the start residual and the reliable updates, as two passes through
-// ctx->d_z64 (t_ = D^dagger x, then y = D t_). GB300's FP64 pipe bounds this operator; the fused
-// kernel recomputes t_ on a one-site ring around each tile (about 2.4 site operations per output
-// site against 2.0 here), and the extra 128 B per RHS-site of traffic hides under the FP64 work:
-// 2.55 ms against 3.33 ms at 80x80x160 with 8 RHS. d_z64 is dead whenever this runs: the next
-// direction restart recomputes z.
-static int apply_A64(hmc_ctx* ctx, const Lat& lat, const double* phi, const double2* x, double2* y, int nrhs) {
+// FP64 true residual r = b - A x for the start from a guess and the reliable updates, as two
+// passes through ctx->d_z64: t_ = D^dagger x, then r = b - D t_ with the complex64 copy and the
+// partial norms fused into the second pass (launch_residual_D). GB300's FP64 pipe bounds both
+// passes; a fused D D^dagger kernel would recompute t_ on a one-site ring around each tile (about
+// 2.4 site operations per output site against 2.0 here) and measured slower (3.33 ms against 2.55
+// ms for A at 80x80x160 with 8 RHS). d_z64 is dead whenever this runs: the next direction restart
+// recomputes z. Right-hand sides already converged (cgs) are skipped.
+static int residual64(hmc_ctx* ctx, const Lat& lat, const double* phi, const double2* x, const double2* b,
+                      double2* r64, float2* r32, int nrhs, double* part, int* nblk, const CgScalars* cgs) {
     int rc;
-    if ((rc = launch_apply_D<double>(ctx, lat, phi, x, ctx->d_z64, 1, nrhs))) return rc;
-    return launch_apply_D<double>(ctx, lat, phi, ctx->d_z64, y, 0, nrhs);
+    if ((rc = launch_apply_D<double>(ctx, lat, phi, x, ctx->d_z64, 1, nrhs, cgs))) return rc;
+    return launch_residual_D(ctx, lat, phi, ctx->d_z64, b, r64, r32, nrhs, part, nblk, cgs);
 }
 
 template <typename R>
@@ -331,16 +333,17 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
         k_dot<double><<<vgrid, 256, 0, sm>>>(reinterpret_cast<const double2*>(b), reinterpret_cast<const double2*>(b),
                                              n, part2, nullptr);
         HMC_LAUNCH(ctx, "k_dot");
-        if ((rc = apply_A64(ctx, lat, phi64, x, ctx->d_q64, nrhs))) return rc;
-        k_residual<<<vgrid, 256, 0, sm>>>(b, ctx->d_q64, ctx->d_r64, kMixed ? ctx->d_r32 : nullptr, n, part, nullptr);
-        HMC_LAUNCH(ctx, "k_residual");
-        k_cg_start<<<nrhs, 256, 0, sm>>>(cgs, part2, part, kRedBlocks, tol2);
+        int nbr = 0;
+        if ((rc = residual64(ctx, lat, phi64, x, b, ctx->d_r64, kMixed ? ctx->d_r32 : nullptr, nrhs, part, &nbr,
+                             nullptr)))
+            return rc;
+        k_cg_start<<<nrhs, 256, 0, sm>>>(cgs, part2, kRedBlocks, part, nbr, tol2);
     } else {
         // zero start: r_hi = b
         HMC_CUDA(ctx, cudaMemsetAsync(x, 0, nrhs * n * sizeof(double2), sm));
         k_residual<<<vgrid, 256, 0, sm>>>(b, x, ctx->d_r64, kMixed ? ctx->d_r32 : nullptr, n, part, nullptr);
         HMC_LAUNCH(ctx, "k_residual");
-        k_cg_start<<<nrhs, 256, 0, sm>>>(cgs, part, nullptr, kRedBlocks, tol2);
+        k_cg_start<<<nrhs, 256, 0, sm>>>(cgs, part, kRedBlocks, nullptr, 0, tol2);
     }
     HMC_LAUNCH(ctx, "k_cg_start");
 
@@ -389,10 +392,10 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
             k_accum_x<<<vgrid, 256, 0, sm>>>(x, ctx->d_x32, n, cgs);
             HMC_LAUNCH(ctx, "k_accum_x");
         }
-        if ((rc = apply_A64(ctx, lat, phi64, x, ctx->d_q64, nrhs))) return rc;
-        k_residual<<<vgrid, 256, 0, sm>>>(b, ctx->d_q64, ctx->d_r64, kMixed ? ctx->d_r32 : nullptr, n, part, cgs);
-        HMC_LAUNCH(ctx, "k_residual");
-        k_ru_finish<<<nrhs, 256, 0, sm>>>(cgs, part, kRedBlocks, tol2);
+        int nbr = 0;
+        if ((rc = residual64(ctx, lat, phi64, x, b, ctx->d_r64, kMixed ? ctx->d_r32 : nullptr, nrhs, part, &nbr, cgs)))
+            return rc;
+        k_ru_finish<<<nrhs, 256, 0, sm>>>(cgs, part, nbr, tol2);
         HMC_LAUNCH(ctx, "k_ru_finish");
         return restart_dir();
     };

@@ -216,9 +216,16 @@ int cuda_check(hmc_ctx* ctx, cudaError_t e, const char* what);
 template <typename R> Coef<R> make_coef(const hmc_params& p);
 
 // stencil.cu
+// y = D x (dagger 0) or D^dagger x; right-hand sides with cgs[k].active == 0 are skipped when cgs
+// is given.
 template <typename R>
 int launch_apply_D(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x, cplx<R>* y,
-                   int dagger, int nrhs);
+                   int dagger, int nrhs, const CgScalars* cgs = nullptr);
+// FP64 true residual r = b - D t (t = D^dagger x from launch_apply_D), written as r64 and, if
+// r32 != nullptr, as complex64; per-block partial sums of ||r||^2 in part[k * nblk + b], nblk =
+// *nblk_out. Inactive right-hand sides (cgs) are skipped.
+int launch_residual_D(hmc_ctx* ctx, const Lat& lat, const double* phi, const double2* t, const double2* b,
+                      double2* r64, float2* r32, int nrhs, double* part, int* nblk_out, const CgScalars* cgs);
 // y = A x; if part != nullptr, per-block partial sums of ||D^dag x||^2 are written to
 // part[k * nblk + b] and *nblk_out receives nblk.
 // cgs (may be null): right-hand sides whose cgs[k].active is 0 are skipped. With pnew set,

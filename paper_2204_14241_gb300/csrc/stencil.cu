@@ -24,7 +24,8 @@ template Coef<double> make_coef<double>(const hmc_params&);
 template <typename R, bool DAG>
 __global__ void __launch_bounds__(256) k_apply_D(Lat lat, Coef<R> cf, const R* __restrict__ phi,
                                                  const Site<R>* __restrict__ x,
-                                                 Site<R>* __restrict__ y) {
+                                                 Site<R>* __restrict__ y, const CgScalars* __restrict__ cgs) {
+    if (cgs && !cgs[blockIdx.y].active) return;
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= lat.V) return;
     const int64_t V = lat.V;
@@ -51,19 +52,84 @@ __global__ void __launch_bounds__(256) k_apply_D(Lat lat, Coef<R> cf, const R* _
 
 template <typename R>
 int launch_apply_D(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x, cplx<R>* y,
-                   int dagger, int nrhs) {
+                   int dagger, int nrhs, const CgScalars* cgs) {
     if (nrhs <= 0) return HMC_OK;
     dim3 grid((unsigned)((lat.V + 255) / 256), nrhs);
     Coef<R> cf = make_coef<R>(ctx->p);
     auto xs = reinterpret_cast<const Site<R>*>(x);
     auto ys = reinterpret_cast<Site<R>*>(y);
-    if (dagger) k_apply_D<R, true><<<grid, 256, 0, ctx->stream>>>(lat, cf, phi, xs, ys);
-    else        k_apply_D<R, false><<<grid, 256, 0, ctx->stream>>>(lat, cf, phi, xs, ys);
+    if (dagger) k_apply_D<R, true><<<grid, 256, 0, ctx->stream>>>(lat, cf, phi, xs, ys, cgs);
+    else        k_apply_D<R, false><<<grid, 256, 0, ctx->stream>>>(lat, cf, phi, xs, ys, cgs);
     HMC_LAUNCH(ctx, "k_apply_D");
     return HMC_OK;
 }
-template int launch_apply_D<float>(hmc_ctx*, const Lat&, const float*, const float2*, float2*, int, int);
-template int launch_apply_D<double>(hmc_ctx*, const Lat&, const double*, const double2*, double2*, int, int);
+template int launch_apply_D<float>(hmc_ctx*, const Lat&, const float*, const float2*, float2*, int, int,
+                                   const CgScalars*);
+template int launch_apply_D<double>(hmc_ctx*, const Lat&, const double*, const double2*, double2*, int, int,
+                                    const CgScalars*);
+
+// The FP64 true residual r = b - D t of a reliable update or of a start from a guess, in the
+// operator's second pass: the pass is bound by the FP64 pipe, so streaming b in and r (and its
+// complex64 copy) out costs no extra time, and the separate residual pass is not needed.
+__global__ void __launch_bounds__(256) k_residual_D(Lat lat, Coef<double> cf, const double* __restrict__ phi,
+                                                    const Site<double>* __restrict__ t,
+                                                    const Site<double>* __restrict__ b, Site<double>* __restrict__ r,
+                                                    Site<float>* __restrict__ r32, double* __restrict__ part,
+                                                    const CgScalars* __restrict__ cgs) {
+    __shared__ double red[8];
+    if (cgs && !cgs[blockIdx.y].active) return;
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t V = lat.V;
+    double e = 0.0;
+    if (s < V) {
+        const int L = lat.L;
+        const Site<double>* tk = t + blockIdx.y * V;
+        const int xx = (int)(s % L);
+        const int64_t rest = s / L;
+        const int yy = (int)(rest % L);
+        const int tt = (int)(rest / L);
+        const int64_t row = s - xx, slice = (int64_t)tt * L * L;
+        const int tn = tnext(tt, lat.Nt);
+        const double tsign = tt == lat.Nt - 1 ? -1.0 : 1.0;
+        const double eta = ((xx + yy) & 1) ? -1.0 : 1.0;
+        auto ld = [&](int64_t i) {
+            Site<double> z{};
+            return HMC_IN(i >= 0 && i < V, kBndApplyD) ? load_site(tk + i) : z;
+        };
+        const Site<double> o = site_op<double>(cf, ld(s), ld(row + wrap_dec(xx, L)), ld(row + wrap_inc(xx, L)),
+                                               ld(slice + (int64_t)wrap_dec(yy, L) * L + xx),
+                                               ld(slice + (int64_t)wrap_inc(yy, L) * L + xx),
+                                               ld((int64_t)tn * L * L + (s - slice)), tsign, __ldg(phi + s),
+                                               __ldg(phi + V + s), __ldg(phi + 2 * V + s), eta);
+        const int64_t g = blockIdx.y * V + s;
+        const Site<double> bb = load_site(b + g);
+        Site<double> rr;
+        Site<float> rf;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            rr.c[q] = make_double2(bb.c[q].x - o.c[q].x, bb.c[q].y - o.c[q].y);
+            rf.c[q] = make_float2((float)rr.c[q].x, (float)rr.c[q].y);
+            e += rr.c[q].x * rr.c[q].x + rr.c[q].y * rr.c[q].y;
+        }
+        store_site(r + g, rr);
+        if (r32) store_site(r32 + g, rf);
+    }
+    e = block_sum(e, red);
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = e;
+}
+
+int launch_residual_D(hmc_ctx* ctx, const Lat& lat, const double* phi, const double2* t, const double2* b,
+                      double2* r64, float2* r32, int nrhs, double* part, int* nblk_out, const CgScalars* cgs) {
+    const int nblk = (int)((lat.V + 255) / 256);
+    if ((int64_t)nblk * nrhs > ctx->part_cap) return fail(ctx, HMC_ERR_ARG, "residual: reduction buffer too small");
+    k_residual_D<<<dim3((unsigned)nblk, nrhs), 256, 0, ctx->stream>>>(
+        lat, make_coef<double>(ctx->p), phi, reinterpret_cast<const Site<double>*>(t),
+        reinterpret_cast<const Site<double>*>(b), reinterpret_cast<Site<double>*>(r64),
+        reinterpret_cast<Site<float>*>(r32), part, cgs);
+    HMC_LAUNCH(ctx, "k_residual_D");
+    *nblk_out = nblk;
+    return HMC_OK;
+}
 
 // ---------------------------------------------------------------------------------------
 // Fused y = D (D^dagger x). A block owns a TX x TY tile of sites and marches through a
