@@ -10,8 +10,10 @@
 //
 // Scalars (alpha, beta, norms, flags) live on the device; kernels of right-hand sides that
 // have converged return at once. The host looks at the flags every few iterations.
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
+#include <vector>
 
 #include "internal.h"
 
@@ -400,7 +402,32 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
         return restart_dir();
     };
 
+    // The host reads the flags (one stream synchronisation) after at most check_every iterations.
+    // From each right-hand side's residual decay it predicts when the next reliable update or the
+    // stop is due and checks then, so that the last right-hand side does not run idle up to a
+    // fixed multiple of check_every.
     const int check_every = 8;
+    int next_check = check_every, last_check = 0;
+    std::vector<double> last_r2(nrhs, -1.0), rate(nrhs, 0.0);   // ln ||r||^2 per iteration (< 0)
+    auto plan_next = [&](int now) {
+        int step = check_every;
+        for (int k = 0; k < nrhs; ++k) {
+            const CgScalars& c = ctx->h_cg[k];
+            if (!c.active || !(c.r2 > 0.0)) continue;
+            if (last_r2[k] > 0.0 && now > last_check && c.r2 < last_r2[k])
+                rate[k] = (std::log(c.r2) - std::log(last_r2[k])) / (double)(now - last_check);
+            last_r2[k] = c.r2;
+            // the first threshold the residual crosses (k_cg_beta flags either)
+            const double target = std::max(tol2 * c.b2, kMixed ? delta2 * c.r2_max : tol2 * c.b2);
+            if (rate[k] < 0.0 && c.r2 > target) {
+                const double n = (std::log(target) - std::log(c.r2)) / rate[k];
+                step = std::min(step, std::max(1, (int)std::ceil(n)));
+            }
+        }
+        last_check = now;
+        next_check = now + step;
+    };
+    bool pending = false;   // an x update was deferred to the next iteration (fused path)
     bool done = false, nonfinite = false;
     int it = 0;
     while (!done) {
@@ -427,9 +454,10 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
                 if ((rc = launch_apply_A_strip(ctx, lat, phiR, pv, qv, nrhs, part, &nb, cgs, part2))) return rc;
                 k_cg_ab<<<nrhs, 256, 0, sm>>>(cgs, part, part2, nb);
                 HMC_LAUNCH(ctx, "k_cg_ab");
-                // x is updated on odd iterations only (see k_cg_xrp); never deferred across the host's
-                // checks, where a reliable update may fold x in, nor past maxit
-                const int defer = (it % 2 == 0) && ((it + 1) % check_every != 0) && (it + 1 < maxit);
+                // x is updated on every other iteration only (see k_cg_xrp); never deferred across the
+                // host's checks, where a reliable update may fold x in, nor past maxit
+                const int defer = (!pending && it + 2 <= next_check && it + 2 <= maxit) ? 1 : 0;
+                pending = defer != 0;
                 k_cg_xrp<<<vgrid, 256, 0, sm>>>(reinterpret_cast<float4*>(xv), reinterpret_cast<float4*>(rv),
                                                 reinterpret_cast<float4*>(pv), reinterpret_cast<const float4*>(qv),
                                                 n16, part, cgs, defer);
@@ -469,7 +497,7 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
         HMC_LAUNCH(ctx, "k_cg_beta");
         }
         ++it;
-        if (it % check_every == 0 || it >= maxit) {
+        if (it >= next_check || it >= maxit) {
             HMC_CUDA(ctx, cudaMemcpyAsync(ctx->h_cg, cgs, nrhs * sizeof(CgScalars), cudaMemcpyDeviceToHost, sm));
             if ((rc = check_device_flags(ctx))) return rc;   // synchronises the stream
             bool any_ru = false, any_active = false;
@@ -491,8 +519,10 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
                     if (ctx->h_cg[k].active) any_active = true;
                 }
                 if (nonfinite) break;
+                for (int k = 0; k < nrhs; ++k) last_r2[k] = -1.0;   // a new cycle from the true residual
             }
             if (!any_active) done = true;
+            plan_next(it);
         }
     }
     if (!done && !nonfinite) {
