@@ -583,6 +583,36 @@ def run_batched_bench(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_batched(args):
+    """One trajectory of the batched configuration for an ncu launch list: 64 uneven chains, one
+    warm-up trajectory, then one inside the NVTX range "batched" (the leapfrog's kernels launched
+    one by one, so that each appears in the list)."""
+    import torch
+    from paper_2204_14241_gb300.hmc import Context
+    from paper_2204_14241_gb300 import inputs as I
+    chains = batched_chains()
+    dt = COUPLINGS["dtau"]
+    phis, sigs = [], []
+    for i, (L_, Nt_, r) in enumerate(chains):
+        phis.append(torch.from_numpy(I.ordered_field(5000 + i, L_, Nt_, r, kt(), 1.0 / np.sqrt(dt), B_AMP)).cuda())
+        sigs.append(torch.from_numpy(np.broadcast_to(I.spectrum(L_, Nt_, r, kt())[None] / dt,
+                                                     (3, Nt_, L_, L_)).copy()).cuda())
+    ctx = Context(12, 24, solver="mixed", nrhs_max=B_NRHS, cg_tol=TOL, cg_maxit=MAXIT, chains=chains,
+                  initial_guess=B_GUESS, batch_chains=1, batch_graph=0, **COUPLINGS)
+    for t in range(2):
+        if t == 1:
+            torch.cuda.nvtx.range_push("batched")
+        t0 = time.perf_counter()
+        o = ctx.trajectory(phis, sigs, B_EPS, B_NLEAP, nrhs=B_NRHS, precond=False, seed=args.seed, counter=t,
+                           check=False)
+        torch.cuda.synchronize()
+        if t == 1:
+            torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile_batched": t, "seconds": time.perf_counter() - t0,
+                          "cg_iterations_per_chain": float(np.mean(o["cg_iterations"])), "status": o["status"]}))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -600,12 +630,16 @@ def main():
                     help="run only this many launches of the fused A kernel (the roofline kernel)")
     ap.add_argument("--profile-force", action="store_true",
                     help="run only one force evaluation of the workload (for a capture of the FP64 kernels)")
+    ap.add_argument("--profile-batched", action="store_true",
+                    help="run only two trajectories of the batched configuration, the second inside an NVTX range")
     ap.add_argument("--config", choices=["largest", "batched64"], default="largest",
                     help="largest: the 80x80x160 chain (default); batched64: 64 uneven chains in batched launches")
     args = ap.parse_args()
     global CLOCK_LOG_DIR
     CLOCK_LOG_DIR = args.clock_log
-    if args.config == "batched64":
+    if args.profile_batched:
+        run_profile_batched(args)
+    elif args.config == "batched64":
         run_batched_bench(args)
     elif args.profile_force:
         run_profile_force(args)

@@ -191,14 +191,22 @@ __device__ __forceinline__ void tile_sum(double v, double* part, int tile, int j
     if (threadIdx.x == 0) part[tile * 2 + j] = s;
 }
 
+// Sum of a pair's tile partials by the calling warp (lane l takes tiles l, l + 32, ..., then a fixed
+// shuffle tree): every lane gets the result; the order is fixed, so the sum is reproducible.
 __device__ __forceinline__ double pair_sum(const BatchArgs& a, int p, int j) {
+    const int lane = threadIdx.x & 31;
     double s = 0.0;
-    for (int t = a.pair_t0[p]; t < a.pair_t0[p + 1]; ++t) s += ldcg_dbl(a.part + t * 2 + j);
+    for (int t = a.pair_t0[p] + lane; t < a.pair_t0[p + 1]; t += 32) s += ldcg_dbl(a.part + t * 2 + j);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
 }
 __device__ __forceinline__ int active_of(const BatchArgs& a, int p) { return ldcg_int(&a.sc[p].active); }
 
-__global__ void __launch_bounds__(kBThreads) k_batched_cg(BatchArgs a) {
+// Three blocks per SM (80 registers; the FP64 reliable-update phases spill a little): the phases
+// wait on L2 neighbour loads, and 24 resident warps per SM ran the 64-chain trajectory in 0.88 s
+// against 0.96 s with 16 (two blocks, 90 registers), 0.90 s with 32 and 0.92 s with 40 (spilling).
+__global__ void __launch_bounds__(kBThreads, 3) k_batched_cg(BatchArgs a) {
     __shared__ double red[kBThreads / 32];
     const int G = gridDim.x;
     const int K = a.K;
@@ -268,10 +276,11 @@ __global__ void __launch_bounds__(kBThreads) k_batched_cg(BatchArgs a) {
     if (!(ok = grid_sync(a, never))) return;
     never = false;
     for (int p = blockIdx.x; p < a.npairs; p += G) {
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
             BScal s{};
             s.b2 = pair_sum(a, p, 0);
             s.r2 = pair_sum(a, p, 1);
+            if (threadIdx.x != 0) continue;
             s.r2_max = s.r2;
             s.r2true = s.r2;
             s.rr = s.r2;
@@ -319,8 +328,9 @@ __global__ void __launch_bounds__(kBThreads) k_batched_cg(BatchArgs a) {
         if (!(ok = grid_sync(a, false))) return;
         // ---- II: alpha ----
         for (int p = blockIdx.x; p < a.npairs; p += G) {
-            if (threadIdx.x == 0 && active_of(a, p)) {
+            if (threadIdx.x < 32 && active_of(a, p)) {
                 const double pAp = pair_sum(a, p, 0);
+                if (threadIdx.x != 0) continue;
                 a.sc[p].pAp = pAp;
                 a.sc[p].alpha = (pAp > 0.0 && isfinite(pAp)) ? ldcg_dbl(&a.sc[p].rr) / pAp : 0.0;
                 if (!isfinite(pAp)) a.sc[p].nonfinite = 1;
@@ -355,9 +365,10 @@ __global__ void __launch_bounds__(kBThreads) k_batched_cg(BatchArgs a) {
         if (!(ok = grid_sync(a, false))) return;
         // ---- IV: beta, convergence, reliable-update request ----
         for (int p = blockIdx.x; p < a.npairs; p += G) {
-            if (threadIdx.x == 0 && active_of(a, p)) {
+            if (threadIdx.x < 32 && active_of(a, p)) {
                 BScal& s = a.sc[p];
                 const double r2 = pair_sum(a, p, 1);
+                if (threadIdx.x != 0) continue;
                 const double rr = ldcg_dbl(&s.rr);
                 s.beta = rr > 0.0 ? r2 / rr : 0.0;
                 s.rr = r2;
@@ -447,9 +458,10 @@ __global__ void __launch_bounds__(kBThreads) k_batched_cg(BatchArgs a) {
         }
         if (!(ok = grid_sync(a, false))) return;
         for (int p = blockIdx.x; p < a.npairs; p += G) {
-            if (threadIdx.x == 0 && wants(p)) {
+            if (threadIdx.x < 32 && wants(p)) {
                 BScal& s = a.sc[p];
                 const double r2 = pair_sum(a, p, 1);
+                if (threadIdx.x != 0) continue;
                 s.r2true = r2;
                 s.need_ru = 0;
                 if (!isfinite(r2)) {
