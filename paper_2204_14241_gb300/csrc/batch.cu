@@ -12,8 +12,9 @@
 // so the results are reproducible bit for bit. Phases of one iteration:
 //   I   p = r + beta p_old formed at each site and its neighbours on the fly, t_ = D^dagger p,
 //       partial <p, A p> = ||t_||^2;                                               | barrier
-//   II  alpha = <r, r> / <p, A p> per pair;                                         | barrier
-//   III q = D t_ (never stored), x += alpha p, r -= alpha q, partial ||r||^2;       | barrier
+//   III alpha = <r, r> / <p, A p> of the tile's pair (formed by every block that needs it, in
+//       the same order), q = D t_ (never stored), x += alpha p, r -= alpha q, partial ||r||^2;
+//                                                                                   | barrier
 //   IV  beta, convergence and the reliable-update request per pair;                 | barrier
 // and, when some pair asks for it, a reliable update: x64 += x32, x32 = 0 | t64 = D^dagger x64 |
 // r64 = b - D t64, r32 = r64, partial ||r64||^2 | per pair: converged pairs stop.
@@ -326,24 +327,23 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batched_cg(BatchArgs a) {
             tile_sum(n2, a.part, ti, 0, red);
         }
         if (!(ok = grid_sync(a, false))) return;
-        // ---- II: alpha ----
-        for (int p = blockIdx.x; p < a.npairs; p += G) {
-            if (threadIdx.x < 32 && active_of(a, p)) {
-                const double pAp = pair_sum(a, p, 0);
-                if (threadIdx.x != 0) continue;
-                a.sc[p].pAp = pAp;
-                a.sc[p].alpha = (pAp > 0.0 && isfinite(pAp)) ? ldcg_dbl(&a.sc[p].rr) / pAp : 0.0;
-                if (!isfinite(pAp)) a.sc[p].nonfinite = 1;
-            }
-        }
-        if (!(ok = grid_sync(a, false))) return;
-        // ---- III: q = D t_, x += alpha p, r -= alpha q, ||r||^2 ----
+        // ---- II + III: alpha of the tile's pair, q = D t_, x += alpha p, r -= alpha q, ||r||^2 ----
+        __shared__ double s_alpha;
         for (int ti = blockIdx.x; ti < a.ntiles; ti += G) {
             const BTile tl = a.tiles[ti];
             if (!active_of(a, tl.pair)) continue;
             const BChainDev& c = a.ch[tl.chain];
             const int64_t base = pair_base(c, tl.pair - tl.chain * K);
-            const float alpha = (float)ldcg_dbl(&a.sc[tl.pair].alpha);
+            // every block holding a tile of the pair forms the same alpha (same partials, same order)
+            if (threadIdx.x < 32) {
+                const double pAp = pair_sum(a, tl.pair, 0);
+                if (threadIdx.x == 0) {
+                    s_alpha = (pAp > 0.0 && isfinite(pAp)) ? ldcg_dbl(&a.sc[tl.pair].rr) / pAp : 0.0;
+                    if (!isfinite(pAp)) a.sc[tl.pair].nonfinite = 1;
+                }
+            }
+            __syncthreads();
+            const float alpha = (float)s_alpha;
             const Site<float>* tv = a.t32 + base;
             double r2 = 0.0;
             for (int s = tl.s0 + threadIdx.x; s < tl.s1; s += blockDim.x) {
