@@ -18,6 +18,8 @@
 //   IV  beta, convergence and the reliable-update request per pair;                 | barrier
 // and, when some pair asks for it, a reliable update: x64 += x32, x32 = 0 | t64 = D^dagger x64 |
 // r64 = b - D t64, r32 = r64, partial ||r64||^2 | per pair: converged pairs stop.
+// When the launch ends, t64 holds D^dagger x64 of every pair's returned solution (from the pair's last
+// true residual, or the start), which the force reuses.
 // The grid barrier spins on a generation word with a time limit (globaltimer); a block that gives
 // up sets the error word, and since it never arrives at the next barrier every other block gives
 // up there too: the launch ends and the host reports HMC_ERR_TIMEOUT.
@@ -260,6 +262,7 @@ __global__ void __launch_bounds__(kBThreads, 3) k_batched_cg(BatchArgs a) {
                 }
             } else {
                 store_site(a.x64 + base + s, Site<double>{});
+                store_site(a.t64 + base + s, Site<double>{});   // D^dagger x of the zero start
             }
             store_site(a.r64 + base + s, r);
             Site<float> r32, z{};

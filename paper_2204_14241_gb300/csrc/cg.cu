@@ -302,7 +302,7 @@ static int residual64(hmc_ctx* ctx, const Lat& lat, const double* phi, const dou
 
 template <typename R>
 static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2* b, double2* x,
-               int nrhs, double tol, int maxit, int precond, hmc_cg_stats* st, bool use_x0) {
+               int nrhs, double tol, int maxit, int precond, hmc_cg_stats* st, bool use_x0, bool* y_ready) {
     constexpr bool kMixed = sizeof(R) == 4;
     using C = cplx<R>;
     cudaStream_t sm = ctx->stream;
@@ -341,8 +341,10 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
             return rc;
         k_cg_start<<<nrhs, 256, 0, sm>>>(cgs, part2, kRedBlocks, part, nbr, tol2);
     } else {
-        // zero start: r_hi = b
+        // zero start: r_hi = b. t_ = D^dagger x = 0 until a true residual is formed (a right-hand
+        // side with b = 0 never gets one; y_ready below covers it too)
         HMC_CUDA(ctx, cudaMemsetAsync(x, 0, nrhs * n * sizeof(double2), sm));
+        if (kMixed && y_ready) HMC_CUDA(ctx, cudaMemsetAsync(ctx->d_z64, 0, nrhs * n * sizeof(double2), sm));
         k_residual<<<vgrid, 256, 0, sm>>>(b, x, ctx->d_r64, kMixed ? ctx->d_r32 : nullptr, n, part, nullptr);
         HMC_LAUNCH(ctx, "k_residual");
         k_cg_start<<<nrhs, 256, 0, sm>>>(cgs, part, kRedBlocks, nullptr, 0, tol2);
@@ -551,15 +553,20 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
     }
     if (nonfinite) return fail(ctx, HMC_ERR_NONFINITE, "cg_solve: non-finite residual norm");
     if (!done) return fail(ctx, HMC_ERR_NOCONV, "cg_solve: no convergence in " + std::to_string(maxit) + " iterations");
+    // Mixed mode: every right-hand side stopped at a true-residual evaluation of its final x (or
+    // never iterated, with t_ from the start residual or zero), and nothing else writes d_z64
+    // (the preconditioned residual lives in d_z32), so d_z64 holds D^dagger x.
+    if (y_ready) *y_ready = kMixed;
     return HMC_OK;
 }
 
 int cg_run(hmc_ctx* ctx, int chain, const double* phi, const double2* b, double2* x, int nrhs,
-           double tol, int maxit, int precond, hmc_cg_stats* st, bool use_x0) {
+           double tol, int maxit, int precond, hmc_cg_stats* st, bool use_x0, bool* y_ready) {
     const Lat& lat = ctx->chains[chain].lat;
+    if (y_ready) *y_ready = false;
     if (ctx->p.solver_mode == HMC_SOLVER_MIXED)
-        return run<float>(ctx, lat, phi, b, x, nrhs, tol, maxit, precond, st, use_x0);
-    return run<double>(ctx, lat, phi, b, x, nrhs, tol, maxit, precond, st, use_x0);
+        return run<float>(ctx, lat, phi, b, x, nrhs, tol, maxit, precond, st, use_x0, y_ready);
+    return run<double>(ctx, lat, phi, b, x, nrhs, tol, maxit, precond, st, use_x0, y_ready);
 }
 
 }  // namespace hmc

@@ -461,11 +461,14 @@ static int force_impl(hmc_ctx* ctx, int chain, const double* phi, const double2*
     const ChainDesc& ch = ctx->chains[chain];
     int rc;
     if (tm && (rc = tm->mark(kPhaseSolve))) return rc;
-    rc = cg_run(ctx, chain, phi, pf, X, nrhs, ctx->p.cg_tol, ctx->p.cg_maxit, precond, st, use_x0);
+    bool y_ready = false;   // D^dagger X left by the solve's last true residual
+    rc = cg_run(ctx, chain, phi, pf, X, nrhs, ctx->p.cg_tol, ctx->p.cg_maxit, precond, st, use_x0, &y_ready);
     if (rc) return rc;
     if (tm && (rc = tm->mark(kPhaseForce))) return rc;
     int nb = 0;
-    if ((rc = launch_force(ctx, ch.lat, ch.r, phi, X, pf, nrhs, F, include_boson, ctx->d_part, &nb))) return rc;
+    if ((rc = launch_force(ctx, ch.lat, ch.r, phi, X, pf, nrhs, F, include_boson, ctx->d_part, &nb,
+                           y_ready ? ctx->d_z64 : nullptr)))
+        return rc;
     if (dev_e) return reduce_rows(ctx, ctx->d_part, 2, nb, dev_e);
     if (!s_pf && !s_b) return HMC_OK;
     if ((rc = reduce_rows(ctx, ctx->d_part, 2, nb, ctx->d_red))) return rc;
@@ -838,8 +841,9 @@ static int run_batched(hmc_ctx* ctx, const hmc_traj_in* in, hmc_traj_out* out) {
         for (int c = 0; c < nc; ++c) {
             const ChainDesc& ch = ctx->chains[c];
             int nb = 0;
+            // D^dagger X of the solution is left in d_z64 by the batched solve
             if ((r2 = launch_force(ctx, ch.lat, ch.r, phis[c], fvec(xo, c), fvec(ctx->d_pf, c), K, bvec(ctx->d_F, c), 1,
-                                   ctx->d_part, &nb)))
+                                   ctx->d_part, &nb, fvec(ctx->d_z64, c))))
                 return r2;
             if (want) {
                 if ((r2 = reduce_rows(ctx, ctx->d_part, 1, nb, E + 6 * c + 5))) return r2;

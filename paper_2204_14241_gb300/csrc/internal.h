@@ -240,10 +240,11 @@ int launch_apply_A(hmc_ctx* ctx, const Lat& lat, const R* phi, const cplx<R>* x,
 bool strip_supported(const Lat& lat);
 int launch_apply_A_strip(hmc_ctx* ctx, const Lat& lat, const float* phi, const float2* x, float2* y, int nrhs,
                          double* part, int* nblk_out, const CgScalars* cgs, double* part_q = nullptr);
-// fermion (+ boson) force and the action pieces, see force() in hmc.h.
+// fermion (+ boson) force and the action pieces, see force() in hmc.h. Y (may be null): D^dagger X
+// already computed (same layout as X); otherwise the kernel forms it.
 int launch_force(hmc_ctx* ctx, const Lat& lat, double r, const double* phi, const double2* X,
                  const double2* pf, int nrhs, double* F, int include_boson, double* part,
-                 int* nblk_out);
+                 int* nblk_out, const double2* Y = nullptr);
 int launch_boson(hmc_ctx* ctx, const Lat& lat, double r, const double* phi, double* F,
                  double* part, int* nblk_out);
 
@@ -309,8 +310,10 @@ int check_device_flags(hmc_ctx* ctx);
 // reductions: sum nblk partials for each of k rows into out[k] (device)
 int reduce_rows(hmc_ctx* ctx, const double* part, int k, int nblk, double* out);
 
-// cg.cu; with use_x0 the solve starts from the contents of x instead of zero
+// cg.cu; with use_x0 the solve starts from the contents of x instead of zero. y_ready (may be
+// null): set when ctx->d_z64 holds D^dagger x of the returned solution, computed in FP64 by the
+// true-residual evaluation that ended each right-hand side's solve (mixed mode).
 int cg_run(hmc_ctx* ctx, int chain, const double* phi, const double2* b, double2* x, int nrhs,
-           double tol, int maxit, int precond, hmc_cg_stats* st, bool use_x0 = false);
+           double tol, int maxit, int precond, hmc_cg_stats* st, bool use_x0 = false, bool* y_ready = nullptr);
 
 }  // namespace hmc

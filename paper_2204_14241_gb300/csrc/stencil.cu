@@ -878,14 +878,15 @@ __device__ __forceinline__ void boson_site(const Lat& lat, const BosonCoef& bc,
 }
 
 // Force: F = -dS_B/dphi (optional) + sum_k 2 dtau g eta Re[X^dag (sigma^x (x) sigma^a) Y],
-// Y = D^dagger X computed on the fly. Partials: [0, nblk) = sum_k 2 Re<pf, X> - |Y|^2,
-// [nblk, 2 nblk) = S_B density.
+// Y = D^dagger X computed on the fly, or read from Yin when a solve's last true-residual
+// evaluation left it (the same stencil on the same X, so the same bits, without the FP64 work).
+// Partials: [0, nblk) = sum_k 2 Re<pf, X> - |Y|^2, [nblk, 2 nblk) = S_B density.
 __global__ void __launch_bounds__(256) k_force(Lat lat, Coef<double> cf, BosonCoef bc,
                                                const double* __restrict__ phi,
                                                const Site<double>* __restrict__ X,
                                                const Site<double>* __restrict__ pf, int nrhs,
                                                double* __restrict__ F, int include_boson,
-                                               double* __restrict__ part) {
+                                               double* __restrict__ part, const Site<double>* __restrict__ Yin) {
     __shared__ double red[8];
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double spf = 0.0, sb = 0.0;
@@ -912,8 +913,9 @@ __global__ void __launch_bounds__(256) k_force(Lat lat, Coef<double> cf, BosonCo
         for (int k = 0; k < nrhs; ++k) {
             const Site<double>* Xk = X + k * V;
             const Site<double> xc = ld(Xk, s);
-            const Site<double> Y = site_op<double>(cf, xc, ld(Xk, sxm), ld(Xk, sxp), ld(Xk, sym), ld(Xk, syp),
-                                                   ld(Xk, stm), tsign, p1, p2, p3, eta);
+            const Site<double> Y = Yin ? ld(Yin + k * V, s)
+                                       : site_op<double>(cf, xc, ld(Xk, sxm), ld(Xk, sxp), ld(Xk, sym), ld(Xk, syp),
+                                                         ld(Xk, stm), tsign, p1, p2, p3, eta);
             const Site<double> pk = load_site(pf + k * V + s);
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
@@ -956,13 +958,13 @@ static BosonCoef boson_coef(const hmc_params& p, double r) {
 
 int launch_force(hmc_ctx* ctx, const Lat& lat, double r, const double* phi, const double2* X,
                  const double2* pf, int nrhs, double* F, int include_boson, double* part,
-                 int* nblk_out) {
+                 int* nblk_out, const double2* Y) {
     const int nblk = (int)((lat.V + 255) / 256);
     if (2 * (int64_t)nblk > ctx->part_cap) return fail(ctx, HMC_ERR_ARG, "force: reduction buffer too small");
     k_force<<<nblk, 256, 0, ctx->stream>>>(lat, make_coef<double>(ctx->p), boson_coef(ctx->p, r), phi,
                                            reinterpret_cast<const Site<double>*>(X),
                                            reinterpret_cast<const Site<double>*>(pf), nrhs, F,
-                                           include_boson, part);
+                                           include_boson, part, reinterpret_cast<const Site<double>*>(Y));
     HMC_LAUNCH(ctx, "k_force");
     *nblk_out = nblk;
     return HMC_OK;
