@@ -60,14 +60,14 @@ WORKLOAD_BASE = (f"L={L}x{L}, Nt={NT} (dtau=0.1), 2 bands x 2 spins, {NRHS} pseu
                  f"sigma-hat from Eq. (covest){' about the batch mean' if SIGMA_CENTERED else ''} over the last "
                  f"{N_COVEST}, eps by Eq. (acc_ineq) then backed off until a {NLEAP}-step trajectory is stable")
 # DRAM bytes (read + write) of one launch of the roofline kernel, the plain fused A on 8 RHS at
-# 80x80x160, from one ncu capture of `bench.py --profile-matvec 3` (308.7 MB read + 217.8 MB
+# 80x80x160, from one ncu capture of `bench.py --profile-matvec 3` (324.3 MB read + 220.5 MB
 # written); set to None when that kernel changes until it is captured again.
-ROOFLINE_TRAFFIC_BYTES = 526_469_376
+ROOFLINE_TRAFFIC_BYTES = 544_735_488
 # CG iterations per solve of this workload with the degree-4 chronological start at the tuned step
-# (95.6 measured on a GB300), used only to
+# (92.0 measured on a GB300), used only to
 # scale the oracle's timed sample (a few iterations) to a trajectory when no GPU run is available
 # in the process.
-ITERS_PER_SOLVE_DEFAULT = 96
+ITERS_PER_SOLVE_DEFAULT = 92
 
 
 def kt():
