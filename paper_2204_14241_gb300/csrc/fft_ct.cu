@@ -517,40 +517,55 @@ template <> struct TauSplit<160> { static constexpr int N1 = 16, N2 = 10; };
 
 constexpr int kTauLines = 16, kTauThreads = 256;
 
-// In-place DFTs of size R for every (line, f) task over the positions f + N1 m (STEP_A) or
-// N1 f + m; TW multiplies output m by w_N^{DIR f m}; TWIST multiplies input point pos by
-// conj(e^{i pi pos / N}) before the transform.
-template <int N, bool STEP_A, bool TW, bool TWIST, int DIR>
-__device__ __forceinline__ void tau_step(float2* sm, const float2* tw, const float2* twist) {
+// The tau pass in three steps over a shared tile [N][16] of one right-hand side's 16
+// consecutive inner indices (4 sites x 4 components), N = N1 * N2, loaded whole first:
+//   1. (line, n1): the N2 points t = n1 + N1 m of the tile, times
+//      conj(e^{i pi t / N}) (the twist), N2-point DFT over m, times w_N^{-n1 k2}, into the tile
+//      at position n1 + N1 k2;
+//   2. (line, k2): the N1 points at positions N1 k2 + m: N1-point DFT over m (the spectrum, in
+//      digit-permuted order: position N1 k2 + k1 holds frequency k2 + N2 k1), times P-hat,
+//      inverse N1-point DFT, times w_N^{+m k2}, back in place: forward and inverse of this step
+//      touch the same N1 positions, so P-hat is applied between them in registers;
+//   3. (line, n1): the N2 points n1 + N1 m, inverse N2-point DFT, times e^{i pi t / N} / N,
+//      straight to global memory at t = n1 + N1 m (the 16 lines of one t: 128 contiguous bytes).
+// Against separate forward and inverse steps with P-hat between them, the middle step saves two
+// passes over the tile and two barriers, and the direct stores a third pass.
+template <int N, bool FWD>
+__device__ __forceinline__ void tau_outer(float2* __restrict__ sm, float2* __restrict__ y, int64_t inner, float sc,
+                                          const float2* tw, const float2* twist) {
     constexpr int N1 = TauSplit<N>::N1, N2 = TauSplit<N>::N2;
-    constexpr int R = STEP_A ? N2 : N1;
-    constexpr int NF = STEP_A ? N1 : N2;
-    constexpr int total = kTauLines * NF;
+    constexpr int total = kTauLines * N1;
 #pragma unroll 1
     for (int task = threadIdx.x; task < total; task += kTauThreads) {
         const int line = task % kTauLines, f = task / kTauLines;
-        float2* base = sm + (STEP_A ? f : N1 * f) * kTauLines + line;
-        constexpr int S = (STEP_A ? N1 : 1) * kTauLines;
-        float2 v[R];
+        float2 v[N2];
+        if constexpr (FWD) {
 #pragma unroll
-        for (int m = 0; m < R; ++m) {
-            v[m] = base[m * S];
-            if constexpr (TWIST) {
-                const float2 w = twist[STEP_A ? f + N1 * m : N1 * f + m];
+            for (int m = 0; m < N2; ++m) v[m] = sm[(f + N1 * m) * kTauLines + line];
+#pragma unroll
+            for (int m = 0; m < N2; ++m) {
+                const float2 w = twist[f + N1 * m];
                 v[m] = make_float2(v[m].x * w.x + v[m].y * w.y, v[m].y * w.x - v[m].x * w.y);
             }
-        }
-        bfly<R, DIR>(v);
-        if constexpr (TW) {
+            bfly<N2, -1>(v);
 #pragma unroll
-            for (int m = 1; m < R; ++m) {
-                float2 w = tw[f * m];   // f * m < N
-                if (DIR > 0) w.y = -w.y;
+            for (int m = 1; m < N2; ++m) {
+                const float2 w = tw[f * m];   // f * m < N
                 v[m] = make_float2(v[m].x * w.x - v[m].y * w.y, v[m].x * w.y + v[m].y * w.x);
             }
-        }
 #pragma unroll
-        for (int m = 0; m < R; ++m) base[m * S] = v[m];
+            for (int m = 0; m < N2; ++m) sm[(f + N1 * m) * kTauLines + line] = v[m];
+        } else {
+#pragma unroll
+            for (int m = 0; m < N2; ++m) v[m] = sm[(f + N1 * m) * kTauLines + line];
+            bfly<N2, +1>(v);
+#pragma unroll
+            for (int m = 0; m < N2; ++m) {
+                const float2 w = twist[f + N1 * m];
+                y[(int64_t)(f + N1 * m) * inner + line] =
+                    make_float2(sc * (v[m].x * w.x - v[m].y * w.y), sc * (v[m].x * w.y + v[m].y * w.x));
+            }
+        }
     }
 }
 
@@ -558,10 +573,12 @@ __device__ __forceinline__ void tau_step(float2* sm, const float2* tw, const flo
 // digit-permuted order of the split; A.cosk the cos k table in the order of the x and y
 // positions. A.part (optional): per block sum P-hat |y-hat|^2 / N (= <y_in, P y_in> when y_in is
 // the unitary (x, y) transform of a vector).
-// Six blocks per SM (40 registers): the pass waits on its cp.async loads and barriers, and more
-// resident blocks measured faster than fewer blocks without spills.
+// Resident blocks per SM: six (40 registers) for the short lengths; five (48 registers) from N = 80
+// on, where the 16-point DFTs of the middle step would spill at 40.
+constexpr int tau_min_blocks(int N) { return N >= 80 ? 5 : 6; }
 template <int N>
-__global__ void __launch_bounds__(kTauThreads, 6) k_tau(FftcArgs A) {
+__global__ void __launch_bounds__(kTauThreads, tau_min_blocks(N)) k_tau(FftcArgs A) {
+    constexpr int N1 = TauSplit<N>::N1, N2 = TauSplit<N>::N2;
     __shared__ __align__(16) float2 sm[N * kTauLines];
     __shared__ float2 s_tw[N], s_twist[N], s_ew[N];
     __shared__ double red[kTauThreads / 32];
@@ -570,7 +587,7 @@ __global__ void __launch_bounds__(kTauThreads, 6) k_tau(FftcArgs A) {
     const int64_t i0 = (int64_t)(blockIdx.x % nib) * kTauLines;
     if (A.cgs && !A.cgs[k].active) return;
     float2* y = A.dst + (int64_t)k * N * A.inner + i0;
-    // 16-byte chunks: row t = c / 8, column pair c % 8
+    // the tile arrives whole (cp.async, 16 bytes: row t = c / 8, column pair c % 8)
     for (int c = threadIdx.x; c < N * kTauLines / 2; c += kTauThreads)
         cp_async16(sm + 2 * c, y + (int64_t)(c >> 3) * A.inner + 2 * (c & 7));
     cp_async_commit();
@@ -581,11 +598,9 @@ __global__ void __launch_bounds__(kTauThreads, 6) k_tau(FftcArgs A) {
     }
     cp_async_wait<0>();
     __syncthreads();
-    tau_step<N, true, true, true, -1>(sm, s_tw, s_twist);
+    tau_outer<N, true>(sm, y, A.inner, 0.f, s_tw, s_twist);
     __syncthreads();
-    tau_step<N, false, false, false, -1>(sm, s_tw, s_twist);
-    __syncthreads();
-    // P-hat = 1 / |K-hat|^2; the momentum part depends only on the line
+    // P-hat = 1 / |K-hat|^2; the momentum part depends only on the line (= threadIdx.x % 16)
     float acc = 0.f;
     {
         const int line = threadIdx.x % kTauLines;
@@ -593,29 +608,34 @@ __global__ void __launch_bounds__(kTauThreads, 6) k_tau(FftcArgs A) {
         const int ab = (int)((i & 3) >> 1);
         const int kk = (int)(i >> 2);
         const float base = A.c0[ab] + A.chx[ab] * __ldg(A.cosk + kk % A.L) + A.chy[ab] * __ldg(A.cosk + kk / A.L);
-        for (int p = threadIdx.x / kTauLines; p < N; p += kTauThreads / kTauLines) {
-            const float re = s_ew[p].x + base;
-            const float ph = 1.0f / (re * re + s_ew[p].y * s_ew[p].y);
-            float2 v = sm[p * kTauLines + line];
-            acc += ph * (v.x * v.x + v.y * v.y);
-            sm[p * kTauLines + line] = make_float2(v.x * ph, v.y * ph);
+#pragma unroll 1
+        for (int task = threadIdx.x; task < kTauLines * N2; task += kTauThreads) {
+            const int f = task / kTauLines;
+            float2* col = sm + N1 * f * kTauLines + line;
+            float2 v[N1];
+#pragma unroll
+            for (int m = 0; m < N1; ++m) v[m] = col[m * kTauLines];
+            bfly<N1, -1>(v);
+#pragma unroll
+            for (int m = 0; m < N1; ++m) {
+                const float2 e = s_ew[N1 * f + m];
+                const float re = e.x + base;
+                const float ph = 1.0f / (re * re + e.y * e.y);
+                acc += ph * (v[m].x * v[m].x + v[m].y * v[m].y);
+                v[m] = make_float2(v[m].x * ph, v[m].y * ph);
+            }
+            bfly<N1, +1>(v);
+#pragma unroll
+            for (int m = 1; m < N1; ++m) {
+                const float2 w = s_tw[f * m];   // f * m < N; conjugated
+                v[m] = make_float2(v[m].x * w.x + v[m].y * w.y, v[m].y * w.x - v[m].x * w.y);
+            }
+#pragma unroll
+            for (int m = 0; m < N1; ++m) col[m * kTauLines] = v[m];
         }
     }
     __syncthreads();
-    tau_step<N, false, true, false, +1>(sm, s_tw, s_twist);
-    __syncthreads();
-    tau_step<N, true, false, false, +1>(sm, s_tw, s_twist);
-    __syncthreads();
-    const float sc = A.scale;
-    const float4* s4 = reinterpret_cast<const float4*>(sm);
-    for (int c = threadIdx.x; c < N * kTauLines / 2; c += kTauThreads) {
-        const int t = c >> 3;
-        const float2 w = s_twist[t];
-        const float4 v = s4[c];
-        *reinterpret_cast<float4*>(y + (int64_t)t * A.inner + 2 * (c & 7)) =
-            make_float4(sc * (v.x * w.x - v.y * w.y), sc * (v.x * w.y + v.y * w.x), sc * (v.z * w.x - v.w * w.y),
-                        sc * (v.z * w.y + v.w * w.x));
-    }
+    tau_outer<N, false>(sm, y, A.inner, A.scale, s_tw, s_twist);
     if (A.part) {
         const double tot = block_sum((double)acc, red);
         if (threadIdx.x == 0) A.part[blockIdx.x] = tot / N;   // block = k * nib + inner block
