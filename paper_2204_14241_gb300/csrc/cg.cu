@@ -362,7 +362,7 @@ static int run(hmc_ctx* ctx, const Lat& lat, const double* phi64, const double2*
     // z = P r, rz = <r, z>
     auto restart_dir = [&]() -> int {
         if (precond) {
-            if ((rc = launch_precond<R>(ctx, lat, rv, zv, nrhs))) return rc;
+            if ((rc = launch_precond<R>(ctx, lat, rv, zv, nrhs, qv))) return rc;   // q is free at a restart
             k_dot<R><<<vgrid, 256, 0, sm>>>(reinterpret_cast<const V16<R>*>(rv), reinterpret_cast<const V16<R>*>(zv),
                                             n16, part, cgs);
         } else {

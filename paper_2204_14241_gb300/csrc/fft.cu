@@ -497,7 +497,7 @@ int precond_tau(hmc_ctx* ctx, const Lat& lat, cplx<R>* y, int nrhs, const CgScal
     if (!p || !pt) return fail(ctx, HMC_ERR_STATE, "no preconditioner plan for this lattice");
     if constexpr (sizeof(R) == 4) {
         if (fftc_can(Nt, 4 * (int64_t)L * L))
-            return fftc_precond_tau(ctx, lat, y, nrhs, cgs, pt, pt->cosk32, nullptr, nullptr);
+            return fftc_precond_tau(ctx, lat, y, nrhs, cgs, pt, pt->cosk32, nullptr, nullptr, false);
     }
     PrecondCoef pc;
     pc.dtau = ctx->p.dtau;
@@ -528,16 +528,26 @@ int precond_tau(hmc_ctx* ctx, const Lat& lat, cplx<R>* y, int nrhs, const CgScal
 
 // y = P x: FFT along x (reading x, writing y), along y, the fused tau pass, inverse y and x.
 template <typename R>
-int launch_precond(hmc_ctx* ctx, const Lat& lat, const cplx<R>* x, cplx<R>* y, int nrhs) {
+int launch_precond(hmc_ctx* ctx, const Lat& lat, const cplx<R>* x, cplx<R>* y, int nrhs, cplx<R>* scratch) {
     const int L = lat.L, Nt = lat.Nt;
     int rc;
     if constexpr (sizeof(R) == 4) {
-        // the (x, y) passes and tau pass that PCG runs
+        // the (x, y) passes and tau pass that PCG runs, with the (band-major) spectrum in scratch:
+        // those passes do not run in place
         const PcTables* pt = get_pc(ctx, L, Nt);
-        if (pt && pt->cosk32_xy && fftc_can(Nt, 4 * (int64_t)L * L)) {
-            if ((rc = fftc_xy_apply(ctx, lat, x, y, nrhs, -1, nullptr))) return rc;
-            if ((rc = fftc_precond_tau(ctx, lat, y, nrhs, nullptr, pt, pt->cosk32_xy, nullptr, nullptr))) return rc;
-            return fftc_xy_apply(ctx, lat, y, y, nrhs, +1, nullptr);
+        const int64_t n = (int64_t)nrhs * Nt * L * L * 4;
+        auto apart = [n](const void* a, const void* b) {
+            const cplx<R>* u = static_cast<const cplx<R>*>(a);
+            const cplx<R>* v = static_cast<const cplx<R>*>(b);
+            return u + n <= v || v + n <= u;
+        };
+        if (pt && pt->cosk32_xy && fftc_can(Nt, 4 * (int64_t)L * L) && scratch && apart(scratch, x) &&
+            apart(scratch, y)) {
+            cplx<R>* mid = scratch;
+            if ((rc = fftc_xy_apply(ctx, lat, x, mid, nrhs, -1, nullptr))) return rc;
+            if ((rc = fftc_precond_tau(ctx, lat, mid, nrhs, nullptr, pt, pt->cosk32_xy, nullptr, nullptr, true)))
+                return rc;
+            return fftc_xy_apply(ctx, lat, mid, y, nrhs, +1, nullptr);
         }
     }
     if ((rc = fft_axis<R>(ctx, y, (int64_t)nrhs * Nt * L, L, 4, -1, x))) return rc;
@@ -547,8 +557,8 @@ int launch_precond(hmc_ctx* ctx, const Lat& lat, const cplx<R>* x, cplx<R>* y, i
     if ((rc = fft_axis<R>(ctx, y, (int64_t)nrhs * Nt * L, L, 4, +1))) return rc;
     return HMC_OK;
 }
-template int launch_precond<float>(hmc_ctx*, const Lat&, const float2*, float2*, int);
-template int launch_precond<double>(hmc_ctx*, const Lat&, const double2*, double2*, int);
+template int launch_precond<float>(hmc_ctx*, const Lat&, const float2*, float2*, int, float2*);
+template int launch_precond<double>(hmc_ctx*, const Lat&, const double2*, double2*, int, double2*);
 
 // One preconditioned-CG vector step for every active RHS (see cg.cu): x += alpha p,
 // r -= alpha q with partial ||r||^2 into part_r2, z = P r with partial <r, z> into part_rz.
@@ -616,7 +626,7 @@ int launch_pcg_xy_forward(hmc_ctx* ctx, const Lat& lat, float2* x, float2* r, co
     // order, and the tau pass forms <r, z> = sum P-hat |F~^* r|^2 (F~ unitary) as it applies P-hat
     if ((rc = fftc_xy_update(ctx, lat, x, r, p, q, nrhs, cgs, part_r2, nblk_r2))) return rc;
     if ((rc = fftc_xy_apply(ctx, lat, r, zhat, nrhs, -1, cgs))) return rc;
-    return fftc_precond_tau(ctx, lat, zhat, nrhs, cgs, pt, pt->cosk32_xy, part_rz, nblk_rz);
+    return fftc_precond_tau(ctx, lat, zhat, nrhs, cgs, pt, pt->cosk32_xy, part_rz, nblk_rz, true);
 }
 
 int launch_pcg_xy_inverse(hmc_ctx* ctx, const Lat& lat, const float2* zhat, const float2* pold, float2* pnew,

@@ -405,7 +405,9 @@ int apply_precond(hmc_ctx* ctx, int chain, int prec, const void* x, void* y, int
     DevGuard g(ctx);
     const Lat& lat = ctx->chains[chain].lat;
     if (prec == HMC_FP64) return launch_precond<double>(ctx, lat, (const double2*)x, (double2*)y, nrhs);
-    if (prec == HMC_FP32) return launch_precond<float>(ctx, lat, (const float2*)x, (float2*)y, nrhs);
+    // the FP64 q workspace (twice the bytes needed) holds the complex64 spectrum between passes
+    if (prec == HMC_FP32)
+        return launch_precond<float>(ctx, lat, (const float2*)x, (float2*)y, nrhs, reinterpret_cast<float2*>(ctx->d_q64));
     return fail(ctx, HMC_ERR_ARG, "apply_precond: unknown precision");
 }
 

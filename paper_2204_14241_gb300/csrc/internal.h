@@ -260,7 +260,9 @@ template <typename R>
 int fft_axis(hmc_ctx* ctx, cplx<R>* data, int64_t outer, int n, int64_t inner, int dir,
              const cplx<R>* src = nullptr, const CgScalars* cgs = nullptr, int64_t opr = 1);
 template <typename R>
-int launch_precond(hmc_ctx* ctx, const Lat& lat, const cplx<R>* x, cplx<R>* y, int nrhs);
+// scratch (a vector's worth, aliasing neither x nor y): holds the complex64 (x, y) spectrum
+// between the passes; without it the FP32 path takes the axis-by-axis kernels, which run in place
+int launch_precond(hmc_ctx* ctx, const Lat& lat, const cplx<R>* x, cplx<R>* y, int nrhs, cplx<R>* scratch = nullptr);
 // x += alpha p, r -= alpha q, z = P r for every active RHS with partial sums of ||r||^2 and
 // <r, z> (rows of *nblk_out entries per RHS in part_r2, of *nblk_rz_out in part_rz).
 template <typename R>
