@@ -430,8 +430,9 @@ def run_ours(args):
 
 def run_profile_solve(args):
     """A capture-sized sample of the workload for ncu: on the full lattice, one 8-RHS solve of
-    the workload's solver cut at a fixed iteration count, run twice (the second is the one to
-    capture), plus one fused A apply. Prints the solve statistics."""
+    the workload's solver (the paper's preconditioned CG with --pcg) cut at a fixed iteration
+    count, run twice (the second is the one to capture), plus one fused A apply. Prints the solve
+    statistics."""
     import torch
     from paper_2204_14241_gb300.hmc import Context
     from paper_2204_14241_gb300 import inputs as I
@@ -442,7 +443,7 @@ def run_profile_solve(args):
     for rep in range(2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, st = ctx.cg_solve(phi, b, precond=PRECOND, maxit=args.profile_solve, raise_on_noconv=False)
+        _, st = ctx.cg_solve(phi, b, precond=PRECOND or args.pcg, maxit=args.profile_solve, raise_on_noconv=False)
         torch.cuda.synchronize()
         print(json.dumps({"profile_solve": args.profile_solve, "seconds": time.perf_counter() - t0, **st}))
     x = b.to(torch.complex64)
@@ -624,6 +625,8 @@ def main():
     ap.add_argument("--clock-log", default=None, help="directory for the raw nvidia-smi clock samples")
     ap.add_argument("--profile-solve", type=int, default=0,
                     help="run only a capture-sized sample: one solve cut at this many iterations")
+    ap.add_argument("--pcg", action="store_true",
+                    help="with --profile-solve: the preconditioned CG (the preconditioner's passes) instead")
     ap.add_argument("--profile-trajectory", action="store_true",
                     help="run only two trajectories of the workload, the second inside an NVTX range")
     ap.add_argument("--profile-matvec", type=int, default=0,
