@@ -170,7 +170,10 @@ int apply_MdagM_static(const hmc_params* p, int L, int Nt, int prec, const void*
                        int nrhs, double* norm2, void* cuda_stream);
 
 /* y = P x with P = (K K^dagger)^{-1} = F~ P-hat F~^* (Eqs. Dsplit, twist, Kdiag, precon),
- * K the phi-independent part of D, applied with the twisted FFT. x, y: [nrhs][V][4] in prec. */
+ * K the phi-independent part of D, applied with the twisted FFT. x, y: [nrhs][V][4] in prec
+ * (device), owned by the caller; y may equal x (the complex64 spectrum between the passes is
+ * kept in the context's workspace). Uses the context's stream; errors: HMC_ERR_ARG for a bad
+ * chain, nrhs, pointer or precision. */
 int apply_precond(hmc_ctx* ctx, int chain, int prec, const void* x, void* y, int nrhs);
 
 /* Solve A x = b (Eq. linsys) by CG (precond = 0) or preconditioned CG (precond = 1),

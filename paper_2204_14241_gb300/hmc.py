@@ -296,9 +296,16 @@ class Context:
         return (y, list(nrm)) if norms else y
 
     def apply_precond(self, x, chain=0, out=None):
+        """y = P x (libhmc's apply_precond); out may be x itself."""
         prec, _ = self._prec(x)
         k = self._fermion(x, chain, x.dtype)
-        y = torch.empty_like(x) if out is None else out
+        if out is None:
+            y = torch.empty_like(x)
+        else:
+            self._fermion(out, chain, x.dtype)
+            if tuple(out.shape) != tuple(x.shape):
+                raise ValueError("out must have the shape of x")
+            y = out
         self._check(self.lib.apply_precond(self.h, chain, prec, _ptr(x), _ptr(y), k))
         return y
 

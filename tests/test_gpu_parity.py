@@ -126,17 +126,33 @@ def test_preconditioner(L, Nt, prec):
         assert rel(ys[k], solver.apply_precond(P, xs[k])) < tol
 
 
-@pytest.mark.parametrize("L,Nt", [(16, 8), (24, 6), (40, 4), (80, 4), (20, 160), (12, 80), (16, 48)])
+@pytest.mark.parametrize("L,Nt", [(16, 8), (24, 6), (40, 4), (80, 4), (20, 160), (12, 80), (16, 48), (16, 96)])
 def test_preconditioner_fp32_xy_pass(L, Nt):
     # complex64, L with a compiled (x, y) split: one kernel per band and plane does both axes,
-    # leaving the spectrum in digit-permuted order for the in-place tau pass (the same kernels
-    # as PCG; N_tau = 160, 80, 48 exercise the tau splits 16 x 10, 10 x 8, 8 x 6)
+    # leaving the band-major spectrum in digit-permuted order for the in-place tau pass (the same
+    # kernels as PCG; N_tau = 160, 80, 48 exercise the tau splits 16 x 10, 10 x 8, 8 x 6, and 96
+    # the Stockham tau kernel on that spectrum)
     ctx = ctx_for(L, Nt)
     P = oparams(L, Nt)
     x = dev(I.fermion_noise(50 + L, 2, L, Nt), torch.complex64)
     y = ctx.apply_precond(x)
     for yk, xk in zip(to_paper_vecs(y), to_paper_vecs(x)):
         assert rel(yk, solver.apply_precond(P, xk)) < 1e-5
+
+
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+def test_preconditioner_in_place(dtype):
+    # y may equal x: the complex64 (x, y) passes keep the band-major spectrum in the context's
+    # workspace, so an in-place call gives exactly the out-of-place result
+    L, Nt = 16, 8
+    ctx = ctx_for(L, Nt)
+    x = dev(I.fermion_noise(77, 2, L, Nt), dtype)
+    y = ctx.apply_precond(x)
+    z = x.clone()
+    assert ctx.apply_precond(z, out=z) is z
+    assert torch.equal(y, z)
+    with pytest.raises(ValueError):
+        ctx.apply_precond(x, out=torch.empty_like(x[:1]))
 
 
 @pytest.mark.parametrize("mode", ["fp64", "mixed"])
