@@ -281,6 +281,16 @@ int hmc_counters(const hmc_ctx* ctx, int64_t* kernel_launches);
  * not for use inside stream capture. Errors: HMC_ERR_ARG, HMC_ERR_CUDA. */
 int hmc_fma_peak(int prec, double* flop_per_s);
 
+/* Launch plan of the complex64 strip kernel of A = D D^dagger (Eq. linsys) for an L x L x Nt
+ * lattice (L a multiple of 16 up to 80), nrhs right-hand sides (1..64) and `slots` resident
+ * blocks (SMs x blocks per SM; not in the paper). Right-hand side k runs in nch[k] time chunks of
+ * the Nt slices, each chunk as L/16 strip blocks; right-hand sides are launched in the order
+ * order[0..nrhs-1], and *nblk receives the launch's block count. The chunk counts are the ones
+ * whose greedy dealing of blocks to the slots, a block costing its chunk length + 1.5 slice steps,
+ * ends first. nch and order (caller-owned, nrhs entries) are overwritten. Host only: no device
+ * work, usable without a GPU. Errors: HMC_ERR_ARG. */
+int hmc_strip_plan(int L, int Nt, int nrhs, int slots, int* nch, int* order, int* nblk);
+
 /* Index checks of a library built with -DHMC_BOUNDS: the operator, force and strip kernels check
  * their global and shared-memory indices, record a failed check in a device error word and skip
  * the access (no trap). *word receives the OR of the codes recorded since the last call (1: D

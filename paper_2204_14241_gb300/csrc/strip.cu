@@ -587,6 +587,20 @@ static const StripSched* strip_sched(hmc_ctx* ctx, const Lat& lat, int nrhs, int
     return &ctx->strip_sched.back();
 }
 
+// Host-only view of the block schedule (hmc.h): what a launch of the strip operator would run.
+int strip_plan(int L, int Nt, int nrhs, int slots, int* nch, int* order, int* nblk) {
+    if (L % 16 != 0 || L < 16 || L > 80 || Nt < 1 || nrhs < 1 || nrhs > 64 || slots < 1 || !nch || !order || !nblk)
+        return fail(nullptr, HMC_ERR_ARG, "hmc_strip_plan: bad argument");
+    StripSched s{};
+    strip_schedule(Nt, nrhs, L / 16, slots, &s);
+    for (int i = 0; i < nrhs; ++i) {
+        nch[i] = s.nch[i];
+        order[i] = s.order[i];
+    }
+    *nblk = s.nblk;
+    return HMC_OK;
+}
+
 // cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no link against
 // the driver library)
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -686,3 +700,7 @@ int launch_apply_A_strip(hmc_ctx* ctx, const Lat& lat, const float* phi, const f
 }
 
 }  // namespace hmc
+
+extern "C" int hmc_strip_plan(int L, int Nt, int nrhs, int slots, int* nch, int* order, int* nblk) {
+    return hmc::strip_plan(L, Nt, nrhs, slots, nch, order, nblk);
+}

@@ -29,7 +29,7 @@ METRIC_MOMENTUM, METRIC_VELOCITY, METRIC_KINETIC, METRIC_ACCUM, METRIC_MNORM = r
 EXPORTS = ("hmc_init", "hmc_destroy", "hmc_last_error", "hmc_counters", "apply_M", "apply_MdagM",
            "apply_MdagM_static", "apply_precond", "green_estimate",
            "cg_solve", "force", "metric_apply", "trajectory", "hmc_trajectory_stats", "philox_raw", "philox_normal",
-           "hmc_fma_peak", "hmc_bounds_status")
+           "hmc_fma_peak", "hmc_bounds_status", "hmc_strip_plan")
 
 
 class HmcError(RuntimeError):
@@ -125,6 +125,8 @@ def lib():
         "philox_normal": [_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, _I, _P],
         "hmc_fma_peak": [_I, ctypes.POINTER(ctypes.c_double)],
         "hmc_bounds_status": [ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_int)],
+        "hmc_strip_plan": [_I, _I, _I, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                           ctypes.POINTER(ctypes.c_int)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -146,6 +148,17 @@ def bounds_status():
     if rc:
         raise HmcError(rc, lib_.hmc_last_error(None).decode())
     return w.value, bool(e.value)
+
+
+def strip_plan(L, Nt, nrhs, slots):
+    """(nch, order, nblk): the complex64 strip operator's launch plan (libhmc's hmc_strip_plan,
+    host only)."""
+    lib_ = lib()
+    nch, order, nblk = (ctypes.c_int * nrhs)(), (ctypes.c_int * nrhs)(), ctypes.c_int()
+    rc = lib_.hmc_strip_plan(L, Nt, nrhs, slots, nch, order, ctypes.byref(nblk))
+    if rc:
+        raise HmcError(rc, lib_.hmc_last_error(None).decode())
+    return list(nch), list(order), nblk.value
 
 
 def fma_peak(prec=FP64, device=None):
