@@ -30,15 +30,18 @@ def index(p: Params, alpha, s, tau, x, y):
 
 
 def hop(p: Params, alpha, x, y, xp, yp):
-    """t_{alpha, (x,y), (x',y')}: sum of the nearest-neighbour bond amplitudes joining the
-    two sites on the periodic L x L lattice (each of the four bonds of a site counted once,
-    so on L = 2 the +x and -x bonds both join the same pair)."""
+    """t_{alpha, (x,y), (x',y')}: sum of the bond amplitudes joining the two sites on the
+    periodic L x L lattice, nearest-neighbour (t) and of distance two along an axis (t2); each
+    bond of a site counted once, so on L = 2 the +x and -x bonds join the same pair and the
+    distance-two bonds return to the site itself (and on L = 4 the +2 and -2 bonds coincide)."""
     L = p.L
     t = 0.0
     if yp == y:
         t += p.t_h[alpha] * (((xp - x) % L == 1) + ((x - xp) % L == 1))
+        t += p.t2_h[alpha] * (((xp - x - 2) % L == 0) + ((x - xp - 2) % L == 0))
     if xp == x:
         t += p.t_v[alpha] * (((yp - y) % L == 1) + ((y - yp) % L == 1))
+        t += p.t2_v[alpha] * (((yp - y - 2) % L == 0) + ((y - yp - 2) % L == 0))
     return t
 
 
@@ -93,7 +96,9 @@ def _coupling(p: Params, phi, v):
 def _spatial_hop(p: Params, alpha, v):
     """sum_{r'} t_{alpha, r, r'} v(r') on the periodic lattice; axes -2 = x, -1 = y."""
     return (p.t_h[alpha] * (np.roll(v, 1, axis=-2) + np.roll(v, -1, axis=-2))
-            + p.t_v[alpha] * (np.roll(v, 1, axis=-1) + np.roll(v, -1, axis=-1)))
+            + p.t_v[alpha] * (np.roll(v, 1, axis=-1) + np.roll(v, -1, axis=-1))
+            + p.t2_h[alpha] * (np.roll(v, 2, axis=-2) + np.roll(v, -2, axis=-2))
+            + p.t2_v[alpha] * (np.roll(v, 2, axis=-1) + np.roll(v, -2, axis=-1)))
 
 
 def time_sign(p: Params):
@@ -140,14 +145,16 @@ def apply_K(p: Params, v):
 
 def free_symbol(p: Params):
     """K-hat of Eq. (Kdiag) on the twisted Fourier grid, shape (2, Nt, L, L) indexed
-    [alpha, n, m_x, m_y]: e^{i w_n} - 1 - dtau (mu_alpha + 2 t_h cos k_x + 2 t_v cos k_y)
-    with antiperiodic w_n = (2n + 1) pi / Nt and k = 2 pi m / L.
+    [alpha, n, m_x, m_y]: e^{i w_n} - 1 - dtau (mu_alpha + 2 t_h cos k_x + 2 t_v cos k_y
+    + 2 t2_h cos 2k_x + 2 t2_v cos 2k_y) with antiperiodic w_n = (2n + 1) pi / Nt and
+    k = 2 pi m / L.
     """
     w = (2 * np.arange(p.Nt) + 1) * np.pi / p.Nt
     k = 2 * np.pi * np.arange(p.L) / p.L
     out = np.empty((2, p.Nt, p.L, p.L), dtype=complex)
     for alpha in range(2):
-        eps = (2 * p.t_h[alpha] * np.cos(k)[:, None] + 2 * p.t_v[alpha] * np.cos(k)[None, :])
+        eps = (2 * p.t_h[alpha] * np.cos(k)[:, None] + 2 * p.t_v[alpha] * np.cos(k)[None, :]
+               + 2 * p.t2_h[alpha] * np.cos(2 * k)[:, None] + 2 * p.t2_v[alpha] * np.cos(2 * k)[None, :])
         out[alpha] = (np.exp(1j * w)[:, None, None] - 1.0
                       - p.dtau * (p.mu[alpha] + eps[None, :, :]))
     return out

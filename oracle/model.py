@@ -9,6 +9,11 @@ width dtau (0.1 in the paper), fermions antiperiodic and the boson periodic in t
 Readings (the paper is silent or ambiguous):
 * t_h[alpha], t_v[alpha] are the signed nearest-neighbour amplitudes along x and y
   for band alpha; the hop enters D as -dtau * t (Eq. D_formula).
+* t2_h[alpha], t2_v[alpha] are the amplitudes of hops of distance two along x and y (zero by
+  default): the paper's "next-nearest-neighbour" t~_{v,x} = -t~_{h,y} of the five nesting sets,
+  read as the hop of distance two along each band's weak direction, because that reading gives
+  the nesting parameters v_1 ... v_5 the paper prints for those sets (the nearest-neighbour
+  reading gives Fermi lines crossing at ~88 degrees). They enter D like t.
 * e^{i Q_AF . r} with Q_AF = (pi, pi) is (-1)^{x+y}; L must be even.
 """
 
@@ -29,6 +34,8 @@ class Params:
     r: float = 0.5            # boson mass term (r/2) phi^2
     u: float = 1.0            # quartic (u/4) phi^4
     c: float = 3.0            # boson velocity: (1/c^2) (d_tau phi)^2
+    t2_h: tuple = (0.0, 0.0)  # hopping of distance two along x for bands (x, y)
+    t2_v: tuple = (0.0, 0.0)  # hopping of distance two along y for bands (x, y)
 
     def __post_init__(self):
         if self.L < 2 or self.L % 2:

@@ -31,9 +31,16 @@ def match_multisets(a, b):
     return d[i, j].max()
 
 
+def band_energy(p, a, kx, ky):
+    """Fourier transform of band a's hops: a hop of distance d along an axis contributes
+    t (e^{i d k} + e^{-i d k}) = 2 t cos(d k) (d = 1: t_h, t_v; d = 2: t2_h, t2_v)."""
+    return (2 * p.t_h[a] * np.cos(kx) + 2 * p.t_v[a] * np.cos(ky)
+            + 2 * p.t2_h[a] * np.cos(2 * kx) + 2 * p.t2_v[a] * np.cos(2 * ky))
+
+
 def free_eigs_closed_form(p):
-    """Eigenvalues of D at g = 0: e^{i w} - 1 - dtau (mu_a + 2 t_h cos kx + 2 t_v cos ky),
-    w = (2n+1) pi / Nt (antiperiodic), k = 2 pi m / L, each twice (spin)."""
+    """Eigenvalues of D at g = 0: e^{i w} - 1 - dtau (mu_a + eps_a(k)), w = (2n+1) pi / Nt
+    (antiperiodic), k = 2 pi m / L, each twice (spin)."""
     out = []
     for a in range(2):
         for n in range(p.Nt):
@@ -41,36 +48,41 @@ def free_eigs_closed_form(p):
             for mx in range(p.L):
                 for my in range(p.L):
                     kx, ky = 2 * np.pi * mx / p.L, 2 * np.pi * my / p.L
-                    e = np.exp(1j * w) - 1 - p.dtau * (p.mu[a] + 2 * p.t_h[a] * np.cos(kx)
-                                                        + 2 * p.t_v[a] * np.cos(ky))
+                    e = np.exp(1j * w) - 1 - p.dtau * (p.mu[a] + band_energy(p, a, kx, ky))
                     out += [e, e]
     return np.array(out)
 
 
-@pytest.mark.parametrize("L,Nt", [(4, 6), (2, 5), (6, 3)])
-def test_free_spectrum_closed_form(L, Nt):
-    p = Params(L=L, Nt=Nt, g=0.0)
+# the hops of distance two of the paper's first nesting set, read along each band's weak direction
+T2 = dict(t_h=(1.0, 0.0), t_v=(0.0, 1.0), mu=(-0.47, 0.47), t2_h=(0.0, -0.45), t2_v=(0.45, 0.0))
+
+
+@pytest.mark.parametrize("L,Nt,kw", [(4, 6, {}), (2, 5, {}), (6, 3, {}), (6, 3, T2), (4, 4, T2), (2, 3, T2)])
+def test_free_spectrum_closed_form(L, Nt, kw):
+    p = Params(L=L, Nt=Nt, g=0.0, **kw)
     D = fermion.dense_D(p, rand_phi(p))
     assert match_multisets(np.linalg.eigvals(D), free_eigs_closed_form(p)) < 1e-12
 
 
-def test_free_logdet_closed_form():
+@pytest.mark.parametrize("kw", [{}, T2])
+def test_free_logdet_closed_form(kw):
     # prod over the Nt antiperiodic roots z_n of z^Nt = -1 of (z_n - a) has modulus |1 + a^Nt|
-    p = Params(L=4, Nt=6, g=0.0)
+    p = Params(L=6 if kw else 4, Nt=6, g=0.0, **kw)
     D = fermion.dense_D(p, rand_phi(p))
     _, logabs = np.linalg.slogdet(D @ D.conj().T)
     k = 2 * np.pi * np.arange(p.L) / p.L
     ref = 0.0
     for a in range(2):
-        eps = 2 * p.t_h[a] * np.cos(k)[:, None] + 2 * p.t_v[a] * np.cos(k)[None, :]
+        eps = band_energy(p, a, k[:, None], k[None, :])
         aa = 1 + p.dtau * (p.mu[a] + eps)
         ref += 2 * 2 * np.sum(np.log(np.abs(1 + aa ** p.Nt)))   # x2 spin, x2 for |det D|^2
     assert abs(logabs - ref) < 1e-10 * abs(ref)
 
 
-def test_det_real_nonnegative_and_conjugate_pairs():
+@pytest.mark.parametrize("kw", [{}, T2])
+def test_det_real_nonnegative_and_conjugate_pairs(kw):
     # Berg et al. (cited for sign-problem freedom): det D is real and >= 0 for any phi.
-    p = Params(L=4, Nt=6, g=1.3)
+    p = Params(L=4, Nt=6, g=1.3, **kw)
     D = fermion.dense_D(p, rand_phi(p, 5))
     sign, _ = np.linalg.slogdet(D)
     assert abs(sign - 1.0) < 1e-10
@@ -78,9 +90,10 @@ def test_det_real_nonnegative_and_conjugate_pairs():
     assert match_multisets(ev, np.conj(ev)) < 1e-9
 
 
-def test_antiunitary_symmetry():
+@pytest.mark.parametrize("kw", [{}, T2])
+def test_antiunitary_symmetry(kw):
     # T = (i sigma^y_spin x sigma^z_band) K with T^2 = -1 commutes with D: U conj(D) U^-1 = D.
-    p = Params(L=4, Nt=4, g=0.9)
+    p = Params(L=4, Nt=4, g=0.9, **kw)
     D = fermion.dense_D(p, rand_phi(p, 3))
     isy = np.array([[0, 1], [-1, 0]], dtype=complex)
     sz = np.diag([1.0, -1.0])
@@ -89,10 +102,11 @@ def test_antiunitary_symmetry():
     assert np.abs(U @ U.conj() + np.eye(p.n)).max() < 1e-13
 
 
-def test_uniform_phi_block_diagonalisation():
+@pytest.mark.parametrize("kw", [{}, T2])
+def test_uniform_phi_block_diagonalisation(kw):
     # Uniform phi: e^{iQ.r} couples k to k+Q, so D splits into 8x8 blocks over
     # (band, spin, {k, k+Q}) per Matsubara frequency; brute-force their eigenvalues.
-    p = Params(L=4, Nt=4, g=0.8)
+    p = Params(L=4, Nt=4, g=0.8, **kw)
     ph = np.array([0.3, -0.7, 0.5])
     phi = np.broadcast_to(ph[:, None, None, None], (3, p.Nt, p.L, p.L)).copy()
     D = fermion.dense_D(p, phi)
@@ -108,8 +122,7 @@ def test_uniform_phi_block_diagonalisation():
                 B = np.zeros((8, 8), dtype=complex)   # index (q, alpha, s), q = k or k+Q
                 for q, (kx, ky) in enumerate(ks):
                     for a in range(2):
-                        e = np.exp(1j * w) - 1 - p.dtau * (p.mu[a] + 2 * p.t_h[a] * np.cos(kx)
-                                                            + 2 * p.t_v[a] * np.cos(ky))
+                        e = np.exp(1j * w) - 1 - p.dtau * (p.mu[a] + band_energy(p, a, kx, ky))
                         for sp in range(2):
                             B[q * 4 + a * 2 + sp, q * 4 + a * 2 + sp] = e
                         for sp in range(2):
@@ -122,8 +135,9 @@ def test_uniform_phi_block_diagonalisation():
     assert match_multisets(np.concatenate([dense, dense]), eigs) < 1e-11
 
 
-def test_matrix_free_equals_dense():
-    p = Params(L=4, Nt=5, g=1.1)
+@pytest.mark.parametrize("L,kw", [(4, {}), (4, T2), (6, T2), (2, T2)])
+def test_matrix_free_equals_dense(L, kw):
+    p = Params(L=L, Nt=5, g=1.1, **kw)
     phi = rand_phi(p, 7)
     D = fermion.dense_D(p, phi)
     v = rand_vec(p, 8)
@@ -176,8 +190,9 @@ def test_twisted_fourier_diagonalises_K():
         assert np.abs(K @ v.ravel() - kh[a, n, mx, my] * v.ravel()).max() < 1e-13
 
 
-def test_precond_is_inverse_of_KKdag():
-    p = Params(L=4, Nt=6, g=0.7)
+@pytest.mark.parametrize("L,kw", [(4, {}), (6, T2)])
+def test_precond_is_inverse_of_KKdag(L, kw):
+    p = Params(L=L, Nt=6, g=0.7, **kw)
     K = fermion.dense_D(p, np.zeros((3, p.Nt, p.L, p.L)))
     v = rand_vec(p, 9)
     Pv = solver.apply_precond(p, v)
