@@ -95,10 +95,13 @@ def _coupling(p: Params, phi, v):
 
 def _spatial_hop(p: Params, alpha, v):
     """sum_{r'} t_{alpha, r, r'} v(r') on the periodic lattice; axes -2 = x, -1 = y."""
-    return (p.t_h[alpha] * (np.roll(v, 1, axis=-2) + np.roll(v, -1, axis=-2))
-            + p.t_v[alpha] * (np.roll(v, 1, axis=-1) + np.roll(v, -1, axis=-1))
-            + p.t2_h[alpha] * (np.roll(v, 2, axis=-2) + np.roll(v, -2, axis=-2))
-            + p.t2_v[alpha] * (np.roll(v, 2, axis=-1) + np.roll(v, -2, axis=-1)))
+    out = (p.t_h[alpha] * (np.roll(v, 1, axis=-2) + np.roll(v, -1, axis=-2))
+           + p.t_v[alpha] * (np.roll(v, 1, axis=-1) + np.roll(v, -1, axis=-1)))
+    if p.t2_h[alpha] != 0.0:   # hops of distance two (absent unless set)
+        out = out + p.t2_h[alpha] * (np.roll(v, 2, axis=-2) + np.roll(v, -2, axis=-2))
+    if p.t2_v[alpha] != 0.0:
+        out = out + p.t2_v[alpha] * (np.roll(v, 2, axis=-1) + np.roll(v, -2, axis=-1))
+    return out
 
 
 def time_sign(p: Params):
